@@ -1,0 +1,185 @@
+/*
+ * bs.h -- C ABI of libbs: visible-surface surfel sampling and progressive
+ * (greedy-permutation) ordering on a GB300 GPU (sm_103a), after Brandt et al.,
+ * "Rendering of Complex Heterogenous Scenes using Progressive Blue Surfels".
+ *
+ * Conventions shared by every call:
+ *  - Plain pointers and sizes only.  Unless a field says otherwise, array
+ *    pointers are CUDA DEVICE pointers owned by the caller; the library never
+ *    frees or keeps them after the call's stream work completes.
+ *  - Work is issued on the CUDA stream passed as `cuda_stream` (a cudaStream_t;
+ *    NULL = the legacy default stream) and is ordered with the caller's other
+ *    work on that stream.  Scratch memory is taken from the device's
+ *    stream-ordered memory pool on that stream and returned on it.
+ *  - The library never aborts.  Every failure returns a status and records a
+ *    message readable through bs_last_error() on the calling thread.  A CUDA
+ *    runtime error maps to BS_ECUDA.
+ *  - All arithmetic on the ordering path is integer; results are bit-exact and
+ *    do not depend on launch configuration, stream or batch composition.
+ */
+#ifndef BS_H
+#define BS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BS_OK = 0,
+    BS_EINVAL = 1,     /* argument out of range, non-finite vertex, zero extent */
+    BS_ENOMEM = 2,     /* device scratch or admission budget exhausted */
+    BS_EOVERFLOW = 3,  /* output capacity too small (the needed size is reported) */
+    BS_ETIMEOUT = 4,   /* a bounded device wait ran out of iterations */
+    BS_EBUSY = 5,      /* server queue full; retry later */
+    BS_ECUDA = 6,      /* CUDA runtime error */
+    BS_ENOTREADY = 7   /* server result not finished yet */
+} bs_status;
+
+/* Largest quantised coordinate: positions are integers in [0, 2^21 - 1]. */
+#define BS_QMAX 2097151
+/* Maximum raster resolution per direction and maximum number of directions. */
+#define BS_MAX_RES 4096
+#define BS_MAX_DIRS 26
+/* Largest part bs_order / bs_order_batched accept (points). */
+#define BS_MAX_POINTS 6291456u
+
+/* A triangle mesh of one scene node (Sec. 3: geometry in the node's subtree).
+ * xyz: nverts*3 float32 positions; tri: ntris*3 vertex indices (< nverts);
+ * face_rgb: ntris*3 bytes of per-face colour, or NULL (colour 0).  Device pointers. */
+typedef struct {
+    const float *xyz;
+    uint32_t nverts;
+    const uint32_t *tri;
+    uint32_t ntris;
+    const uint8_t *face_rgb;
+} bs_mesh;
+
+/* A view direction with integer components in {-1, 0, 1}, not all zero.  The
+ * camera sits on the +d side of the node and looks along -d (Sec. 3.1 renders
+ * from the bounding-box corners toward the centre; d = (+-1, +-1, +-1) are those
+ * corners, the six axis directions are also allowed). */
+typedef struct {
+    int8_t x, y, z;
+} bs_dir;
+
+/* A surfel array in canonical order (ascending Morton code of the position).
+ *  key : packed quantised position, x << 42 | y << 21 | z (21 bits each)
+ *  nrm : unit normal as 3 x int16 (round-half-even of 32767 * n / |n|), facing
+ *        the view it was sampled from; may be NULL for bs_order
+ *  rgb : 3 bytes of face colour; may be NULL for bs_order
+ *  src : emission index dir * res^2 + py * res + px of the kept pixel; may be NULL
+ *  n   : number of surfels (output of bs_sample_visible, input of bs_order)
+ *  cap : capacity of each array in rows (input of bs_sample_visible)
+ *  bbox_min, scale : world position = bbox_min + q / scale (output of
+ *        bs_sample_visible; bs_order reads scale to convert radii). */
+typedef struct {
+    uint64_t *key;
+    int16_t *nrm;
+    uint8_t *rgb;
+    uint32_t *src;
+    uint64_t n;
+    uint64_t cap;
+    float bbox_min[3];
+    double scale;
+} bs_surfels;
+
+/* Ordering options.
+ *  seed, part_id : the random starting surfel (Sec. 3.2) is
+ *      s = (w0 * n) >> 32, w0 = word 0 of Philox4x32-10(ctr = {part_id, 0, 0, 0},
+ *      key = {seed & 0xffffffff, seed >> 32}), unless start >= 0.
+ *  start     : explicit starting index (< n), or -1 for the Philox start.
+ *  max_count : order only the first max_count surfels (0 = all); the result is
+ *      exactly the prefix of the full ordering (Sec. 3.2 stops at a target count). */
+typedef struct {
+    uint64_t seed;
+    uint32_t part_id;
+    int64_t start;
+    uint64_t max_count;
+} bs_order_opts;
+
+/* bs_sample_visible -- initial surfel set (Sec. 3.1).
+ * Quantises the mesh to 21-bit integers over its bounding cube, rasterises it
+ * orthographically from each of `ndirs` directions at res x res pixels with an
+ * integer rasteriser (pixel-centre sampling, shared edges covered once, nearest
+ * depth wins, equal depth to the lower triangle id), emits one surfel per
+ * covered pixel, merges surfels with identical positions (keeping the smallest
+ * emission index) and writes them in ascending Morton order.
+ *  mesh  : device geometry (see bs_mesh); dirs: HOST array of ndirs directions.
+ *  res   : pixels per side, 1..BS_MAX_RES; ndirs: 1..BS_MAX_DIRS.
+ *  out   : caller-owned device arrays of out->cap rows (nrm, rgb, src may be NULL).
+ * Returns BS_OK with out->n, out->bbox_min, out->scale set; BS_EOVERFLOW with
+ * out->n set and nothing written when n > cap (n <= ndirs * res^2 always);
+ * BS_EINVAL for bad arguments, a non-finite vertex or a zero-extent mesh.
+ * Synchronises `cuda_stream` before returning (the count is read back). */
+bs_status bs_sample_visible(const bs_mesh *mesh, const bs_dir *dirs, int ndirs, int res,
+                            bs_surfels *out, void *cuda_stream);
+
+/* bs_order -- progressive ordering of one part (Sec. 3.2 goal; Sec. 4.1 radius).
+ * Computes the exact greedy permutation (farthest-first traversal) of the
+ * points s->key[0..n): perm[0] is the start index; perm[k] (k >= 1) is the
+ * unchosen point whose squared distance to the nearest chosen point is largest,
+ * ties to the lowest index; rad2[k] is that squared distance (int64, exact) and
+ * rad2[0] = INT64_MAX.  Every prefix of length k >= 2 is then an r-net with
+ * r^2 = rad2[k-1] (separation) covering all points within r^2 = rad2[k].
+ * radius[k] = (float)(sqrt((double)rad2[k]) / s->scale), +inf for k = 0: the
+ * splat radius in world units of the prefix of length k+1's covering.
+ *  s    : device keys, s->n points (1..BS_MAX_POINTS); s->scale > 0 if radius != NULL.
+ *  perm, rad2, radius : device outputs of m = min(max_count or n, n) entries;
+ *         rad2 and radius may be NULL.
+ * Duplicate keys are allowed: the remaining copies get rad2 = 0 and come last.
+ * Stream-ordered: returns after enqueueing (no host synchronisation). */
+bs_status bs_order(const bs_surfels *s, const bs_order_opts *opts, uint32_t *perm, int64_t *rad2,
+                   float *radius, void *cuda_stream);
+
+/* bs_order_batched -- bs_order for many independent parts in one persistent
+ * launch (the per-node preprocessing of Sec. 3.4 run for a whole scene).
+ *  parts : HOST array of nparts descriptors (device keys inside).
+ *  opts  : HOST array of nparts options (one per part).
+ *  perm, rad2, radius : HOST arrays of nparts DEVICE pointers (rad2/radius
+ *          arrays, or their entries, may be NULL).
+ * Results are bit-identical to calling bs_order on each part.  Stream-ordered. */
+bs_status bs_order_batched(const bs_surfels *parts, int nparts, const bs_order_opts *opts,
+                           uint32_t *const *perm, int64_t *const *rad2, float *const *radius,
+                           void *cuda_stream);
+
+/* ---- Serving: continuous batching of ordering requests (Sec. 3.4 at scale). ---- */
+typedef struct bs_server bs_server;
+
+/* Creates a server on the current CUDA device that keeps request state on the
+ * device, admitting requests while their scratch fits in device_budget_bytes.
+ * max_inflight bounds requests resident on the device at once (0 = 4096).
+ * Returns NULL and sets *st on failure. */
+bs_server *bs_server_create(uint64_t device_budget_bytes, int max_inflight, bs_status *st);
+
+/* Queues one ordering request.  key: HOST array of n packed positions (copied
+ * before return); scale: as in bs_surfels (for radius).  *ticket receives an id
+ * for bs_server_poll.  BS_EBUSY if the host queue is full; BS_ENOMEM if the
+ * request alone exceeds the device budget. */
+bs_status bs_server_submit(bs_server *srv, const uint64_t *key, uint64_t n, double scale,
+                           const bs_order_opts *opts, uint64_t *ticket);
+
+/* Drives the server (admits queued requests, launches work, retires finished
+ * ones) and, if the ticket's result is ready, copies it to the HOST arrays
+ * perm/rad2/radius (m entries; rad2/radius may be NULL) and releases it.
+ * BS_ENOTREADY while the request is queued or running; BS_EINVAL for an
+ * unknown ticket. */
+bs_status bs_server_poll(bs_server *srv, uint64_t ticket, uint32_t *perm, int64_t *rad2, float *radius);
+
+/* Per-ticket timestamps in seconds on the server's monotonic clock:
+ * t[0] submit, t[1] admitted to the device, t[2] finished on the device.
+ * Valid after bs_server_poll returned BS_OK for the ticket. */
+bs_status bs_server_times(bs_server *srv, uint64_t ticket, double t[3]);
+
+/* Waits for all in-flight work, frees device memory and the server. */
+void bs_server_destroy(bs_server *srv);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char *bs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BS_H */

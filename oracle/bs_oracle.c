@@ -107,6 +107,8 @@ int or_quantise(const float *xyz, uint64_t nverts, int32_t *q, float *bbox_min, 
         if (e > E) E = e;
     }
     if (!(E > 0.0)) return 1;
+    /* a -0.0 minimum is reported as +0.0 (x + 0 turns -0 into +0; no q changes) */
+    for (int a = 0; a < 3; a++) mn[a] = mn[a] + 0.0f;
     double S = 2097151.0 / E;
     for (uint64_t i = 0; i < nverts; i++)
         for (int a = 0; a < 3; a++) {

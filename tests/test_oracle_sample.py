@@ -327,3 +327,11 @@ def test_dedup_keeps_lowest_emission_index():
     hit = np.where(both["key"] == np.uint64(keyA))[0]
     assert len(hit) == 1
     assert int(both["src"][hit[0]]) == min(rows) < res * res
+
+
+def test_quantiser_negative_zero_minimum():
+    """A bbox minimum of -0.0 is reported as +0.0; the quantised positions are unchanged."""
+    xyz = np.array([[-0.0, 0, 0], [1, 1, 1], [0.0, 0.5, 0.5]], np.float32)
+    q, mn, s = oracle.quantise(xyz)
+    assert not np.signbit(mn).any()
+    assert q[0].tolist() == [0, 0, 0] and q[2].tolist() == [0, Q // 2, Q // 2]
