@@ -175,6 +175,20 @@ bs_status bs_server_times(bs_server *srv, uint64_t ticket, double t[3]);
 /* Waits for all in-flight work, frees device memory and the server. */
 void bs_server_destroy(bs_server *srv);
 
+/* Launch-shape knobs for the autotuner (results never depend on them):
+ *  "order_threads"      threads per ordering CTA (64, 128, 256, 512, 1024; 0 = auto)
+ *  "order_ctas_per_sm"  cap on resident ordering CTAs per SM (0 = occupancy limit)
+ *  "kernel_timing"      1 = record CUDA events around internal kernels (bs_last_launch_ms)
+ * Process-wide; BS_EINVAL for an unknown name or value. */
+bs_status bs_set_tuning(const char *name, int value);
+
+/* Device time in milliseconds of the most recent launch of an internal kernel,
+ * measured with CUDA events recorded on the launch's own stream around that one
+ * kernel.  Recording is off until bs_set_tuning("kernel_timing", 1).  kernel:
+ * "order_init", "order_loop" or "order_radius".  Waits for the stop event.
+ * BS_ENOTREADY if no timed launch happened yet; BS_EINVAL for an unknown name. */
+bs_status bs_last_launch_ms(const char *kernel, double *ms);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char *bs_last_error(void);
 

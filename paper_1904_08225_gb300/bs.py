@@ -1,0 +1,281 @@
+"""ctypes binding of libbs (include/bs.h): argument marshalling only.
+
+Every step of sampling and ordering runs in the CUDA kernels of libbs.so; this
+module allocates output tensors with PyTorch (device memory and streams are the
+only things taken from it), passes raw pointers and sizes across the C ABI and
+turns status codes into exceptions.  There is no CPU fallback: if the library or
+a GPU is missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+BS_OK, BS_EINVAL, BS_ENOMEM, BS_EOVERFLOW, BS_ETIMEOUT, BS_EBUSY, BS_ECUDA, BS_ENOTREADY = range(8)
+STATUS_NAMES = ["BS_OK", "BS_EINVAL", "BS_ENOMEM", "BS_EOVERFLOW", "BS_ETIMEOUT", "BS_EBUSY", "BS_ECUDA",
+                "BS_ENOTREADY"]
+INT64_MAX = (1 << 63) - 1
+
+# symbols include/bs.h declares; the library must export every one
+EXPORTS = ["bs_sample_visible", "bs_order", "bs_order_batched", "bs_server_create", "bs_server_submit",
+           "bs_server_poll", "bs_server_times", "bs_server_destroy", "bs_set_tuning", "bs_last_launch_ms",
+           "bs_last_error"]
+
+
+class BsError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class Mesh(C.Structure):
+    _fields_ = [("xyz", C.c_void_p), ("nverts", C.c_uint32), ("tri", C.c_void_p), ("ntris", C.c_uint32),
+                ("face_rgb", C.c_void_p)]
+
+
+class Dir(C.Structure):
+    _fields_ = [("x", C.c_int8), ("y", C.c_int8), ("z", C.c_int8)]
+
+
+class Surfels(C.Structure):
+    _fields_ = [("key", C.c_void_p), ("nrm", C.c_void_p), ("rgb", C.c_void_p), ("src", C.c_void_p),
+                ("n", C.c_uint64), ("cap", C.c_uint64), ("bbox_min", C.c_float * 3), ("scale", C.c_double)]
+
+
+class OrderOpts(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("part_id", C.c_uint32), ("start", C.c_int64), ("max_count", C.c_uint64)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_stale: bool = True) -> C.CDLL:
+    """Load libbs.so (compiling it first when sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_stale else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"libbs.so not found at {path}: build it with paper_1904_08225_gb300.build")
+            lib = C.CDLL(path)
+            P = C.c_void_p
+            lib.bs_sample_visible.argtypes = [C.POINTER(Mesh), C.POINTER(Dir), C.c_int, C.c_int, C.POINTER(Surfels), P]
+            lib.bs_order.argtypes = [C.POINTER(Surfels), C.POINTER(OrderOpts), P, P, P, P]
+            lib.bs_order_batched.argtypes = [C.POINTER(Surfels), C.c_int, C.POINTER(OrderOpts), P, P, P, P]
+            lib.bs_server_create.argtypes = [C.c_uint64, C.c_int, C.POINTER(C.c_int)]
+            lib.bs_server_create.restype = P
+            lib.bs_server_submit.argtypes = [P, P, C.c_uint64, C.c_double, C.POINTER(OrderOpts), C.POINTER(C.c_uint64)]
+            lib.bs_server_poll.argtypes = [P, C.c_uint64, P, P, P]
+            lib.bs_server_times.argtypes = [P, C.c_uint64, P]
+            lib.bs_server_destroy.argtypes = [P]
+            lib.bs_set_tuning.argtypes = [C.c_char_p, C.c_int]
+            lib.bs_last_launch_ms.argtypes = [C.c_char_p, C.POINTER(C.c_double)]
+            lib.bs_last_error.restype = C.c_char_p
+            for fn in EXPORTS[:-1]:
+                if fn != "bs_server_create" and fn != "bs_server_destroy":
+                    getattr(lib, fn).restype = C.c_int
+            _lib = lib
+    return _lib
+
+
+def last_error() -> str:
+    return load().bs_last_error().decode()
+
+
+def _check(st: int, where: str):
+    if st != BS_OK:
+        raise BsError(st, where, last_error())
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libbs needs a CUDA GPU; none is available")
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def set_tuning(name: str, value: int):
+    _check(load().bs_set_tuning(name.encode(), int(value)), "bs_set_tuning")
+
+
+def last_launch_ms(kernel: str) -> float:
+    """Device ms of the latest timed launch of an internal kernel (needs set_tuning("kernel_timing", 1))."""
+    ms = C.c_double(0.0)
+    _check(load().bs_last_launch_ms(kernel.encode(), C.byref(ms)), "bs_last_launch_ms")
+    return ms.value
+
+
+def sample_visible(xyz, tri, rgb, dirs, res: int, stream=None, cap: int | None = None):
+    """Visible-surface surfels of a mesh (Sec. 3.1) via bs_sample_visible.
+
+    xyz float32 (V,3), tri int32/uint32 (T,3), rgb uint8 (T,3) or None: CUDA tensors.
+    dirs: (D,3) integer directions.  Returns dict(key u64-as-int64 (N,), nrm int16 (N,3),
+    rgb uint8 (N,3), src int32-view of u32 (N,), bbox_min (3,), scale float).
+    """
+    torch = _torch()
+    lib = load()
+    d = np.asarray(dirs, dtype=np.int8).reshape(-1, 3)
+    darr = (Dir * len(d))(*[Dir(int(a), int(b), int(c)) for a, b, c in d])
+    dev = xyz.device
+    xyz = xyz.contiguous()
+    tri = tri.contiguous()
+    rgb = rgb.contiguous() if rgb is not None else None
+    mesh = Mesh(xyz.data_ptr(), xyz.shape[0], tri.data_ptr() if tri.numel() else None, tri.shape[0],
+                rgb.data_ptr() if rgb is not None else None)
+    if cap is None:
+        cap = len(d) * res * res
+    key = torch.empty(cap, dtype=torch.int64, device=dev)
+    nrm = torch.empty((cap, 3), dtype=torch.int16, device=dev)
+    col = torch.empty((cap, 3), dtype=torch.uint8, device=dev)
+    src = torch.empty(cap, dtype=torch.int32, device=dev)
+    out = Surfels(key.data_ptr(), nrm.data_ptr(), col.data_ptr(), src.data_ptr(), 0, cap, (C.c_float * 3)(), 0.0)
+    st = lib.bs_sample_visible(C.byref(mesh), darr, len(d), int(res), C.byref(out), _stream(stream))
+    _check(st, "bs_sample_visible")
+    n = int(out.n)
+    return dict(key=key[:n], nrm=nrm[:n], rgb=col[:n], src=src[:n], n=n,
+                bbox_min=np.array(list(out.bbox_min), np.float32), scale=float(out.scale))
+
+
+def _opts(seed=0, part_id=0, start=-1, max_count=0) -> OrderOpts:
+    return OrderOpts(int(seed) & (2**64 - 1), int(part_id), int(start), int(max_count))
+
+
+def order(key, start: int = -1, seed: int = 0, part_id: int = 0, max_count: int = 0, scale: float = 1.0,
+          stream=None, want_radius: bool = True, out=None):
+    """Exact greedy permutation of one part (bs_order).  key: CUDA int64 tensor (N,).
+
+    Returns (perm int32 view of u32 (m,), rad2 int64 (m,), radius float32 (m,) or None).
+    """
+    torch = _torch()
+    lib = load()
+    n = key.shape[0]
+    m = n if max_count == 0 or max_count > n else max_count
+    if out is None:
+        perm = torch.empty(m, dtype=torch.int32, device=key.device)
+        rad2 = torch.empty(m, dtype=torch.int64, device=key.device)
+        radius = torch.empty(m, dtype=torch.float32, device=key.device) if want_radius else None
+    else:
+        perm, rad2, radius = out
+    s = Surfels(key.data_ptr(), None, None, None, n, n, (C.c_float * 3)(), float(scale))
+    o = _opts(seed, part_id, start, max_count)
+    st = lib.bs_order(C.byref(s), C.byref(o), _ptr(perm), _ptr(rad2), _ptr(radius), _stream(stream))
+    _check(st, "bs_order")
+    return perm, rad2, radius
+
+
+def order_batched(keys, starts=None, seeds=None, part_ids=None, max_counts=None, scales=None, stream=None,
+                  want_radius: bool = True, outs=None):
+    """bs_order_batched over a list of CUDA int64 key tensors; returns a list of (perm, rad2, radius)."""
+    torch = _torch()
+    lib = load()
+    P = len(keys)
+    starts = starts if starts is not None else [-1] * P
+    seeds = seeds if seeds is not None else [0] * P
+    part_ids = part_ids if part_ids is not None else list(range(P))
+    max_counts = max_counts if max_counts is not None else [0] * P
+    scales = scales if scales is not None else [1.0] * P
+    parts = (Surfels * P)()
+    opts = (OrderOpts * P)()
+    pp = (C.c_void_p * P)()
+    rp = (C.c_void_p * P)()
+    fp = (C.c_void_p * P)()
+    result = []
+    for i, k in enumerate(keys):
+        n = k.shape[0]
+        m = n if max_counts[i] == 0 or max_counts[i] > n else max_counts[i]
+        if outs is None:
+            perm = torch.empty(m, dtype=torch.int32, device=k.device)
+            rad2 = torch.empty(m, dtype=torch.int64, device=k.device)
+            radius = torch.empty(m, dtype=torch.float32, device=k.device) if want_radius else None
+        else:
+            perm, rad2, radius = outs[i]
+        parts[i] = Surfels(k.data_ptr(), None, None, None, n, n, (C.c_float * 3)(), float(scales[i]))
+        opts[i] = _opts(seeds[i], part_ids[i], starts[i], max_counts[i])
+        pp[i] = perm.data_ptr()
+        rp[i] = rad2.data_ptr()
+        fp[i] = radius.data_ptr() if radius is not None else None
+        result.append((perm, rad2, radius))
+    st = lib.bs_order_batched(parts, P, opts, C.cast(pp, C.c_void_p), C.cast(rp, C.c_void_p),
+                              C.cast(fp, C.c_void_p), _stream(stream))
+    _check(st, "bs_order_batched")
+    return result
+
+
+class Server:
+    """Continuous-batching ordering server (bs_server_*); host arrays in and out."""
+
+    def __init__(self, budget_bytes: int = 64 << 30, max_inflight: int = 0):
+        _torch()
+        self._lib = load()
+        st = C.c_int(0)
+        self._h = self._lib.bs_server_create(int(budget_bytes), int(max_inflight), C.byref(st))
+        if not self._h:
+            raise BsError(st.value, "bs_server_create", last_error())
+        self._m = {}
+
+    def submit(self, key: np.ndarray, scale: float = 1.0, start: int = -1, seed: int = 0, part_id: int = 0,
+               max_count: int = 0) -> int:
+        k = np.ascontiguousarray(key, dtype=np.uint64)
+        t = C.c_uint64(0)
+        o = _opts(seed, part_id, start, max_count)
+        st = self._lib.bs_server_submit(self._h, k.ctypes.data_as(C.c_void_p), k.shape[0], float(scale), C.byref(o),
+                                        C.byref(t))
+        _check(st, "bs_server_submit")
+        n = k.shape[0]
+        self._m[t.value] = n if max_count == 0 or max_count > n else max_count
+        return t.value
+
+    def poll(self, ticket: int):
+        """(perm u32, rad2 i64, radius f32) numpy arrays, or None while not ready."""
+        m = self._m[ticket]
+        perm = np.empty(m, np.uint32)
+        rad2 = np.empty(m, np.int64)
+        radius = np.empty(m, np.float32)
+        st = self._lib.bs_server_poll(self._h, ticket, perm.ctypes.data_as(C.c_void_p),
+                                      rad2.ctypes.data_as(C.c_void_p), radius.ctypes.data_as(C.c_void_p))
+        if st == BS_ENOTREADY:
+            return None
+        _check(st, "bs_server_poll")
+        return perm, rad2, radius
+
+    def times(self, ticket: int):
+        t = (C.c_double * 3)()
+        _check(self._lib.bs_server_times(self._h, ticket, t), "bs_server_times")
+        return tuple(t)
+
+    def close(self):
+        if self._h:
+            self._lib.bs_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,449 @@
+// bs_api.cu -- the extern "C" entry points of libbs (declared in include/bs.h):
+// argument validation, start-index selection, and the serving loop.
+#include <chrono>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "bs_internal.cuh"
+
+namespace bs {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+void clear_error() { g_err[0] = 0; }
+
+// Validates one part and fills a descriptor (device pointers from the caller).
+static bs_status make_part(const bs_surfels *s, const bs_order_opts *opts, uint32_t *perm, int64_t *rad2,
+                           float *radius, PartDesc &p) {
+    if (!s || !opts) { set_error("bs_order: NULL argument"); return BS_EINVAL; }
+    if (s->n == 0 || s->n > BS_MAX_POINTS) {
+        set_error("bs_order: n=%llu outside [1, %u]", (unsigned long long)s->n, BS_MAX_POINTS);
+        return s->n == 0 ? BS_EINVAL : BS_EOVERFLOW;
+    }
+    if (!s->key || !perm) { set_error("bs_order: NULL key or perm array"); return BS_EINVAL; }
+    if (radius && !(s->scale > 0.0)) { set_error("bs_order: radius requested but scale <= 0"); return BS_EINVAL; }
+    uint64_t start;
+    if (opts->start >= 0) {
+        if ((uint64_t)opts->start >= s->n) {
+            set_error("bs_order: start %lld >= n %llu", (long long)opts->start, (unsigned long long)s->n);
+            return BS_EINVAL;
+        }
+        start = (uint64_t)opts->start;
+    } else {
+        start = start_from_seed(s->n, opts->seed, opts->part_id);
+    }
+    const uint64_t m = (opts->max_count == 0 || opts->max_count > s->n) ? s->n : opts->max_count;
+    memset(&p, 0, sizeof(p));
+    p.key = s->key;
+    p.perm = perm;
+    p.rad2 = rad2;
+    p.radius = radius;
+    p.scale = s->scale;
+    p.n = (uint32_t)s->n;
+    p.m = (uint32_t)m;
+    p.start = (uint32_t)start;
+    return BS_OK;
+}
+
+}  // namespace bs
+
+using namespace bs;
+
+extern "C" {
+
+const char *bs_last_error(void) { return g_err; }
+
+bs_status bs_set_tuning(const char *name, int value) {
+    static int threads = 0, ctas = 0;
+    if (!name) { set_error("bs_set_tuning: NULL name"); return BS_EINVAL; }
+    if (!strcmp(name, "order_threads")) {
+        if (value != 0 && value != 64 && value != 128 && value != 256 && value != 512 && value != 1024) {
+            set_error("bs_set_tuning: order_threads=%d not in {0,64,128,256,512,1024}", value);
+            return BS_EINVAL;
+        }
+        threads = value;
+    } else if (!strcmp(name, "kernel_timing")) {
+        if (value != 0 && value != 1) { set_error("bs_set_tuning: kernel_timing=%d not 0 or 1", value); return BS_EINVAL; }
+        order_set_kernel_timing(value == 1);
+        return BS_OK;
+    } else if (!strcmp(name, "order_ctas_per_sm")) {
+        if (value < 0 || value > 32) { set_error("bs_set_tuning: order_ctas_per_sm=%d outside [0,32]", value); return BS_EINVAL; }
+        ctas = value;
+    } else {
+        set_error("bs_set_tuning: unknown knob '%s'", name);
+        return BS_EINVAL;
+    }
+    order_set_tuning(threads, ctas);
+    return BS_OK;
+}
+
+bs_status bs_last_launch_ms(const char *kernel, double *ms) {
+    clear_error();
+    if (!kernel || !ms) { set_error("bs_last_launch_ms: NULL argument"); return BS_EINVAL; }
+    int which = -1;
+    if (!strcmp(kernel, "order_init")) which = 0;
+    else if (!strcmp(kernel, "order_loop")) which = 1;
+    else if (!strcmp(kernel, "order_radius")) which = 2;
+    if (which < 0) { set_error("bs_last_launch_ms: unknown kernel '%s'", kernel); return BS_EINVAL; }
+    bs_status st = order_last_launch_ms(which, ms);
+    if (st == BS_ENOTREADY) set_error("bs_last_launch_ms: no timed launch of %s yet", kernel);
+    if (st == BS_ECUDA) set_error("bs_last_launch_ms: event query failed");
+    return st;
+}
+
+bs_status bs_sample_visible(const bs_mesh *mesh, const bs_dir *dirs, int ndirs, int res, bs_surfels *out,
+                            void *cuda_stream) {
+    clear_error();
+    return sample_visible(mesh, dirs, ndirs, res, out, (cudaStream_t)cuda_stream);
+}
+
+bs_status bs_order(const bs_surfels *s, const bs_order_opts *opts, uint32_t *perm, int64_t *rad2, float *radius,
+                   void *cuda_stream) {
+    clear_error();
+    std::vector<PartDesc> parts(1);
+    bs_status st = make_part(s, opts, perm, rad2, radius, parts[0]);
+    if (st != BS_OK) return st;
+    return order_parts(parts, (cudaStream_t)cuda_stream, false);
+}
+
+bs_status bs_order_batched(const bs_surfels *parts, int nparts, const bs_order_opts *opts, uint32_t *const *perm,
+                           int64_t *const *rad2, float *const *radius, void *cuda_stream) {
+    clear_error();
+    if (nparts < 0 || (nparts > 0 && (!parts || !opts || !perm))) { set_error("bs_order_batched: bad arguments"); return BS_EINVAL; }
+    std::vector<PartDesc> hp((size_t)nparts);
+    for (int i = 0; i < nparts; ++i) {
+        bs_status st = make_part(&parts[i], &opts[i], perm[i], rad2 ? rad2[i] : nullptr, radius ? radius[i] : nullptr, hp[i]);
+        if (st != BS_OK) {
+            char msg[512];
+            snprintf(msg, sizeof(msg), "part %d: %s", i, bs_last_error());
+            set_error("%s", msg);
+            return st;
+        }
+    }
+    return order_parts(hp, (cudaStream_t)cuda_stream, true);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Server: continuous batching.  A host thread admits queued requests while their
+// device footprint fits the budget and a stream is free, launches them as one
+// batched ordering on that stream (so batches on different streams overlap on
+// the device), and retires a batch when its completion event fires.
+// ---------------------------------------------------------------------------
+namespace bs {
+
+struct SrvReq {
+    uint64_t ticket;
+    std::vector<uint64_t> key;
+    double scale;
+    bs_order_opts opts;
+    uint64_t n, m, bytes;
+    char *dmem;  // device block: key | perm | rad2 | radius
+    size_t stage_off;
+    std::vector<uint32_t> perm;
+    std::vector<int64_t> rad2;
+    std::vector<float> radius;
+    double t[3];
+    int state;  // 0 queued, 1 running, 2 done, 3 failed
+    bs_status err;
+};
+
+struct SrvSlot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    std::vector<SrvReq *> reqs;
+    char *stage = nullptr;  // pinned host staging for results
+    size_t stage_cap = 0;
+    bool busy = false;
+};
+
+}  // namespace bs
+
+struct bs_server {
+    int device = 0;
+    uint64_t budget = 0, used = 0;
+    int max_inflight = 4096, inflight = 0;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<bs::SrvReq *> queue;
+    std::unordered_map<uint64_t, bs::SrvReq *> all;
+    std::vector<bs::SrvSlot> slots;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    std::thread driver;
+    std::chrono::steady_clock::time_point t0;
+    size_t max_queue = 1u << 20;
+    double now() const {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+namespace bs {
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static size_t req_bytes(uint64_t n) {
+    // key + outputs + ordering scratch (D, bucket and group records) + slack
+    const uint64_t nb = (n + 31) / 32, ng = (nb + 31) / 32;
+    return (size_t)(n * 8 + n * 4 + n * 8 + n * 4) + (size_t)(n * 8 + nb * 32 + ng * 32) + 4096;
+}
+
+static void retire(bs_server *S, SrvSlot &slot) {
+    const double t = S->now();
+    for (SrvReq *r : slot.reqs) {
+        if (r->state == 1) {
+            memcpy(r->perm.data(), slot.stage + r->stage_off, r->m * 4);
+            memcpy(r->rad2.data(), slot.stage + r->stage_off + align256(r->m * 4), r->m * 8);
+            memcpy(r->radius.data(), slot.stage + r->stage_off + align256(r->m * 4) + align256(r->m * 8), r->m * 4);
+            r->state = 2;
+        }
+        r->t[2] = t;
+        if (r->dmem) cudaFreeAsync(r->dmem, slot.stream);
+        r->dmem = nullptr;
+        S->used -= r->bytes;
+        S->inflight -= 1;
+    }
+    slot.reqs.clear();
+    slot.busy = false;
+}
+
+static void launch_batch(bs_server *S, SrvSlot &slot, std::vector<SrvReq *> &batch) {
+    // device memory, H2D keys, ordering, D2H results into pinned staging
+    size_t stage = 0;
+    for (SrvReq *r : batch) {
+        r->stage_off = stage;
+        stage += align256(r->m * 4) + align256(r->m * 8) + align256(r->m * 4);
+    }
+    if (stage > slot.stage_cap) {
+        if (slot.stage) cudaFreeHost(slot.stage);
+        slot.stage = nullptr;
+        slot.stage_cap = 0;
+        if (cudaHostAlloc((void **)&slot.stage, stage * 2, cudaHostAllocDefault) == cudaSuccess) slot.stage_cap = stage * 2;
+        else cudaGetLastError();
+    }
+    std::vector<PartDesc> parts;
+    std::vector<SrvReq *> run;
+    const double t = S->now();
+    for (SrvReq *r : batch) {
+        r->t[1] = t;
+        bool ok = slot.stage != nullptr;
+        if (ok && cudaMallocAsync((void **)&r->dmem, r->bytes, slot.stream) != cudaSuccess) {
+            cudaGetLastError();
+            ok = false;
+        }
+        if (!ok) { r->state = 3; r->err = BS_ENOMEM; r->dmem = nullptr; continue; }
+        uint64_t *dk = (uint64_t *)r->dmem;
+        uint32_t *dp = (uint32_t *)(r->dmem + align256(r->n * 8));
+        int64_t *dr = (int64_t *)(r->dmem + align256(r->n * 8) + align256(r->m * 4));
+        float *df = (float *)(r->dmem + align256(r->n * 8) + align256(r->m * 4) + align256(r->m * 8));
+        cudaMemcpyAsync(dk, r->key.data(), r->n * 8, cudaMemcpyHostToDevice, slot.stream);
+        bs_surfels s{};
+        s.key = dk;
+        s.n = r->n;
+        s.scale = r->scale;
+        PartDesc p;
+        memset(&p, 0, sizeof(p));
+        p.key = dk; p.perm = dp; p.rad2 = dr; p.radius = df; p.scale = r->scale;
+        p.n = (uint32_t)r->n; p.m = (uint32_t)r->m;
+        p.start = (uint32_t)(r->opts.start >= 0 ? (uint64_t)r->opts.start : start_from_seed(r->n, r->opts.seed, r->opts.part_id));
+        parts.push_back(p);
+        run.push_back(r);
+        r->state = 1;
+    }
+    if (!parts.empty()) {
+        bs_status st = order_parts(parts, slot.stream, true);
+        for (size_t i = 0; i < run.size(); ++i) {
+            SrvReq *r = run[i];
+            if (st != BS_OK) { r->state = 3; r->err = st; continue; }
+            cudaMemcpyAsync(slot.stage + r->stage_off, parts[i].perm, r->m * 4, cudaMemcpyDeviceToHost, slot.stream);
+            cudaMemcpyAsync(slot.stage + r->stage_off + align256(r->m * 4), parts[i].rad2, r->m * 8, cudaMemcpyDeviceToHost, slot.stream);
+            cudaMemcpyAsync(slot.stage + r->stage_off + align256(r->m * 4) + align256(r->m * 8), parts[i].radius, r->m * 4,
+                            cudaMemcpyDeviceToHost, slot.stream);
+        }
+    }
+    cudaEventRecord(slot.done, slot.stream);
+    slot.reqs = batch;
+    slot.busy = true;
+}
+
+static void driver_loop(bs_server *S) {
+    cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (!S->stop) {
+        bool progressed = false;
+        for (SrvSlot &slot : S->slots) {
+            if (slot.busy && cudaEventQuery(slot.done) == cudaSuccess) {
+                retire(S, slot);
+                progressed = true;
+            }
+        }
+        if (progressed) S->cv.notify_all();
+        for (SrvSlot &slot : S->slots) {
+            if (slot.busy || S->queue.empty()) continue;
+            std::vector<SrvReq *> batch;
+            while (!S->queue.empty() && S->inflight < S->max_inflight) {
+                SrvReq *r = S->queue.front();
+                if (S->used + r->bytes > S->budget) break;  // FIFO admission under the memory budget
+                S->queue.pop_front();
+                S->used += r->bytes;
+                S->inflight += 1;
+                batch.push_back(r);
+            }
+            if (batch.empty()) break;
+            launch_batch(S, slot, batch);
+            progressed = true;
+        }
+        if (!progressed) {
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            lk.lock();
+        }
+    }
+}
+
+}  // namespace bs
+
+extern "C" {
+
+bs_server *bs_server_create(uint64_t device_budget_bytes, int max_inflight, bs_status *st) {
+    clear_error();
+    if (device_budget_bytes == 0 || max_inflight < 0) {
+        set_error("bs_server_create: budget must be > 0 and max_inflight >= 0");
+        if (st) *st = BS_EINVAL;
+        return nullptr;
+    }
+    bs_server *S = new (std::nothrow) bs_server();
+    if (!S) { if (st) *st = BS_ENOMEM; return nullptr; }
+    cudaGetDevice(&S->device);
+    S->budget = device_budget_bytes;
+    S->max_inflight = max_inflight ? max_inflight : 4096;
+    S->t0 = std::chrono::steady_clock::now();
+    S->slots.resize(4);
+    for (SrvSlot &slot : S->slots) {
+        if (cudaStreamCreateWithFlags(&slot.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&slot.done, cudaEventDisableTiming) != cudaSuccess) {
+            set_error("bs_server_create: stream/event creation failed: %s", cudaGetErrorString(cudaGetLastError()));
+            if (st) *st = BS_ECUDA;
+            for (SrvSlot &s2 : S->slots) {
+                if (s2.stream) cudaStreamDestroy(s2.stream);
+                if (s2.done) cudaEventDestroy(s2.done);
+            }
+            delete S;
+            return nullptr;
+        }
+    }
+    S->driver = std::thread(driver_loop, S);
+    if (st) *st = BS_OK;
+    return S;
+}
+
+bs_status bs_server_submit(bs_server *S, const uint64_t *key, uint64_t n, double scale, const bs_order_opts *opts,
+                           uint64_t *ticket) {
+    clear_error();
+    if (!S || !key || !opts || !ticket) { set_error("bs_server_submit: NULL argument"); return BS_EINVAL; }
+    if (n == 0 || n > BS_MAX_POINTS) { set_error("bs_server_submit: n=%llu outside [1,%u]", (unsigned long long)n, BS_MAX_POINTS); return BS_EINVAL; }
+    if (opts->start >= 0 && (uint64_t)opts->start >= n) { set_error("bs_server_submit: start >= n"); return BS_EINVAL; }
+    if (!(scale > 0.0)) { set_error("bs_server_submit: scale must be > 0"); return BS_EINVAL; }
+    SrvReq *r = new (std::nothrow) SrvReq();
+    if (!r) return BS_ENOMEM;
+    r->n = n;
+    r->m = (opts->max_count == 0 || opts->max_count > n) ? n : opts->max_count;
+    r->bytes = req_bytes(n);
+    if (r->bytes > S->budget) {
+        delete r;
+        set_error("bs_server_submit: request needs %llu bytes, budget is %llu", (unsigned long long)req_bytes(n),
+                  (unsigned long long)S->budget);
+        return BS_ENOMEM;
+    }
+    r->key.assign(key, key + n);
+    r->scale = scale;
+    r->opts = *opts;
+    r->perm.resize(r->m);
+    r->rad2.resize(r->m);
+    r->radius.resize(r->m);
+    r->state = 0;
+    r->err = BS_OK;
+    r->dmem = nullptr;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->queue.size() >= S->max_queue) { delete r; set_error("bs_server_submit: queue full"); return BS_EBUSY; }
+    r->ticket = S->next_ticket++;
+    r->t[0] = S->now();
+    r->t[1] = r->t[2] = 0.0;
+    S->queue.push_back(r);
+    S->all[r->ticket] = r;
+    *ticket = r->ticket;
+    return BS_OK;
+}
+
+bs_status bs_server_poll(bs_server *S, uint64_t ticket, uint32_t *perm, int64_t *rad2, float *radius) {
+    clear_error();
+    if (!S) { set_error("bs_server_poll: NULL server"); return BS_EINVAL; }
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->all.find(ticket);
+    if (it == S->all.end()) { set_error("bs_server_poll: unknown ticket %llu", (unsigned long long)ticket); return BS_EINVAL; }
+    SrvReq *r = it->second;
+    if (r->state == 0 || r->state == 1) return BS_ENOTREADY;
+    if (r->state == 3) {
+        set_error("bs_server_poll: request %llu failed", (unsigned long long)ticket);
+        return r->err == BS_OK ? BS_ECUDA : r->err;
+    }
+    if (r->state == 4) { set_error("bs_server_poll: ticket %llu already collected", (unsigned long long)ticket); return BS_EINVAL; }
+    if (perm) memcpy(perm, r->perm.data(), r->m * 4);
+    if (rad2) memcpy(rad2, r->rad2.data(), r->m * 8);
+    if (radius) memcpy(radius, r->radius.data(), r->m * 4);
+    r->state = 4;
+    std::vector<uint64_t>().swap(r->key);
+    std::vector<uint32_t>().swap(r->perm);
+    std::vector<int64_t>().swap(r->rad2);
+    std::vector<float>().swap(r->radius);
+    return BS_OK;
+}
+
+bs_status bs_server_times(bs_server *S, uint64_t ticket, double t[3]) {
+    clear_error();
+    if (!S || !t) { set_error("bs_server_times: NULL argument"); return BS_EINVAL; }
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->all.find(ticket);
+    if (it == S->all.end()) { set_error("bs_server_times: unknown ticket"); return BS_EINVAL; }
+    SrvReq *r = it->second;
+    if (r->state < 2) return BS_ENOTREADY;
+    t[0] = r->t[0]; t[1] = r->t[1]; t[2] = r->t[2];
+    return BS_OK;
+}
+
+void bs_server_destroy(bs_server *S) {
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    if (S->driver.joinable()) S->driver.join();
+    for (SrvSlot &slot : S->slots) {
+        if (slot.busy) {
+            cudaEventSynchronize(slot.done);
+            retire(S, slot);
+        }
+        if (slot.stage) cudaFreeHost(slot.stage);
+        cudaEventDestroy(slot.done);
+        cudaStreamDestroy(slot.stream);
+    }
+    for (auto &kv : S->all) delete kv.second;
+    for (SrvReq *r : S->queue) (void)r;  // queued requests are owned by `all`
+    delete S;
+}
+
+}  // extern "C"

@@ -1,0 +1,58 @@
+"""CPU checks of the C-ABI boundary: libbs.so builds, loads and exports what include/bs.h declares."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_1904_08225_gb300 import bs, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "bs.h")).read()
+    decl = r"^(?:bs_status|bs_server\s*\*|void|const char\s*\*)\s*(bs_[a-z_]+)\s*\("
+    return sorted(set(re.findall(decl, src, flags=re.M)))
+
+
+def test_header_and_binding_agree():
+    assert _declared() == sorted(bs.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = C.CDLL(build.build())
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_error_message_and_tuning_validation():
+    lib = bs.load()
+    assert lib.bs_set_tuning(b"order_threads", 100) == bs.BS_EINVAL
+    assert "order_threads" in bs.last_error()
+    assert lib.bs_set_tuning(b"nope", 1) == bs.BS_EINVAL
+    assert lib.bs_set_tuning(b"order_threads", 0) == bs.BS_OK
+
+
+def test_bad_arguments_rejected_without_gpu():
+    """Argument checks happen on the host before any device call."""
+    lib = bs.load()
+    s = bs.Surfels(None, None, None, None, 0, 0, (C.c_float * 3)(), 1.0)
+    o = bs.OrderOpts(0, 0, -1, 0)
+    assert lib.bs_order(C.byref(s), C.byref(o), None, None, None, None) == bs.BS_EINVAL
+    s.n = 1 << 40
+    assert lib.bs_order(C.byref(s), C.byref(o), None, None, None, None) == bs.BS_EOVERFLOW
+    mesh = bs.Mesh(None, 0, None, 0, None)
+    d = (bs.Dir * 1)(bs.Dir(0, 0, 1))
+    out = bs.Surfels(None, None, None, None, 0, 0, (C.c_float * 3)(), 0.0)
+    assert lib.bs_sample_visible(C.byref(mesh), d, 1, 64, C.byref(out), None) == bs.BS_EINVAL
+    mesh.nverts = 3
+    mesh.xyz = 16
+    assert lib.bs_sample_visible(C.byref(mesh), d, 1, 0, C.byref(out), None) == bs.BS_EINVAL
+    assert lib.bs_sample_visible(C.byref(mesh), d, 0, 64, C.byref(out), None) == bs.BS_EINVAL
+    bad = (bs.Dir * 1)(bs.Dir(0, 0, 0))
+    assert lib.bs_sample_visible(C.byref(mesh), bad, 1, 64, C.byref(out), None) == bs.BS_EINVAL
+    bad = (bs.Dir * 1)(bs.Dir(2, 0, 0))
+    assert lib.bs_sample_visible(C.byref(mesh), bad, 1, 64, C.byref(out), None) == bs.BS_EINVAL
+    st = C.c_int(0)
+    assert lib.bs_server_create(0, 0, C.byref(st)) is None and st.value == bs.BS_EINVAL

@@ -1,0 +1,304 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, bit for bit.
+
+Everything on this path is integer or correctly rounded IEEE arithmetic, so the
+tolerance is zero: surfel arrays, permutations, squared radii and float radii
+must be identical.  Inputs are seeded synthetic meshes from ``workloads``.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1904_08225_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+I64MAX = np.iinfo(np.int64).max
+
+
+@pytest.fixture(scope="module")
+def bs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1904_08225_gb300 import bs as _bs
+    _bs.load()
+    return _bs
+
+
+def _dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.view(dtype)
+    return t.cuda()
+
+
+def _gpu_sample(bs, mesh, dirs, res):
+    xyz = _dev(mesh.xyz)
+    tri = _dev(mesh.tri.view(np.int32))
+    rgb = _dev(mesh.rgb) if mesh.rgb is not None else None
+    return bs.sample_visible(xyz, tri, rgb, dirs, res)
+
+
+def _np(t, dtype=None):
+    a = t.cpu().numpy()
+    return a.view(dtype) if dtype is not None else a
+
+
+def _check_sample(g, ref, mn, s):
+    assert g["n"] == len(ref["key"])
+    assert np.array_equal(_np(g["key"], np.uint64), ref["key"])
+    assert np.array_equal(_np(g["nrm"]), ref["nrm"])
+    assert np.array_equal(_np(g["rgb"]), ref["rgb"])
+    assert np.array_equal(_np(g["src"], np.uint32), ref["src"])
+    assert g["scale"] == s
+    assert np.array_equal(g["bbox_min"].view(np.uint32), mn.view(np.uint32))
+
+
+def _check_order(bs, key_np, start=-1, seed=0, part_id=0, max_count=0, scale=1.0):
+    key = _dev(key_np.view(np.int64))
+    perm, rad2, radius = bs.order(key, start=start, seed=seed, part_id=part_id, max_count=max_count, scale=scale)
+    s = oracle.start_index(len(key_np), seed=seed, part_id=part_id, start=start)
+    rp, rr = oracle.greedy(key_np, s, max_count=max_count)
+    assert np.array_equal(_np(perm, np.uint32), rp)
+    assert np.array_equal(_np(rad2), rr)
+    assert np.array_equal(_np(radius).view(np.uint32), oracle.radius(rr, scale).view(np.uint32))
+    return rp, rr
+
+
+def test_sample_torus_parity(bs):
+    """Torus (R=1, r=0.3, 128x64 quads) from the 6 axis directions at 128^2."""
+    m = W.torus(seed=0)
+    ref, mn, s = oracle.sample_mesh(m, W.AXIS_DIRS, 128)
+    _check_sample(_gpu_sample(bs, m, W.AXIS_DIRS, 128), ref, mn, s)
+
+
+@pytest.mark.parametrize("res,dirs", [(1, "axis"), (7, "axis"), (96, "corners"), (200, "axis+diag")])
+def test_sample_small_cad_parity(bs, res, dirs):
+    m = W.cad_part(seed=5, nboxes=60, ncyl=20)
+    D = {"axis": W.AXIS_DIRS, "corners": W.CORNER_DIRS,
+         "axis+diag": np.concatenate([W.AXIS_DIRS, W.DIAG_DIRS])}[dirs]
+    ref, mn, s = oracle.sample_mesh(m, D, res)
+    _check_sample(_gpu_sample(bs, m, D, res), ref, mn, s)
+
+
+def test_sample_face_and_edge_directions(bs):
+    """All 26 integer directions, including face and edge diagonals."""
+    import itertools
+    D = np.array([d for d in itertools.product([-1, 0, 1], repeat=3) if any(d)], np.int8)
+    m = W.torus(nu=40, nv=20, seed=2)
+    ref, mn, s = oracle.sample_mesh(m, D, 64)
+    _check_sample(_gpu_sample(bs, m, D, 64), ref, mn, s)
+
+
+def test_sample_overflow_and_invalid(bs):
+    m = W.torus(nu=16, nv=8)
+    xyz, tri = _dev(m.xyz), _dev(m.tri.view(np.int32))
+    with pytest.raises(bs.BsError) as e:
+        bs.sample_visible(xyz, tri, None, W.AXIS_DIRS, 32, cap=10)
+    assert e.value.status == bs.BS_EOVERFLOW
+    bad = m.xyz.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(bs.BsError) as e:
+        bs.sample_visible(_dev(bad), tri, None, W.AXIS_DIRS, 32)
+    assert e.value.status == bs.BS_EINVAL
+    flat = np.zeros_like(m.xyz)
+    with pytest.raises(bs.BsError) as e:
+        bs.sample_visible(_dev(flat), tri, None, W.AXIS_DIRS, 32)
+    assert e.value.status == bs.BS_EINVAL
+    # degenerate-only mesh: no surfels, not an error
+    deg = np.array([[0, 0, 0], [1, 1, 1], [2, 2, 2]], np.float32)
+    g = bs.sample_visible(_dev(deg), _dev(np.array([[0, 1, 2]], np.int32)), None, W.AXIS_DIRS, 16)
+    assert g["n"] == 0
+
+
+def test_order_torus_parity(bs):
+    """Config-1 ordering: full exact greedy permutation of the torus surfels, start from seed 0."""
+    m = W.torus()
+    ref, mn, s = oracle.sample_mesh(m, W.AXIS_DIRS, 128)
+    _check_order(bs, ref["key"], seed=0, scale=s)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 32, 33, 1023, 1024, 1025, 2047, 5000, 33 * 1024 + 17])
+def test_order_ragged_sizes(bs, n):
+    g = np.random.default_rng(n)
+    pts = np.unique(g.integers(0, 1 << 21, size=(n + n // 10 + 5, 3)), axis=0)[:n]
+    order = np.argsort([oracle.morton3(*map(int, p)) for p in pts], kind="stable")
+    key = oracle.pack(pts[order])
+    _check_order(bs, key, seed=7, part_id=3, scale=123.5)
+
+
+def test_order_unsorted_and_duplicate_keys(bs):
+    """Any key array is accepted: random order, repeated positions (rad2 = 0 tail)."""
+    g = np.random.default_rng(1)
+    pts = g.integers(0, 200, size=(3000, 3))
+    pts[100:400] = pts[0:300]  # duplicates
+    key = oracle.pack(pts)
+    rp, rr = _check_order(bs, key, start=17)
+    ndup = len(pts) - len(np.unique(pts, axis=0))
+    assert ndup >= 100 and (rr[-ndup:] == 0).all() and (rr[1:-ndup] > 0).all()
+
+
+def test_order_regular_grid_ties(bs):
+    """A 2-D grid has many equal distances: ties must go to the lowest index."""
+    n1 = 65
+    X, Y = np.meshgrid(np.arange(n1), np.arange(n1), indexing="ij")
+    pts = np.stack([X.ravel() * 1000, Y.ravel() * 1000, np.full(n1 * n1, 5000)], -1)
+    order = np.argsort([oracle.morton3(*map(int, p)) for p in pts], kind="stable")
+    _check_order(bs, oracle.pack(pts[order]), start=0)
+
+
+def test_order_line_closed_form(bs):
+    m = 12
+    n = 2**m + 1
+    p = np.zeros((n, 3), np.int64)
+    p[:, 1] = np.arange(n) * 3
+    rp, rr = _check_order(bs, oracle.pack(p), start=0)
+    assert rp[1] == n - 1 and rr[1] == ((n - 1) * 3) ** 2
+
+
+@pytest.mark.parametrize("max_count", [1, 2, 100, 4999])
+def test_order_truncated(bs, max_count):
+    g = np.random.default_rng(9)
+    pts = np.unique(g.integers(0, 1 << 21, size=(5000, 3)), axis=0)
+    _check_order(bs, oracle.pack(pts), seed=3, max_count=max_count)
+
+
+def test_order_batched_matches_single_and_oracle(bs):
+    g = np.random.default_rng(2)
+    sizes = [1, 5, 32, 1000, 3000, 1025, 20000, 7]
+    keys_np = []
+    for n in sizes:
+        pts = np.unique(g.integers(0, 1 << 18, size=(n + 10, 3)), axis=0)[:n]
+        keys_np.append(oracle.pack(pts))
+    keys = [_dev(k.view(np.int64)) for k in keys_np]
+    seeds = list(range(len(keys)))
+    res = bs.order_batched(keys, seeds=seeds, part_ids=[11 * i for i in range(len(keys))],
+                           max_counts=[0, 0, 0, 500, 0, 0, 0, 3], scales=[2.0] * len(keys))
+    for i, (perm, rad2, radius) in enumerate(res):
+        s = oracle.start_index(sizes[i], seed=seeds[i], part_id=11 * i)
+        rp, rr = oracle.greedy(keys_np[i], s, max_count=[0, 0, 0, 500, 0, 0, 0, 3][i])
+        assert np.array_equal(_np(perm, np.uint32), rp), i
+        assert np.array_equal(_np(rad2), rr), i
+        assert np.array_equal(_np(radius).view(np.uint32), oracle.radius(rr, 2.0).view(np.uint32)), i
+        p1, r1, _ = bs.order(keys[i], seed=seeds[i], part_id=11 * i, max_count=[0, 0, 0, 500, 0, 0, 0, 3][i])
+        assert torch.equal(p1, perm) and torch.equal(r1, rad2)
+
+
+@pytest.mark.parametrize("threads", [64, 128, 256, 512, 1024])
+def test_order_launch_shape_independent(bs, threads):
+    g = np.random.default_rng(4)
+    pts = np.unique(g.integers(0, 1 << 21, size=(40000, 3)), axis=0)
+    order = np.argsort([oracle.morton3(*map(int, p)) for p in pts[:, :]], kind="stable")
+    key = _dev(oracle.pack(pts[order]).view(np.int64))
+    base = bs.order(key, start=5)
+    try:
+        bs.set_tuning("order_threads", threads)
+        got = bs.order(key, start=5)
+        gotb = bs.order_batched([key, key[:1000]], starts=[5, 0])
+    finally:
+        bs.set_tuning("order_threads", 0)
+    assert torch.equal(base[0], got[0]) and torch.equal(base[1], got[1])
+    assert torch.equal(base[0], gotb[0][0]) and torch.equal(base[1], gotb[0][1])
+
+
+def test_cad_part_full_size(bs):
+    """The CAD-like part (2000 boxes + 500 cylinders, ~192k tris) from 6 axis + 2 diagonal
+    directions at 1024^2: surfel arrays identical to the oracle; the ordering's first
+    2000 entries identical to the oracle's truncated ordering, and r-net invariants on
+    sampled prefixes of the full ordering."""
+    m = W.cad_part(seed=0)
+    D = np.concatenate([W.AXIS_DIRS, W.DIAG_DIRS])
+    ref, mn, s = oracle.sample_mesh(m, D, 1024)
+    g = _gpu_sample(bs, m, D, 1024)
+    _check_sample(g, ref, mn, s)
+    n = g["n"]
+    assert 1_000_000 <= n <= 6_291_456  # 5.42M for seed 0 (the 1-3M estimate undercounts this union)
+    perm, rad2, radius = bs.order(g["key"], seed=0, scale=g["scale"])
+    P = _np(perm, np.uint32)
+    R = _np(rad2)
+    st = oracle.start_index(n, seed=0)
+    rp, rr = oracle.greedy(ref["key"], st, max_count=2000, nthreads=oracle.num_threads())
+    assert np.array_equal(P[:2000], rp) and np.array_equal(R[:2000], rr)
+    assert np.array_equal(np.sort(P), np.arange(n, dtype=np.uint32))
+    assert (np.diff(R[1:]) <= 0).all()
+    pts = oracle.unpack(ref["key"]).astype(np.int64)
+    _sampled_rnet(pts, P, R, [2, 10, 1000, n // 3, n - 5])
+
+
+def _sampled_rnet(pts, P, R, ks):
+    """Separation of prefix k: the new point's distance to the earlier prefix equals
+    rad2[k-1] for sampled k, and no prefix point pair is closer (checked for the last
+    200 entries of the prefix); covering: a random sample of points lies within rad2[k]."""
+    g = np.random.default_rng(0)
+    n = len(pts)
+    for k in ks:
+        pre = pts[P[:k]]
+        j = pts[P[k - 1]]
+        if k >= 2:
+            d = ((pre[:-1] - j) ** 2).sum(1)
+            assert d.min() == R[k - 1]
+            for t in range(max(1, k - 200), k):
+                d2 = ((pre[:t] - pts[P[t]]) ** 2).sum(1)
+                assert d2.min() >= R[k - 1]
+        if k < n:
+            samp = pts[g.integers(0, n, 200)]
+            for x in samp:
+                assert ((pre - x) ** 2).sum(1).min() <= R[k]
+
+
+def test_server_alone_equals_mix(bs):
+    """Each request's result is the same submitted alone and inside a concurrent mix."""
+    g = np.random.default_rng(3)
+    keys = []
+    for n in [50, 3000, 1, 12000, 700, 33000, 2048]:
+        pts = np.unique(g.integers(0, 1 << 20, size=(n + 5, 3)), axis=0)[:n]
+        keys.append(oracle.pack(pts))
+    with bs.Server(budget_bytes=1 << 30) as srv:
+        alone = []
+        for i, k in enumerate(keys):
+            t = srv.submit(k, scale=3.0, seed=i, part_id=i)
+            r = None
+            while r is None:
+                r = srv.poll(t)
+                time.sleep(0.0002)
+            alone.append(r)
+        order = g.permutation(len(keys))
+        tickets = {int(i): srv.submit(keys[i], scale=3.0, seed=int(i), part_id=int(i)) for i in order}
+        mix = {}
+        while len(mix) < len(keys):
+            for i, t in tickets.items():
+                if i not in mix:
+                    r = srv.poll(t)
+                    if r is not None:
+                        mix[i] = r
+            time.sleep(0.0002)
+    for i, k in enumerate(keys):
+        s = oracle.start_index(len(k), seed=i, part_id=i)
+        rp, rr = oracle.greedy(k, s)
+        for r in (alone[i], mix[i]):
+            assert np.array_equal(r[0], rp) and np.array_equal(r[1], rr)
+            assert np.array_equal(r[2].view(np.uint32), oracle.radius(rr, 3.0).view(np.uint32))
+
+
+def test_server_budget_admission(bs):
+    """A budget that fits one large request at a time still completes every request."""
+    g = np.random.default_rng(8)
+    keys = [oracle.pack(np.unique(g.integers(0, 1 << 20, size=(20000, 3)), axis=0)[:20000]) for _ in range(4)]
+    with bs.Server(budget_bytes=1_000_000) as srv:
+        ts = [srv.submit(k, seed=i) for i, k in enumerate(keys)]
+        out = {}
+        while len(out) < len(ts):
+            for i, t in enumerate(ts):
+                if i not in out:
+                    r = srv.poll(t)
+                    if r is not None:
+                        out[i] = r
+            time.sleep(0.0002)
+        with pytest.raises(bs.BsError) as e:
+            srv.submit(np.zeros(10**6, np.uint64))
+        assert e.value.status == bs.BS_ENOMEM
+    for i, k in enumerate(keys):
+        rp, rr = oracle.greedy(k, oracle.start_index(len(k), seed=i))
+        assert np.array_equal(out[i][0], rp)
