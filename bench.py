@@ -1,0 +1,505 @@
+#!/usr/bin/env python3
+"""Benchmark: surfels sampled and progressively ordered per second on one GB300.
+
+Workload (the batched-ordering configuration): 4096 seeded tori with lognormal
+triangle counts (2k-50k) and lognormal target surfel counts (median 20k, 1k-500k,
+about 100M surfels in total), each sampled from the 6 axis directions at a
+per-part resolution and then ordered exactly.  One step = bs_sample_visible for
+every part followed by one bs_order_batched over all parts (every row of the hot
+path: quantise, raster, resolve, dedup, ordering, radius).
+
+Printed JSON line (rank 0):
+  value      surfels/s of the device-resident step (inputs already in HBM)
+  e2e        the same with the meshes copied from pinned host memory and the
+             ordered surfels read back inside the timed region
+  order_only batched vs plain (one bs_order launch per part) ordering throughput
+  served     p50/p99/p999 latency of a short Poisson request trace through bs_server
+  roofline   the ordering loop kernel's algorithmic bytes / its event-timed duration
+  cpu_baseline  the CPU oracle on a bounded sample of the same workload
+With --impl reference the CPU oracle is the timed arm (same metric and config).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1904_08225_gb300 import workloads as W  # noqa: E402
+
+METRIC = "surfels ordered/s (sample + exact greedy order, batched)"
+UNIT = "surfels/s"
+
+# Algorithmic work of the exact ordering, per part of N surfels (the update sweep
+# must examine every unchosen point inside the new point's ball): visits/N and
+# improved/N fitted as a + b*ln(N) over seeded torus parts of the batch generator
+# by oracle/fit_visits.py (exact counts from the O(N^2) oracle).
+VISITS_FIT = (-4.25, 2.06)
+IMPROVED_FIT = (-1.06, 0.74)
+BYTES_PER_VISIT = 16   # 8 B key + 8 B D read
+BYTES_PER_IMPROVE = 8  # 8 B D write
+BYTES_OUT = 16         # perm 4 + rad2 8 + radius 4
+
+
+def algorithmic_bytes(n: int) -> float:
+    """Bytes the ordering of an N-surfel part must move (init sweep + update sweeps + outputs)."""
+    if n <= 1:
+        return float(BYTES_OUT * n + BYTES_PER_VISIT * n)
+    ln = math.log(n)
+    visits = max(0.0, VISITS_FIT[0] + VISITS_FIT[1] * ln) * n
+    improved = max(0.0, IMPROVED_FIT[0] + IMPROVED_FIT[1] * ln) * n
+    return BYTES_PER_VISIT * (visits + n) + BYTES_PER_IMPROVE * improved + BYTES_OUT * n
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------
+# reference arm / CPU baseline: the oracle as it stands, on a bounded sample
+# ---------------------------------------------------------------------------
+def oracle_sample_parts(specs, budget_s: float, seed: int):
+    """A seeded sample of parts whose estimated oracle time (O(N^2) greedy, about
+    9 ns per point pair per core) fits budget_s seconds; parts too big alone are skipped."""
+    g = np.random.default_rng(seed)
+    cores = max(1, os.cpu_count() or 1)
+
+    def cost(n):
+        return 9e-9 * n * n / cores + 0.05
+
+    picked, est = [], 0.0
+    for i in g.permutation(len(specs)):
+        c = cost(specs[i].n_target)
+        if est + c > budget_s:
+            continue
+        picked.append(int(i))
+        est += c
+    if not picked:
+        picked = [int(np.argmin([sp.n_target for sp in specs]))]
+    return picked
+
+
+def run_oracle_parts(specs, idx, nthreads):
+    import oracle
+    tot = 0
+    t0 = time.perf_counter()
+    for i in idx:
+        sp = specs[i]
+        m = sp.mesh()
+        sv, mn, s = oracle.sample_mesh(m, W.AXIS_DIRS, sp.res)
+        k = sv["key"]
+        st = oracle.start_index(len(k), seed=0, part_id=i)
+        oracle.greedy(k, st, nthreads=nthreads)
+        tot += len(k)
+    return tot, time.perf_counter() - t0
+
+
+def reference_arm(args, specs, world, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    nthreads = oracle.num_threads()
+    idx = oracle_sample_parts(specs, args.cpu_budget_s, seed=args.seed)
+    for _ in range(args.warmup):
+        run_oracle_parts(specs, idx[:1], nthreads)
+    tot, dt = 0, 0.0
+    for _ in range(args.steps):
+        n, t = run_oracle_parts(specs, idx, nthreads)
+        tot += n
+        dt += t
+    v = tot / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": config_dict(args, specs),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                         "sample": f"{len(idx)} of {len(specs)} parts (seeded), {tot // args.steps} surfels per step; "
+                                   f"oracle sample_visible + O(N^2) greedy, OpenMP"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(args, specs):
+    return {"workload": f"batched ordering: {len(specs)} tori, lognormal tris 2k-50k, lognormal surfels "
+                        f"(median 20k, 1k-500k), 6 axis views at 16^2-1024^2, exact greedy order",
+            "parts": len(specs), "seed": args.seed, "dirs": 6,
+            "l2": "inputs larger than L2 (meshes + keys ~ GBs, no flush needed)"}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--parts", type=int, default=4096)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--plain-parts", type=int, default=64, help="parts timed one launch each for the plain path")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--cpu-budget-s", type=float, default=12.0)
+    ap.add_argument("--no-extras", action="store_true", help="skip plain / served / cpu baseline legs")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    specs = W.batch_parts(args.parts, seed=args.seed + 7919 * rank)
+    if args.impl == "reference":
+        return reference_arm(args, specs, world, rank)
+
+    import torch
+    from paper_1904_08225_gb300 import bs
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    lib = bs.load()
+    stream = torch.cuda.current_stream()
+    dev = torch.device("cuda", local)
+
+    # ---- inputs: all meshes packed in one buffer (host pinned + device copy) ----
+    meshes = [sp.mesh() for sp in specs]
+    vofs = np.cumsum([0] + [m.nverts for m in meshes])
+    tofs = np.cumsum([0] + [m.ntris for m in meshes])
+    xyz_h = torch.from_numpy(np.concatenate([m.xyz for m in meshes])).pin_memory()
+    tri_h = torch.from_numpy(np.concatenate([m.tri for m in meshes]).view(np.int32)).pin_memory()
+    rgb_h = torch.from_numpy(np.concatenate([m.rgb for m in meshes])).pin_memory()
+    xyz_d, tri_d, rgb_d = xyz_h.to(dev), tri_h.to(dev), rgb_h.to(dev)
+    h2d_bytes = xyz_h.numel() * 4 + tri_h.numel() * 4 + rgb_h.numel()
+    dirs = (bs.Dir * 6)(*[bs.Dir(int(a), int(b), int(c)) for a, b, c in W.AXIS_DIRS])
+
+    # first pass learns each part's surfel count (deterministic) to size the outputs
+    caps = [6 * sp.res * sp.res for sp in specs]
+    coff = np.cumsum([0] + caps)
+    key_all = torch.empty(int(coff[-1]), dtype=torch.int64, device=dev)
+    nrm_all = torch.empty((int(coff[-1]), 3), dtype=torch.int16, device=dev)
+    rgb_all = torch.empty((int(coff[-1]), 3), dtype=torch.uint8, device=dev)
+    src_all = torch.empty(int(coff[-1]), dtype=torch.int32, device=dev)
+    import ctypes as C
+    cs = C.c_void_p(stream.cuda_stream)
+    mesh_structs, out_structs = [], []
+    for i, sp in enumerate(specs):
+        mesh_structs.append(bs.Mesh(xyz_d.data_ptr() + int(vofs[i]) * 12, meshes[i].nverts,
+                                    tri_d.data_ptr() + int(tofs[i]) * 12, meshes[i].ntris,
+                                    rgb_d.data_ptr() + int(tofs[i]) * 3))
+        o = int(coff[i])
+        out_structs.append(bs.Surfels(key_all.data_ptr() + 8 * o, nrm_all.data_ptr() + 6 * o,
+                                      rgb_all.data_ptr() + 3 * o, src_all.data_ptr() + 4 * o, 0, caps[i],
+                                      (C.c_float * 3)(), 0.0))
+
+    def sample_all():
+        for i, sp in enumerate(specs):
+            st = lib.bs_sample_visible(C.byref(mesh_structs[i]), dirs, 6, sp.res, C.byref(out_structs[i]), cs)
+            if st != bs.BS_OK:
+                raise bs.BsError(st, "bs_sample_visible", bs.last_error())
+
+    sample_all()
+    ns = np.array([o.n for o in out_structs], np.int64)
+    total = int(ns.sum())
+    pofs = np.cumsum([0] + list(ns))
+    perm_all = torch.empty(total, dtype=torch.int32, device=dev)
+    rad2_all = torch.empty(total, dtype=torch.int64, device=dev)
+    radius_all = torch.empty(total, dtype=torch.float32, device=dev)
+    P = len(specs)
+    parts = (bs.Surfels * P)()
+    opts = (bs.OrderOpts * P)()
+    pp, rp, fp = (C.c_void_p * P)(), (C.c_void_p * P)(), (C.c_void_p * P)()
+    for i in range(P):
+        o = out_structs[i]
+        parts[i] = bs.Surfels(o.key, None, None, None, o.n, o.n, (C.c_float * 3)(), o.scale)
+        opts[i] = bs.OrderOpts(0, i, -1, 0)
+        pp[i] = perm_all.data_ptr() + 4 * int(pofs[i])
+        rp[i] = rad2_all.data_ptr() + 8 * int(pofs[i])
+        fp[i] = radius_all.data_ptr() + 4 * int(pofs[i])
+
+    def order_all():
+        st = lib.bs_order_batched(parts, P, opts, C.cast(pp, C.c_void_p), C.cast(rp, C.c_void_p),
+                                  C.cast(fp, C.c_void_p), cs)
+        if st != bs.BS_OK:
+            raise bs.BsError(st, "bs_order_batched", bs.last_error())
+
+    def step():
+        sample_all()
+        order_all()
+
+    # e2e: host meshes in, ordered surfels out (perm, rad2, radius, key, nrm, rgb)
+    res_h = {
+        "perm": torch.empty(total, dtype=torch.int32).pin_memory(),
+        "rad2": torch.empty(total, dtype=torch.int64).pin_memory(),
+        "radius": torch.empty(total, dtype=torch.float32).pin_memory(),
+        "key": torch.empty(int(coff[-1]), dtype=torch.int64).pin_memory(),
+        "nrm": torch.empty((int(coff[-1]), 3), dtype=torch.int16).pin_memory(),
+        "rgb": torch.empty((int(coff[-1]), 3), dtype=torch.uint8).pin_memory(),
+    }
+    d2h_bytes = total * (4 + 8 + 4) + total * (8 + 6 + 3)
+
+    def step_e2e():
+        xyz_d.copy_(xyz_h, non_blocking=True)
+        tri_d.copy_(tri_h, non_blocking=True)
+        rgb_d.copy_(rgb_h, non_blocking=True)
+        step()
+        res_h["perm"].copy_(perm_all, non_blocking=True)
+        res_h["rad2"].copy_(rad2_all, non_blocking=True)
+        res_h["radius"].copy_(radius_all, non_blocking=True)
+        # surfel records of each part (contiguous per part in the capacity layout)
+        for i in range(P):
+            o, n = int(coff[i]), int(ns[i])
+            res_h["key"][o:o + n].copy_(key_all[o:o + n], non_blocking=True)
+            res_h["nrm"][o:o + n].copy_(nrm_all[o:o + n], non_blocking=True)
+            res_h["rgb"][o:o + n].copy_(rgb_all[o:o + n], non_blocking=True)
+        stream.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(fn, steps):
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    for _ in range(args.warmup):
+        step()
+    bs.set_tuning("kernel_timing", 1)
+    clocks = Clocks(local)
+    clocks.start()
+    # dominant kernel (ordering loop) timed per launch with events on its own stream
+    loop_ms = []
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+        loop_ms.append(bs.last_launch_ms("order_loop"))
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clk = clocks.stop()
+    bs.set_tuning("kernel_timing", 0)
+    ms_step = ms / args.steps
+    value = world * total / (ms_step / 1e3)
+
+    # e2e through the public API with host buffers
+    step_e2e()
+    ms_e2e = timed(step_e2e, args.steps) / args.steps
+    e2e_value = world * total / (ms_e2e / 1e3)
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        # ordering only: batched (one launch) vs plain (one launch per part) on a seeded subset
+        ms_b = timed(order_all, 2) / 2
+        g = np.random.default_rng(args.seed)
+        sub = np.sort(g.choice(P, size=min(args.plain_parts, P), replace=False))
+        sub_n = int(ns[sub].sum())
+
+        def plain():
+            for i in sub:
+                st = lib.bs_order(C.byref(parts[i]), C.byref(opts[i]), C.c_void_p(pp[i]), C.c_void_p(rp[i]),
+                                  C.c_void_p(fp[i]), cs)
+                if st != bs.BS_OK:
+                    raise bs.BsError(st, "bs_order", bs.last_error())
+        plain()
+        ms_p = timed(plain, 1)
+        sub_parts = (bs.Surfels * len(sub))(*[parts[i] for i in sub])
+        sub_opts = (bs.OrderOpts * len(sub))(*[opts[i] for i in sub])
+        spp = (C.c_void_p * len(sub))(*[pp[i] for i in sub])
+        srp = (C.c_void_p * len(sub))(*[rp[i] for i in sub])
+        sfp = (C.c_void_p * len(sub))(*[fp[i] for i in sub])
+
+        def batched_sub():
+            lib.bs_order_batched(sub_parts, len(sub), sub_opts, C.cast(spp, C.c_void_p), C.cast(srp, C.c_void_p),
+                                 C.cast(sfp, C.c_void_p), cs)
+        batched_sub()
+        ms_bs = timed(batched_sub, 1)
+        extras["order_only"] = {
+            "batched_all_parts": total / (ms_b / 1e3),
+            "batched_subset": sub_n / (ms_bs / 1e3),
+            "plain_subset": sub_n / (ms_p / 1e3),
+            "batched_over_plain": (sub_n / (ms_bs / 1e3)) / (sub_n / (ms_p / 1e3)),
+            "subset": f"{len(sub)} seeded parts, {sub_n} surfels, one bs_order launch each on one stream",
+            "unit": UNIT,
+        }
+        extras["served"] = serve_leg(bs, key_all, coff, ns, out_structs, args)
+        extras["cpu_baseline"] = cpu_baseline(specs, args)
+
+    if rank == 0:
+        peak, peak_src = measured_peaks()
+        bytes_launch = float(sum(algorithmic_bytes(int(n)) for n in ns))
+        loop_avg = float(np.mean(loop_ms))
+        achieved = bytes_launch / (loop_avg / 1e3) / 1e9
+        nsample_kernels = 35
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": config_dict(args, specs) | {"surfels_per_gpu": total},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d_bytes),
+                    "d2h_bytes_per_step": int(d2h_bytes)},
+            "gpu_launches": args.steps * (nsample_kernels * P + 3),
+            "roofline": {"bound": "hbm", "kernel": "k_order_loop", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured" else "fallback 6800 GB/s",
+                         "algorithmic_bytes_per_launch": bytes_launch, "loop_ms_per_launch": loop_avg},
+            "clocks": clk,
+        }
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def serve_leg(bs, key_all, coff, ns, out_structs, args):
+    """Poisson arrivals of ordering requests (surfel arrays of the sampled parts, each
+    with its own seed) through bs_server; latency = device completion - submit."""
+    g = np.random.default_rng(args.seed + 1)
+    nreq = args.serve_requests
+    pool = np.where((ns >= 1000) & (ns <= 1_000_000))[0]
+    pick = g.choice(pool, size=nreq)
+    keys = {int(i): key_all[int(coff[i]):int(coff[i]) + int(ns[i])].cpu().numpy().view(np.uint64) for i in np.unique(pick)}
+    gaps = g.exponential(1.0 / args.serve_rate, nreq)
+    arr = np.cumsum(gaps)
+    srv = bs.Server(budget_bytes=64 << 30)
+    tickets = []
+    t0 = time.perf_counter()
+    for r in range(nreq):
+        now = time.perf_counter() - t0
+        if arr[r] > now:
+            time.sleep(arr[r] - now)
+        i = int(pick[r])
+        tickets.append((srv.submit(keys[i], scale=out_structs[i].scale, seed=r, part_id=i), int(ns[i])))
+    lat, done = [], 0
+    t_first, t_last = None, 0.0
+    pending = list(tickets)
+    while pending:
+        rest = []
+        for t, n in pending:
+            r = srv.poll(t)
+            if r is None:
+                rest.append((t, n))
+                continue
+            ts = srv.times(t)
+            lat.append((ts[2] - ts[0]) * 1e3)
+            t_first = ts[0] if t_first is None else min(t_first, ts[0])
+            t_last = max(t_last, ts[2])
+            done += n
+        pending = rest
+        if pending:
+            time.sleep(0.0005)
+    srv.close()
+    lat = np.array(lat)
+    return {"requests": nreq, "offered_rate_hz": args.serve_rate, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "p999_ms": float(np.percentile(lat, 99.9)),
+            "sustained_surfels_per_s": done / max(1e-9, t_last - t_first),
+            "requests_from": "surfel arrays of the batch parts with 1k-1M surfels, seeded choice and start"}
+
+
+def cpu_baseline(specs, args):
+    import oracle
+    oracle.build()
+    nthreads = oracle.num_threads()
+    idx = oracle_sample_parts(specs, args.cpu_budget_s, seed=args.seed)
+    tot, dt = run_oracle_parts(specs, idx, nthreads)
+    return {"value": tot / dt, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "sample": f"{len(idx)} of {len(specs)} parts (seeded), {tot} surfels, {dt:.1f} s; oracle "
+                      f"sample_visible + O(N^2) greedy"}
+
+
+if __name__ == "__main__":
+    sys.exit(main())
