@@ -144,6 +144,28 @@ bs_status bs_order_batched(const bs_surfels *parts, int nparts, const bs_order_o
                            uint32_t *const *perm, int64_t *const *rad2, float *const *radius,
                            void *cuda_stream);
 
+/* bs_order_noalloc -- bs_order for callers that may not allocate device memory.
+ * The paper has no counterpart: this entry point exists for library users.  A
+ * plugin or render thread running inside a host application that owns the GPU
+ * memory budget, or a real-time loop that cannot afford an allocation that may
+ * block or fail, cannot let the library call cudaMalloc or grow a memory pool.
+ * This call computes exactly what bs_order computes (same arguments, same
+ * bit-identical outputs) but takes all of its scratch from one fixed array of
+ * about 1.1 MB that the library reserves in device memory on every GPU where it
+ * is loaded, held until the process exits.  It calls no allocating routine.
+ *  - Parts of at most BS_NOALLOC_MAX_POINTS points; larger ones return
+ *    BS_EOVERFLOW with a message and nothing is launched.
+ *  - The first call on a device looks up the array's device address (once per
+ *    device, with that device current); make that first call before any stream
+ *    capture.
+ *  - Every call shares the one array: calls whose work can overlap on the GPU
+ *    (different streams, or different host threads, without ordering between
+ *    them) race on it and give wrong results.  Serialise them on one stream.
+ * Stream-ordered like bs_order. */
+#define BS_NOALLOC_MAX_POINTS 65536u
+bs_status bs_order_noalloc(const bs_surfels *s, const bs_order_opts *opts, uint32_t *perm, int64_t *rad2,
+                           float *radius, void *cuda_stream);
+
 /* ---- Serving: continuous batching of ordering requests (Sec. 3.4 at scale). ---- */
 typedef struct bs_server bs_server;
 

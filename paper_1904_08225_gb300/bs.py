@@ -22,7 +22,7 @@ STATUS_NAMES = ["BS_OK", "BS_EINVAL", "BS_ENOMEM", "BS_EOVERFLOW", "BS_ETIMEOUT"
 INT64_MAX = (1 << 63) - 1
 
 # symbols include/bs.h declares; the library must export every one
-EXPORTS = ["bs_sample_visible", "bs_order", "bs_order_batched", "bs_server_create", "bs_server_submit",
+EXPORTS = ["bs_sample_visible", "bs_order", "bs_order_noalloc", "bs_order_batched", "bs_server_create", "bs_server_submit",
            "bs_server_poll", "bs_server_times", "bs_server_destroy", "bs_set_tuning", "bs_last_launch_ms",
            "bs_last_error"]
 
@@ -71,6 +71,7 @@ def load(build_if_stale: bool = True) -> C.CDLL:
             P = C.c_void_p
             lib.bs_sample_visible.argtypes = [C.POINTER(Mesh), C.POINTER(Dir), C.c_int, C.c_int, C.POINTER(Surfels), P]
             lib.bs_order.argtypes = [C.POINTER(Surfels), C.POINTER(OrderOpts), P, P, P, P]
+            lib.bs_order_noalloc.argtypes = [C.POINTER(Surfels), C.POINTER(OrderOpts), P, P, P, P]
             lib.bs_order_batched.argtypes = [C.POINTER(Surfels), C.c_int, C.POINTER(OrderOpts), P, P, P, P]
             lib.bs_server_create.argtypes = [C.c_uint64, C.c_int, C.POINTER(C.c_int)]
             lib.bs_server_create.restype = P
@@ -180,6 +181,27 @@ def order(key, start: int = -1, seed: int = 0, part_id: int = 0, max_count: int 
     o = _opts(seed, part_id, start, max_count)
     st = lib.bs_order(C.byref(s), C.byref(o), _ptr(perm), _ptr(rad2), _ptr(radius), _stream(stream))
     _check(st, "bs_order")
+    return perm, rad2, radius
+
+
+def order_noalloc(key, start: int = -1, seed: int = 0, part_id: int = 0, max_count: int = 0, scale: float = 1.0,
+                  stream=None, want_radius: bool = True, out=None):
+    """bs_order_noalloc: same result as order(), with the library's fixed scratch instead of
+    allocations (parts of at most 65536 points; calls that overlap on the GPU race)."""
+    torch = _torch()
+    lib = load()
+    n = key.shape[0]
+    m = n if max_count == 0 or max_count > n else max_count
+    if out is None:
+        perm = torch.empty(m, dtype=torch.int32, device=key.device)
+        rad2 = torch.empty(m, dtype=torch.int64, device=key.device)
+        radius = torch.empty(m, dtype=torch.float32, device=key.device) if want_radius else None
+    else:
+        perm, rad2, radius = out
+    s = Surfels(key.data_ptr(), None, None, None, n, n, (C.c_float * 3)(), float(scale))
+    o = _opts(seed, part_id, start, max_count)
+    st = lib.bs_order_noalloc(C.byref(s), C.byref(o), _ptr(perm), _ptr(rad2), _ptr(radius), _stream(stream))
+    _check(st, "bs_order_noalloc")
     return perm, rad2, radius
 
 

@@ -119,6 +119,15 @@ bs_status bs_order(const bs_surfels *s, const bs_order_opts *opts, uint32_t *per
     return order_parts(parts, (cudaStream_t)cuda_stream, false);
 }
 
+bs_status bs_order_noalloc(const bs_surfels *s, const bs_order_opts *opts, uint32_t *perm, int64_t *rad2,
+                           float *radius, void *cuda_stream) {
+    clear_error();
+    PartDesc p;
+    bs_status st = make_part(s, opts, perm, rad2, radius, p);
+    if (st != BS_OK) return st;
+    return order_part_noalloc(p, (cudaStream_t)cuda_stream);
+}
+
 bs_status bs_order_batched(const bs_surfels *parts, int nparts, const bs_order_opts *opts, uint32_t *const *perm,
                            int64_t *const *rad2, float *const *radius, void *cuda_stream) {
     clear_error();

@@ -130,6 +130,7 @@ struct PartDesc {
 namespace bs {
 
 bs_status order_parts(std::vector<PartDesc> &parts, cudaStream_t stream, bool batched);
+bs_status order_part_noalloc(PartDesc part, cudaStream_t stream);
 void order_set_tuning(int threads, int ctas_per_sm);
 void order_set_kernel_timing(bool on);
 bs_status order_last_launch_ms(int which, double *ms);

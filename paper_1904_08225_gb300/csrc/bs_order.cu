@@ -26,6 +26,7 @@
 //                 touched group updating its touched buckets.     (the update sweep)
 //   k_radius      radius[k] = sqrt(rad2[k]) / scale in IEEE double, as float.
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "bs_internal.cuh"
@@ -392,6 +393,101 @@ bs_status order_parts(std::vector<PartDesc> &hp, cudaStream_t stream, bool batch
     } while (0);
     cudaFreeAsync(ws, stream);
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the single-part ordering.
+//
+// Some callers cannot allocate device memory while they run: a plugin or render
+// thread inside a host application that owns the GPU memory budget, or a
+// real-time loop where cudaMalloc / a stream-ordered pool growth may block or fail.
+// bs_order_noalloc serves them: the caller passes keys and outputs as usual and all
+// ordering scratch (distance array, bucket and group records, descriptor, part
+// counter, and rad2 when the caller passes none) lives in the fixed device array
+// below, which every GPU that loads the library holds until process exit.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr uint32_t NOALLOC_MAX_POINTS = BS_NOALLOC_MAX_POINTS;
+constexpr uint32_t NOALLOC_MAX_BUCKETS = NOALLOC_MAX_POINTS / 32;
+constexpr uint32_t NOALLOC_MAX_GROUPS = (NOALLOC_MAX_BUCKETS + 31) / 32;
+constexpr size_t NA_DESC = 0;                                               // PartDesc
+constexpr size_t NA_NEXT = 256;                                             // part counter
+constexpr size_t NA_D = 512;                                                // int64 D[n]
+constexpr size_t NA_RAD2 = NA_D + 8ull * NOALLOC_MAX_POINTS;                // int64 rad2[m]
+constexpr size_t NA_BUCKETS = NA_RAD2 + 8ull * NOALLOC_MAX_POINTS;          // 4 x u64 [nb]
+constexpr size_t NA_GROUPS = NA_BUCKETS + 4 * 8ull * NOALLOC_MAX_BUCKETS;   // 4 x u64 [ng]
+constexpr size_t NA_BYTES = NA_GROUPS + 4 * 8ull * NOALLOC_MAX_GROUPS;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+std::mutex g_noalloc_mu;
+char *g_noalloc_addr[64] = {nullptr};
+
+// Device address of the scratch array on the current device, looked up once per device.
+bs_status noalloc_scratch(char **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) { set_error("bs_order_noalloc: cudaGetDevice: %s", cudaGetErrorString(e)); return BS_ECUDA; }
+    if (dev < 0 || dev >= 64) { set_error("bs_order_noalloc: device %d out of range", dev); return BS_EINVAL; }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error("bs_order_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+            return BS_ECUDA;
+        }
+        g_noalloc_addr[dev] = (char *)p;
+    }
+    *out = g_noalloc_addr[dev];
+    return BS_OK;
+}
+
+}  // namespace
+
+bs_status order_part_noalloc(PartDesc p, cudaStream_t stream) {
+    if (p.n > NOALLOC_MAX_POINTS) {
+        set_error("bs_order_noalloc: n=%u exceeds the fixed scratch limit of %u points", p.n, NOALLOC_MAX_POINTS);
+        return BS_EOVERFLOW;
+    }
+    char *base = nullptr;
+    bs_status st = noalloc_scratch(&base);
+    if (st != BS_OK) return st;
+    p.nb = (p.n + 31) / 32;
+    p.ng = (p.nb + 31) / 32;
+    p.D = (int64_t *)(base + NA_D);
+    if (!p.rad2) p.rad2 = (int64_t *)(base + NA_RAD2);
+    uint64_t *bk = (uint64_t *)(base + NA_BUCKETS);
+    p.bkey = bk;
+    p.bq = bk + NOALLOC_MAX_BUCKETS;
+    p.blo = bk + 2 * NOALLOC_MAX_BUCKETS;
+    p.bhi = bk + 3 * NOALLOC_MAX_BUCKETS;
+    uint64_t *gk = (uint64_t *)(base + NA_GROUPS);
+    p.gkey = gk;
+    p.gq = gk + NOALLOC_MAX_GROUPS;
+    p.glo = gk + 2 * NOALLOC_MAX_GROUPS;
+    p.ghi = gk + 3 * NOALLOC_MAX_GROUPS;
+    PartDesc *d_desc = (PartDesc *)(base + NA_DESC);
+    uint32_t *d_next = (uint32_t *)(base + NA_NEXT);
+    cudaError_t e = cudaMemcpyAsync(d_desc, &p, sizeof(PartDesc), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_next, 0, 8, stream);  // d_next[0] counter, d_next[1] = gofs[0] = 0
+    if (e != cudaSuccess) { set_error("bs_order_noalloc: descriptor upload failed: %s", cudaGetErrorString(e)); return BS_ECUDA; }
+    k_order_init<<<(p.ng + 7) / 8, 256, 0, stream>>>(d_desc, d_next + 1, 1, p.ng);
+    const int T = pick_threads((int)p.ng, false);
+    switch (T) {
+        case 64: e = launch_loop<64>(d_desc, 1, d_next, (int)p.ng, 1, stream); break;
+        case 128: e = launch_loop<128>(d_desc, 1, d_next, (int)p.ng, 1, stream); break;
+        case 256: e = launch_loop<256>(d_desc, 1, d_next, (int)p.ng, 1, stream); break;
+        case 512: e = launch_loop<512>(d_desc, 1, d_next, (int)p.ng, 1, stream); break;
+        default: e = launch_loop<1024>(d_desc, 1, d_next, (int)p.ng, 1, stream); break;
+    }
+    if (e == cudaSuccess && p.radius) {
+        k_radius<<<dim3(std::min<uint32_t>((p.m + 255) / 256, 64), 1), 256, 0, stream>>>(d_desc, 1);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) { set_error("bs_order_noalloc: launch failed: %s", cudaGetErrorString(e)); return BS_ECUDA; }
+    return BS_OK;
 }
 
 }  // namespace bs
