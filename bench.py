@@ -4,9 +4,9 @@
 Workload (the batched-ordering configuration): 4096 seeded tori with lognormal
 triangle counts (2k-50k) and lognormal target surfel counts (median 20k, 1k-500k,
 about 100M surfels in total), each sampled from the 6 axis directions at a
-per-part resolution and then ordered exactly.  One step = bs_sample_visible for
-every part followed by one bs_order_batched over all parts (every row of the hot
-path: quantise, raster, resolve, dedup, ordering, radius).
+per-part resolution and then ordered exactly.  One step = one bs_sample_visible_batched
+call over every part followed by one bs_order_batched over all parts (every row of
+the hot path: quantise, raster, resolve, dedup, ordering, radius).
 
 Printed JSON line (rank 0):
   value      surfels/s of the device-resident step (inputs already in HBM)
@@ -267,13 +267,17 @@ def main():
                                       rgb_all.data_ptr() + 3 * o, src_all.data_ptr() + 4 * o, 0, caps[i],
                                       (C.c_float * 3)(), 0.0))
 
+    mesh_arr = (bs.Mesh * len(specs))(*mesh_structs)
+    out_arr = (bs.Surfels * len(specs))(*out_structs)
+    res_arr = (C.c_int * len(specs))(*[sp.res for sp in specs])
+
     def sample_all():
-        for i, sp in enumerate(specs):
-            st = lib.bs_sample_visible(C.byref(mesh_structs[i]), dirs, 6, sp.res, C.byref(out_structs[i]), cs)
-            if st != bs.BS_OK:
-                raise bs.BsError(st, "bs_sample_visible", bs.last_error())
+        st = lib.bs_sample_visible_batched(mesh_arr, res_arr, len(specs), dirs, 6, out_arr, cs)
+        if st != bs.BS_OK:
+            raise bs.BsError(st, "bs_sample_visible_batched", bs.last_error())
 
     sample_all()
+    out_structs = [out_arr[i] for i in range(len(specs))]
     ns = np.array([o.n for o in out_structs], np.int64)
     total = int(ns.sum())
     pofs = np.cumsum([0] + list(ns))
@@ -422,7 +426,10 @@ def main():
         bytes_launch = float(sum(algorithmic_bytes(int(n)) for n in ns))
         loop_avg = float(np.mean(loop_ms))
         achieved = bytes_launch / (loop_avg / 1e3) / 1e9
-        nsample_kernels = 35
+        # one sampling call: bbox, quantise, setup, raster, cover count, 1-3 scan kernels,
+        # resolve, 10 radix passes x (hist, 1-3 scan kernels, scatter), part keys,
+        # unique count, scan, 2 unique passes; ordering: init, loop, radius
+        nsample_kernels = 64
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -430,7 +437,7 @@ def main():
             "config": config_dict(args, specs) | {"surfels_per_gpu": total},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d_bytes),
                     "d2h_bytes_per_step": int(d2h_bytes)},
-            "gpu_launches": args.steps * (nsample_kernels * P + 3),
+            "gpu_launches": args.steps * (nsample_kernels + 3),
             "roofline": {"bound": "hbm", "kernel": "k_order_loop", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                          "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured" else "fallback 6800 GB/s",

@@ -116,6 +116,19 @@ typedef struct {
 bs_status bs_sample_visible(const bs_mesh *mesh, const bs_dir *dirs, int ndirs, int res,
                             bs_surfels *out, void *cuda_stream);
 
+/* bs_sample_visible_batched -- bs_sample_visible for many meshes in one set of
+ * launches (the per-node sampling of Sec. 3.4 run for a whole scene).
+ *  meshes : HOST array of nparts device meshes (1 <= nparts <= 65535)
+ *  res    : HOST array of nparts resolutions; dirs: HOST array of ndirs directions
+ *           shared by all parts; the total pixel count must stay below 2^32
+ *  out    : HOST array of nparts descriptors of caller-owned device arrays
+ * Every part's surfels are bit-identical to a bs_sample_visible call on that part.
+ * On return out[p].n, bbox_min and scale are set for every part; a part whose n
+ * exceeds its cap is not written and the call returns BS_EOVERFLOW (the other parts
+ * are written).  BS_EINVAL names the first invalid part.  Synchronises the stream. */
+bs_status bs_sample_visible_batched(const bs_mesh *meshes, const int *res, int nparts, const bs_dir *dirs,
+                                    int ndirs, bs_surfels *out, void *cuda_stream);
+
 /* bs_order -- progressive ordering of one part (Sec. 3.2 goal; Sec. 4.1 radius).
  * Computes the exact greedy permutation (farthest-first traversal) of the
  * points s->key[0..n): perm[0] is the start index; perm[k] (k >= 1) is the
@@ -200,6 +213,7 @@ void bs_server_destroy(bs_server *srv);
 /* Launch-shape knobs for the autotuner (results never depend on them):
  *  "order_threads"      threads per ordering CTA (64, 128, 256, 512, 1024; 0 = auto)
  *  "order_ctas_per_sm"  cap on resident ordering CTAs per SM (0 = occupancy limit)
+ *  "order_algo"         2 = exact multi-pick rounds (default), 1 = one pick per step
  *  "kernel_timing"      1 = record CUDA events around internal kernels (bs_last_launch_ms)
  * Process-wide; BS_EINVAL for an unknown name or value. */
 bs_status bs_set_tuning(const char *name, int value);

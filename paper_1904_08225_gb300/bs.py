@@ -22,7 +22,7 @@ STATUS_NAMES = ["BS_OK", "BS_EINVAL", "BS_ENOMEM", "BS_EOVERFLOW", "BS_ETIMEOUT"
 INT64_MAX = (1 << 63) - 1
 
 # symbols include/bs.h declares; the library must export every one
-EXPORTS = ["bs_sample_visible", "bs_order", "bs_order_noalloc", "bs_order_batched", "bs_server_create", "bs_server_submit",
+EXPORTS = ["bs_sample_visible", "bs_sample_visible_batched", "bs_order", "bs_order_noalloc", "bs_order_batched", "bs_server_create", "bs_server_submit",
            "bs_server_poll", "bs_server_times", "bs_server_destroy", "bs_set_tuning", "bs_last_launch_ms",
            "bs_last_error"]
 
@@ -70,6 +70,8 @@ def load(build_if_stale: bool = True) -> C.CDLL:
             lib = C.CDLL(path)
             P = C.c_void_p
             lib.bs_sample_visible.argtypes = [C.POINTER(Mesh), C.POINTER(Dir), C.c_int, C.c_int, C.POINTER(Surfels), P]
+            lib.bs_sample_visible_batched.argtypes = [C.POINTER(Mesh), C.POINTER(C.c_int), C.c_int, C.POINTER(Dir),
+                                                      C.c_int, C.POINTER(Surfels), P]
             lib.bs_order.argtypes = [C.POINTER(Surfels), C.POINTER(OrderOpts), P, P, P, P]
             lib.bs_order_noalloc.argtypes = [C.POINTER(Surfels), C.POINTER(OrderOpts), P, P, P, P]
             lib.bs_order_batched.argtypes = [C.POINTER(Surfels), C.c_int, C.POINTER(OrderOpts), P, P, P, P]
@@ -155,6 +157,44 @@ def sample_visible(xyz, tri, rgb, dirs, res: int, stream=None, cap: int | None =
     n = int(out.n)
     return dict(key=key[:n], nrm=nrm[:n], rgb=col[:n], src=src[:n], n=n,
                 bbox_min=np.array(list(out.bbox_min), np.float32), scale=float(out.scale))
+
+
+def sample_visible_batched(meshes, res, dirs, stream=None, caps=None):
+    """bs_sample_visible_batched over a list of (xyz, tri, rgb-or-None) CUDA tensor triples.
+
+    res: per-part resolutions.  Returns a list of dicts like sample_visible()."""
+    torch = _torch()
+    lib = load()
+    P = len(meshes)
+    d = np.asarray(dirs, dtype=np.int8).reshape(-1, 3)
+    darr = (Dir * len(d))(*[Dir(int(a), int(b), int(c)) for a, b, c in d])
+    marr = (Mesh * P)()
+    rarr = (C.c_int * P)(*[int(r) for r in res])
+    outs = (Surfels * P)()
+    keep = []
+    for i, (xyz, tri, rgb) in enumerate(meshes):
+        xyz, tri = xyz.contiguous(), tri.contiguous()
+        rgb = rgb.contiguous() if rgb is not None else None
+        keep.append((xyz, tri, rgb))
+        marr[i] = Mesh(xyz.data_ptr(), xyz.shape[0], tri.data_ptr() if tri.numel() else None, tri.shape[0],
+                       rgb.data_ptr() if rgb is not None else None)
+        cap = caps[i] if caps is not None else len(d) * int(res[i]) ** 2
+        dev = xyz.device
+        key = torch.empty(cap, dtype=torch.int64, device=dev)
+        nrm = torch.empty((cap, 3), dtype=torch.int16, device=dev)
+        col = torch.empty((cap, 3), dtype=torch.uint8, device=dev)
+        src = torch.empty(cap, dtype=torch.int32, device=dev)
+        keep.append((key, nrm, col, src))
+        outs[i] = Surfels(key.data_ptr(), nrm.data_ptr(), col.data_ptr(), src.data_ptr(), 0, cap, (C.c_float * 3)(), 0.0)
+    st = lib.bs_sample_visible_batched(marr, rarr, P, darr, len(d), outs, _stream(stream))
+    _check(st, "bs_sample_visible_batched")
+    res_list = []
+    for i in range(P):
+        key, nrm, col, src = keep[2 * i + 1]
+        n = int(outs[i].n)
+        res_list.append(dict(key=key[:n], nrm=nrm[:n], rgb=col[:n], src=src[:n], n=n,
+                             bbox_min=np.array(list(outs[i].bbox_min), np.float32), scale=float(outs[i].scale)))
+    return res_list
 
 
 def _opts(seed=0, part_id=0, start=-1, max_count=0) -> OrderOpts:

@@ -75,6 +75,10 @@ bs_status bs_set_tuning(const char *name, int value) {
             return BS_EINVAL;
         }
         threads = value;
+    } else if (!strcmp(name, "order_algo")) {
+        if (value != 1 && value != 2) { set_error("bs_set_tuning: order_algo=%d not 1 or 2", value); return BS_EINVAL; }
+        order_set_algo(value);
+        return BS_OK;
     } else if (!strcmp(name, "kernel_timing")) {
         if (value != 0 && value != 1) { set_error("bs_set_tuning: kernel_timing=%d not 0 or 1", value); return BS_EINVAL; }
         order_set_kernel_timing(value == 1);
@@ -108,6 +112,12 @@ bs_status bs_sample_visible(const bs_mesh *mesh, const bs_dir *dirs, int ndirs, 
                             void *cuda_stream) {
     clear_error();
     return sample_visible(mesh, dirs, ndirs, res, out, (cudaStream_t)cuda_stream);
+}
+
+bs_status bs_sample_visible_batched(const bs_mesh *meshes, const int *res, int nparts, const bs_dir *dirs, int ndirs,
+                                    bs_surfels *out, void *cuda_stream) {
+    clear_error();
+    return sample_visible_parts(meshes, res, nparts, dirs, ndirs, out, (cudaStream_t)cuda_stream);
 }
 
 bs_status bs_order(const bs_surfels *s, const bs_order_opts *opts, uint32_t *perm, int64_t *rad2, float *radius,
@@ -260,10 +270,6 @@ static void launch_batch(bs_server *S, SrvSlot &slot, std::vector<SrvReq *> &bat
         int64_t *dr = (int64_t *)(r->dmem + align256(r->n * 8) + align256(r->m * 4));
         float *df = (float *)(r->dmem + align256(r->n * 8) + align256(r->m * 4) + align256(r->m * 8));
         cudaMemcpyAsync(dk, r->key.data(), r->n * 8, cudaMemcpyHostToDevice, slot.stream);
-        bs_surfels s{};
-        s.key = dk;
-        s.n = r->n;
-        s.scale = r->scale;
         PartDesc p;
         memset(&p, 0, sizeof(p));
         p.key = dk; p.perm = dp; p.rad2 = dr; p.radius = df; p.scale = r->scale;

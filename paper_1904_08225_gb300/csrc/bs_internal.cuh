@@ -133,9 +133,12 @@ bs_status order_parts(std::vector<PartDesc> &parts, cudaStream_t stream, bool ba
 bs_status order_part_noalloc(PartDesc part, cudaStream_t stream);
 void order_set_tuning(int threads, int ctas_per_sm);
 void order_set_kernel_timing(bool on);
+void order_set_algo(int algo);
 bs_status order_last_launch_ms(int which, double *ms);
 bs_status sample_visible(const bs_mesh *mesh, const bs_dir *dirs, int ndirs, int res, bs_surfels *out,
                          cudaStream_t stream);
+bs_status sample_visible_parts(const bs_mesh *meshes, const int *res, int nparts, const bs_dir *dirs, int ndirs,
+                               bs_surfels *out, cudaStream_t stream);
 
 // ---- warp reductions ----
 __device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {

@@ -34,7 +34,6 @@
 namespace bs {
 
 constexpr uint32_t FULL = 0xffffffffu;
-constexpr int MAX_GROUPS = 6144;  // BS_MAX_POINTS / 1024
 
 __global__ void __launch_bounds__(256) k_order_init(const PartDesc *__restrict__ parts, const uint32_t *__restrict__ gofs,
                                                     int nparts, uint32_t total_groups) {
@@ -195,6 +194,375 @@ __global__ void __launch_bounds__(T) k_order_loop(const PartDesc *__restrict__ p
     }
 }
 
+// ---------------------------------------------------------------------------
+// Exact multi-pick rounds.  A round takes a threshold tau <= D1 (the current
+// maximum) and gathers every unchosen point i with D[i] > tau, or D[i] == tau and
+// i < icut, into a candidate set C (at most CAP points).  Every point outside C is
+// below (tau, icut) in the (D, lowest index) order, and D only decreases, so while
+// the best candidate (D updated by this round's picks) is still above (tau, icut)
+// it is exactly the greedy's next pick.  One warp runs that small greedy; then all
+// picks are applied to the whole part at once.  A fourth level of super-groups
+// (32 groups, 32768 points) prunes the apply sweep of large parts.
+//   sgkey = (D+1) << 15 | (32767 - i_in_supergroup);   top = (D+1) << 8 | (255 - sg)
+// ---------------------------------------------------------------------------
+constexpr int CAP = 64;      // candidates per round (two per lane of the simulating warp)
+constexpr int MAXP = 64;     // picks per round
+constexpr int MAX_SG = 192;  // super-groups: BS_MAX_POINTS / 32768
+
+__device__ __forceinline__ uint64_t pick_mask(uint32_t np, const uint32_t *pi, const uint64_t *pk, uint64_t allow,
+                                              uint32_t own_shift, uint32_t own, uint64_t lo, uint64_t hi, int64_t maxD) {
+    // bit t set if pick t may lower a D inside the box [lo, hi] (whose largest D is maxD)
+    // or lies inside the index range `own` at granularity own_shift
+    const int lane = threadIdx.x & 31;
+    bool ra = false, rb = false;
+    const uint32_t ta = lane, tb = lane + 32;
+    if (ta < np && ((allow >> ta) & 1ull)) ra = (pi[ta] >> own_shift) == own || box_dist2(lo, hi, pk[ta]) < maxD;
+    if (tb < np && ((allow >> tb) & 1ull)) rb = (pi[tb] >> own_shift) == own || box_dist2(lo, hi, pk[tb]) < maxD;
+    return (uint64_t)__ballot_sync(0xffffffffu, ra) | ((uint64_t)__ballot_sync(0xffffffffu, rb) << 32);
+}
+
+template <int T>
+__global__ void __launch_bounds__(T) k_order_rounds(const PartDesc *__restrict__ parts, int nparts,
+                                                    uint32_t *__restrict__ next_part, int ngmax) {
+    constexpr int NW = T / 32;
+    extern __shared__ uint64_t sm[];
+    uint64_t *s_gkey = sm;
+    uint64_t *s_glo = sm + ngmax;
+    uint64_t *s_ghi = sm + 2 * ngmax;
+    uint32_t *s_glist = (uint32_t *)(sm + 3 * ngmax);
+    __shared__ uint64_t s_sgkey[MAX_SG], s_sglo[MAX_SG], s_sghi[MAX_SG], s_sgmask[MAX_SG];
+    __shared__ uint32_t s_sglist[MAX_SG];
+    __shared__ uint64_t s_ck[CAP];
+    __shared__ int64_t s_cd[CAP];
+    __shared__ uint32_t s_ci[CAP];
+    __shared__ uint64_t s_pk[MAXP];
+    __shared__ uint32_t s_pi[MAXP];
+    __shared__ uint32_t s_part, s_ccnt, s_gcnt, s_sgcnt, s_npick;
+    __shared__ int s_shift;
+    __shared__ int64_t s_tieD;
+    __shared__ uint32_t s_icut;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_part = atomicAdd(next_part, 1u);
+        __syncthreads();
+        const uint32_t p = s_part;
+        if (p >= (uint32_t)nparts) break;
+        const PartDesc P = parts[p];
+        const uint32_t ng = P.ng, ns = (ng + 31) / 32;
+        for (uint32_t g = threadIdx.x; g < ng; g += T) {
+            s_gkey[g] = P.gkey[g];
+            s_glo[g] = P.glo[g];
+            s_ghi[g] = P.ghi[g];
+        }
+        if (threadIdx.x == 0) {
+            P.perm[0] = P.start;
+            P.rad2[0] = INT64_MAX;
+            s_shift = 3;
+            s_tieD = -2;
+        }
+        __syncthreads();
+        for (uint32_t sg = warp; sg < ns; sg += NW) {
+            const uint32_t g = sg * 32 + lane;
+            const bool vg = g < ng;
+            const uint64_t gk = vg ? s_gkey[g] : 0ull;
+            const uint64_t cand = vg ? (((gk >> 10) << 15) | (uint64_t)(32767 - (lane * 1024 + (1023 - (int)(gk & 1023))))) : 0ull;
+            const uint64_t sk = warp_max_u64(cand);
+            const uint64_t lo = vg ? s_glo[g] : ~0ull, hi = vg ? s_ghi[g] : 0ull;
+            const uint32_t lx = __reduce_min_sync(FULL, vg ? pos_x(lo) : 0xffffffffu);
+            const uint32_t ly = __reduce_min_sync(FULL, vg ? pos_y(lo) : 0xffffffffu);
+            const uint32_t lz = __reduce_min_sync(FULL, vg ? pos_z(lo) : 0xffffffffu);
+            const uint32_t hx = __reduce_max_sync(FULL, vg ? pos_x(hi) : 0u);
+            const uint32_t hy = __reduce_max_sync(FULL, vg ? pos_y(hi) : 0u);
+            const uint32_t hz = __reduce_max_sync(FULL, vg ? pos_z(hi) : 0u);
+            if (lane == 0) {
+                s_sgkey[sg] = sk;
+                s_sglo[sg] = pack_pos(lx, ly, lz);
+                s_sghi[sg] = pack_pos(hx, hy, hz);
+            }
+        }
+        __syncthreads();
+        uint32_t k = 1;
+        while (k < P.m) {
+            // (1) current maximum (every warp computes it; no barrier needed)
+            uint64_t top = 0;
+            for (uint32_t sg = lane; sg < ns; sg += 32) top = max(top, ((s_sgkey[sg] >> 15) << 8) | (uint64_t)(255 - sg));
+            top = warp_max_u64(top);
+            const int64_t D1 = (int64_t)(top >> 8) - 1;
+            const uint32_t sgj = 255u - (uint32_t)(top & 255u);
+            const uint32_t j = sgj * 32768u + (32767u - (uint32_t)(s_sgkey[sgj] & 32767u));
+            // (2) threshold: tau = D1 (1 - 2^-shift); when more than CAP points tie at D1, a tie
+            //     window instead: tau = D1 and an index cut inside the argmax's group
+            const int shift = s_shift;
+            const bool tie = D1 == s_tieD;
+            const int64_t tau = tie ? D1 : D1 - (D1 >> shift);
+            __syncthreads();
+            if (threadIdx.x == 0) { s_ccnt = 0; s_gcnt = 0; s_sgcnt = 0; s_icut = 0xffffffffu; }
+            __syncthreads();
+            // (3) gather the candidates
+            if (tie) {
+                // the D1 points of the buckets of group(j) from bucket(j) on, in index order, while
+                // they fit; icut = first index left out (no point with D = D1 lies below j)
+                if (warp == 0) {
+                    const uint32_t g0 = j >> 10;
+                    const uint32_t b = g0 * 32 + lane;
+                    const uint64_t bk = (b < P.nb && b >= (j >> 5)) ? P.bkey[b] : 0ull;
+                    uint32_t mask = __ballot_sync(FULL, (int64_t)(bk >> 5) - 1 >= tau);
+                    uint32_t cnt = 0, icut = min(P.n, (g0 + 1) * 1024u);
+                    while (mask) {
+                        const int bb = __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        const uint32_t i = (g0 * 32 + bb) * 32 + lane;
+                        const int64_t d = i < P.n ? P.D[i] : -1;
+                        const uint64_t ki = i < P.n ? P.key[i] : 0ull;
+                        const bool c = d >= tau;
+                        const uint32_t cm = __ballot_sync(FULL, c);
+                        if (cnt + __popc(cm) > (uint32_t)CAP) {
+                            icut = (g0 * 32 + bb) * 32;
+                            break;
+                        }
+                        if (c) {
+                            const uint32_t slot = cnt + __popc(cm & ((1u << lane) - 1u));
+                            s_ci[slot] = i;
+                            s_cd[slot] = d;
+                            s_ck[slot] = ki;
+                        }
+                        cnt += __popc(cm);
+                    }
+                    if (lane == 0) { s_ccnt = cnt; s_icut = icut; }
+                }
+            } else {
+                for (uint32_t sg = threadIdx.x; sg < ns; sg += T)
+                    if ((int64_t)(s_sgkey[sg] >> 15) - 1 >= tau) s_sglist[atomicAdd(&s_sgcnt, 1u)] = sg;
+                __syncthreads();
+                const uint32_t nsgl = s_sgcnt;
+                for (uint32_t li = warp; li < nsgl; li += NW) {
+                    const uint32_t g = s_sglist[li] * 32 + lane;
+                    if (g < ng && (int64_t)(s_gkey[g] >> 10) - 1 >= tau) s_glist[atomicAdd(&s_gcnt, 1u)] = g;
+                }
+                __syncthreads();
+                const uint32_t ngl = s_gcnt;
+                for (uint32_t li = warp; li < ngl; li += NW) {
+                    const uint32_t g = s_glist[li];
+                    const uint32_t b = g * 32 + lane;
+                    const uint64_t bk = b < P.nb ? P.bkey[b] : 0ull;
+                    uint32_t mask = __ballot_sync(FULL, (int64_t)(bk >> 5) - 1 >= tau);
+                    while (mask) {
+                        // up to four buckets per pass so their loads overlap
+                        uint32_t bbs[4];
+                        int nb4 = 0;
+                        while (mask && nb4 < 4) {
+                            bbs[nb4++] = (uint32_t)(__ffs(mask) - 1);
+                            mask &= mask - 1;
+                        }
+                        int64_t d[4];
+                        uint64_t ki[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const uint32_t i = (g * 32 + (u < nb4 ? bbs[u] : 0)) * 32 + lane;
+                            const bool ok = u < nb4 && i < P.n;
+                            d[u] = ok ? P.D[i] : -1;
+                            ki[u] = ok ? P.key[i] : 0ull;
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            if (u < nb4 && d[u] >= tau && d[u] >= 0) {
+                                const uint32_t slot = atomicAdd(&s_ccnt, 1u);
+                                if (slot < CAP) {
+                                    s_ci[slot] = (g * 32 + bbs[u]) * 32 + lane;
+                                    s_cd[slot] = d[u];
+                                    s_ck[slot] = ki[u];
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            const uint32_t ccnt = s_ccnt;
+            const uint32_t icut = s_icut;
+            if (ccnt > CAP) {
+                // too many candidates: move tau toward D1 by about log2(ccnt / CAP) halvings;
+                // at tau == D1 switch to the tie window until D1 drops
+                if (threadIdx.x == 0) {
+                    if (tau == D1) {
+                        s_tieD = D1;
+                    } else {
+                        int inc = 1;
+                        for (uint32_t c = ccnt / CAP; c > 1; c >>= 1) ++inc;
+                        s_shift = min(shift + inc, 62);
+                    }
+                }
+                __syncthreads();
+                continue;
+            }
+            // (4) candidates in index order: slot order is the lowest-index tie-break
+            {
+                uint32_t ci = 0, rank = 0;
+                int64_t cd = 0;
+                uint64_t ck = 0;
+                if (threadIdx.x < ccnt) {
+                    ci = s_ci[threadIdx.x];
+                    cd = s_cd[threadIdx.x];
+                    ck = s_ck[threadIdx.x];
+                    for (uint32_t u = 0; u < ccnt; ++u) rank += s_ci[u] < ci ? 1u : 0u;
+                }
+                __syncthreads();
+                if (threadIdx.x < ccnt) {
+                    s_ci[rank] = ci;
+                    s_cd[rank] = cd;
+                    s_ck[rank] = ck;
+                }
+                __syncthreads();
+            }
+            // (5) the greedy restricted to C, one warp, while the best stays above (tau, icut)
+            if (warp == 0) {
+                const uint32_t a = lane, b = lane + 32;
+                bool la = a < ccnt, lb = b < ccnt;
+                int64_t Da = la ? s_cd[a] : 0, Db = lb ? s_cd[b] : 0;
+                const uint64_t qa = la ? s_ck[a] : 0ull, qb = lb ? s_ck[b] : 0ull;
+                const uint32_t budget = min((uint32_t)MAXP, P.m - k);
+                uint32_t np = 0;
+                while (np < budget) {
+                    const uint64_t ka = la ? (((uint64_t)(Da + 1) << 7) | (uint64_t)(127 - a)) : 0ull;
+                    const uint64_t kb = lb ? (((uint64_t)(Db + 1) << 7) | (uint64_t)(127 - b)) : 0ull;
+                    const uint64_t best = warp_max_u64(max(ka, kb));
+                    if (best == 0) break;
+                    const uint32_t slot = 127u - (uint32_t)(best & 127u);
+                    const int64_t Dbest = (int64_t)(best >> 7) - 1;
+                    const uint32_t idx = s_ci[slot];
+                    if (!(Dbest > tau || (Dbest == tau && idx < icut))) break;
+                    const uint64_t qbest = s_ck[slot];
+                    if (lane == 0) {
+                        s_pk[np] = qbest;
+                        s_pi[np] = idx;
+                        P.perm[k + np] = idx;
+                        P.rad2[k + np] = Dbest;
+                    }
+                    ++np;
+                    if (a == slot) la = false;
+                    else if (la) Da = min(Da, dist2(qa, qbest));
+                    if (b == slot) lb = false;
+                    else if (lb) Db = min(Db, dist2(qb, qbest));
+                }
+                if (lane == 0) s_npick = np;
+            }
+            __syncthreads();
+            const uint32_t np = s_npick;
+            // (6) apply the round's picks to the whole part
+            for (uint32_t t = threadIdx.x; t < np; t += T) P.D[s_pi[t]] = -1;
+            if (threadIdx.x == 0) { s_sgcnt = 0; s_gcnt = 0; }
+            __syncthreads();
+            const uint64_t all = np >= 64 ? ~0ull : ((1ull << np) - 1ull);
+            for (uint32_t sg = warp; sg < ns; sg += NW) {
+                const uint64_t m = pick_mask(np, s_pi, s_pk, all, 15, sg, s_sglo[sg], s_sghi[sg],
+                                             (int64_t)(s_sgkey[sg] >> 15) - 1);
+                if (m && lane == 0) {
+                    s_sgmask[sg] = m;
+                    s_sglist[atomicAdd(&s_sgcnt, 1u)] = sg;
+                }
+            }
+            __syncthreads();
+            const uint32_t nsgl = s_sgcnt;
+            for (uint32_t li = warp; li < nsgl; li += NW) {
+                const uint32_t sg = s_sglist[li];
+                const uint32_t g = sg * 32 + lane;
+                if (g < ng) {
+                    const int64_t gD = (int64_t)(s_gkey[g] >> 10) - 1;
+                    const uint64_t lo = s_glo[g], hi = s_ghi[g];
+                    uint64_t m = s_sgmask[sg];
+                    bool rel = false;
+                    while (m && !rel) {
+                        const int t = __ffsll((long long)m) - 1;
+                        m &= m - 1;
+                        rel = (s_pi[t] >> 10) == g || box_dist2(lo, hi, s_pk[t]) < gD;
+                    }
+                    if (rel) s_glist[atomicAdd(&s_gcnt, 1u)] = g;
+                }
+            }
+            __syncthreads();
+            const uint32_t ngl = s_gcnt;
+            for (uint32_t li = warp; li < ngl; li += NW) {
+                const uint32_t g = s_glist[li];
+                const uint64_t gm = pick_mask(np, s_pi, s_pk, s_sgmask[g >> 5], 10, g, s_glo[g], s_ghi[g],
+                                              (int64_t)(s_gkey[g] >> 10) - 1);
+                const uint32_t b = g * 32 + lane;
+                const bool vb = b < P.nb;
+                uint64_t bk = vb ? P.bkey[b] : 0ull;
+                const uint64_t blo = vb ? P.blo[b] : 0ull, bhi = vb ? P.bhi[b] : 0ull;
+                const int64_t bD = (int64_t)(bk >> 5) - 1;
+                bool aff = false;
+                if (vb) {
+                    uint64_t m = gm;
+                    while (m && !aff) {
+                        const int t = __ffsll((long long)m) - 1;
+                        m &= m - 1;
+                        aff = (s_pi[t] >> 5) == b || box_dist2(blo, bhi, s_pk[t]) < bD;
+                    }
+                }
+                uint32_t amask = __ballot_sync(FULL, aff);
+                while (amask) {
+                    // up to four affected buckets per pass so their loads overlap
+                    uint32_t bbs[4];
+                    int nb4 = 0;
+                    while (amask && nb4 < 4) {
+                        bbs[nb4++] = (uint32_t)(__ffs(amask) - 1);
+                        amask &= amask - 1;
+                    }
+                    int64_t d[4];
+                    uint64_t ki[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const uint32_t i = (g * 32 + (u < nb4 ? bbs[u] : 0)) * 32 + lane;
+                        const bool ok = u < nb4 && i < P.n;
+                        d[u] = ok ? P.D[i] : -1;
+                        ki[u] = ok ? P.key[i] : 0ull;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (u >= nb4) break;
+                        const uint32_t i = (g * 32 + bbs[u]) * 32 + lane;
+                        int64_t dd = d[u];
+                        if (dd > 0) {
+                            int64_t nd = dd;
+                            uint64_t m = gm;
+                            while (m) {
+                                const int t = __ffsll((long long)m) - 1;
+                                m &= m - 1;
+                                nd = min(nd, dist2(ki[u], s_pk[t]));
+                            }
+                            if (nd < dd) {
+                                dd = nd;
+                                P.D[i] = nd;
+                            }
+                        }
+                        const uint64_t nk = i < P.n ? (((uint64_t)(dd + 1) << 5) | (uint64_t)(31 - lane)) : 0ull;
+                        const uint64_t nbk = warp_max_u64(nk);
+                        if (lane == (int)bbs[u]) bk = nbk;
+                    }
+                }
+                if (aff) P.bkey[b] = bk;
+                const uint64_t cand = vb ? (((bk >> 5) << 10) | (uint64_t)(1023 - (lane * 32 + (31 - (int)(bk & 31))))) : 0ull;
+                const uint64_t ngk = warp_max_u64(cand);
+                if (lane == 0) s_gkey[g] = ngk;
+            }
+            __syncthreads();
+            for (uint32_t li = warp; li < nsgl; li += NW) {
+                const uint32_t sg = s_sglist[li];
+                const uint32_t g = sg * 32 + lane;
+                const uint64_t gk = g < ng ? s_gkey[g] : 0ull;
+                const uint64_t cand = g < ng ? (((gk >> 10) << 15) | (uint64_t)(32767 - (lane * 1024 + (1023 - (int)(gk & 1023))))) : 0ull;
+                const uint64_t sk = warp_max_u64(cand);
+                if (lane == 0) s_sgkey[sg] = sk;
+            }
+            if (threadIdx.x == 0 && !tie && ccnt < CAP / 4 && shift > 1) s_shift = shift - 1;
+            k += np;
+            __syncthreads();
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void k_radius(const PartDesc *__restrict__ parts, int nparts) {
     for (int p = blockIdx.y; p < nparts; p += gridDim.y) {
         const PartDesc P = parts[p];
@@ -217,12 +585,15 @@ struct LoopCfg {
 };
 
 static int g_loop_threads_override = 0;   // set by bs_set_tuning("order_threads", v)
+static int g_order_algo = 2;              // 1 = one pick per step, 2 = exact multi-pick rounds
 static int g_ctas_per_sm_override = 0;    // set by bs_set_tuning("order_ctas_per_sm", v)
 
 void order_set_tuning(int threads, int ctas_per_sm) {
     g_loop_threads_override = threads;
     g_ctas_per_sm_override = ctas_per_sm;
 }
+
+void order_set_algo(int algo) { g_order_algo = algo; }
 
 // Optional per-kernel timing: events recorded on the launch stream around one kernel.
 static bool g_kernel_timing = false;
@@ -258,19 +629,35 @@ bs_status order_last_launch_ms(int which, double *ms) {
 template <int T>
 static cudaError_t launch_loop(const PartDesc *d_parts, int nparts, uint32_t *d_next, int ngmax, int grid,
                                cudaStream_t stream) {
-    const size_t smem = (size_t)ngmax * 36;
-    cudaError_t e = cudaFuncSetAttribute(k_order_loop<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_order_loop<T><<<grid, T, smem, stream>>>(d_parts, nparts, d_next, ngmax);
+    cudaError_t e;
+    if (g_order_algo == 1) {
+        const size_t smem = (size_t)ngmax * 36;
+        e = cudaFuncSetAttribute(k_order_loop<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_order_loop<T><<<grid, T, smem, stream>>>(d_parts, nparts, d_next, ngmax);
+    } else {
+        const size_t smem = (size_t)ngmax * 28;
+        e = cudaFuncSetAttribute(k_order_rounds<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_order_rounds<T><<<grid, T, smem, stream>>>(d_parts, nparts, d_next, ngmax);
+    }
     return cudaGetLastError();
 }
 
 template <int T>
 static int occupancy(int ngmax) {
     int blocks = 0;
-    const size_t smem = (size_t)ngmax * 36;
-    cudaFuncSetAttribute(k_order_loop<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_order_loop<T>, T, smem) != cudaSuccess) {
+    cudaError_t e;
+    if (g_order_algo == 1) {
+        const size_t smem = (size_t)ngmax * 36;
+        cudaFuncSetAttribute(k_order_loop<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_order_loop<T>, T, smem);
+    } else {
+        const size_t smem = (size_t)ngmax * 28;
+        cudaFuncSetAttribute(k_order_rounds<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_order_rounds<T>, T, smem);
+    }
+    if (e != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }

@@ -1,19 +1,22 @@
-// bs_sample.cu -- visible-surface sampling (Sec. 3.1): quantise a mesh, rasterise it
+// bs_sample.cu -- visible-surface sampling (Sec. 3.1): quantise each mesh, rasterise it
 // orthographically from several integer directions with an integer rasteriser,
-// emit one surfel per covered pixel, merge identical positions and sort the
-// surfels into ascending Morton order.
+// emit one surfel per covered pixel, merge identical positions and sort each part's
+// surfels into ascending Morton order.  Any number of parts go through one set of
+// launches; a single part is the one-part case.
 //
 // Pipeline (all on the caller's stream):
-//   k_bbox -> k_scale -> k_quantise              node-local 21-bit integer positions
-//   k_setup   (dir x triangle)                   snapped screen coords, winding, area
+//   k_bbox -> k_scale -> k_quantise              node-local 21-bit integer positions (block per part)
+//   k_setup   (dir x triangle, all parts)        snapped screen coords, winding, area
 //   k_raster  (warp per dir x triangle)          64-bit atomicMin(depth << 32 | tri)
-//   k_cover_count -> scan -> k_resolve           covered pixels in emission order
-//   radix sort (Morton code, row)                stable LSD, 8-bit digits
-//   k_unique_count -> scan -> k_unique_write     keep the first row of each position
+//   k_cover_count -> scan -> k_resolve           covered pixels in (part, emission) order
+//   radix sort (Morton code), then (part)        stable LSD, 8-bit digits
+//   k_unique_count -> scan -> k_segments -> k_unique_write
+//                                                keep the first row of each (part, position)
 //
 // Arithmetic: integers throughout, except the quantiser (IEEE double subtract and
 // multiply, written with explicit round-to-nearest intrinsics so nothing is fused)
 // and the unit normal (IEEE double multiply/add/sqrt/divide, same intrinsics).
+#include <algorithm>
 #include <cstdio>
 #include <vector>
 
@@ -35,7 +38,6 @@ struct View {
 struct Views {
     View v[BS_MAX_DIRS];
     int ndirs;
-    int res;
 };
 
 static void make_frame(const bs_dir &dir, View &V) {
@@ -66,19 +68,48 @@ static void make_frame(const bs_dir &dir, View &V) {
 }
 
 // ---------------------------------------------------------------------------
-// Quantisation: bbox over float32 vertices, isotropic scale S = (2^21-1)/E.
+// Part table and per-part state
 // ---------------------------------------------------------------------------
-struct QuantState {
-    uint32_t mn_ord[3], mx_ord[3];  // order-preserving encodings of the float bounds
-    uint32_t nonfinite;
-    uint32_t invalid;
-    uint32_t badtri;  // triangles with a vertex index >= nverts
-    float mn[3];
-    double scale;
-    uint32_t count;  // surfels after dedup
-    uint32_t rows;   // covered pixels before dedup
+struct SPart {
+    const float *xyz;
+    const uint32_t *tri;
+    const uint8_t *rgb;
+    uint64_t *okey;
+    int16_t *onrm;
+    uint8_t *orgb;
+    uint32_t *osrc;
+    uint64_t cap;
+    uint64_t vofs;  // first vertex of this part in the packed q array
+    uint64_t tofs;  // first triangle of this part in the packed triangle numbering
+    uint64_t pofs;  // first pixel (all directions) of this part in the packed depth buffer
+    uint32_t nverts, ntris;
+    int32_t res;
+    uint32_t pad;
 };
 
+struct SState {
+    uint32_t mn_ord[3], mx_ord[3];  // order-preserving encodings of the float bounds
+    uint32_t nonfinite, invalid, badtri, pad0;
+    float mn[3];
+    float pad1;
+    double scale;
+    uint64_t first_out, end_out;  // [first_out, end_out): this part's surfels in the packed output numbering
+};
+
+// index of the part whose range [ofs[p], ofs[p+1]) holds x (ofs ascending, ofs[0] = 0)
+__device__ __forceinline__ int find_part(const uint64_t *__restrict__ ofs, int nparts, uint64_t x) {
+    int lo = 0, hi = nparts - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ofs[mid] <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Quantisation: bbox over float32 vertices, isotropic scale S = (2^21-1)/E.
+// ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t f2ord(float f) {
     const uint32_t b = __float_as_uint(f);
     return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
@@ -87,12 +118,14 @@ __device__ __forceinline__ float ord2f(uint32_t o) {
     return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
 }
 
-__global__ void k_bbox(const float *__restrict__ xyz, uint32_t nverts, QuantState *st) {
+// one block per part
+__global__ void __launch_bounds__(256) k_bbox(const SPart *__restrict__ parts, SState *__restrict__ st) {
+    const SPart P = parts[blockIdx.x];
     uint32_t mn[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, mx[3] = {0u, 0u, 0u}, bad = 0;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nverts; i += gridDim.x * blockDim.x) {
+    for (uint32_t i = threadIdx.x; i < P.nverts; i += blockDim.x) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const float f = xyz[3ull * i + a];
+            const float f = P.xyz[3ull * i + a];
             if (!isfinite(f)) {
                 ++bad;
             } else {
@@ -102,46 +135,59 @@ __global__ void k_bbox(const float *__restrict__ xyz, uint32_t nverts, QuantStat
             }
         }
     }
+    __shared__ uint32_t red[8][7];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         mn[a] = __reduce_min_sync(0xffffffffu, mn[a]);
         mx[a] = __reduce_max_sync(0xffffffffu, mx[a]);
     }
     bad = __reduce_add_sync(0xffffffffu, bad);
-    if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            atomicMin(&st->mn_ord[a], mn[a]);
-            atomicMax(&st->mx_ord[a], mx[a]);
+    if (lane == 0) {
+        for (int a = 0; a < 3; ++a) { red[warp][a] = mn[a]; red[warp][3 + a] = mx[a]; }
+        red[warp][6] = bad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        SState &S = st[blockIdx.x];
+        for (int a = 0; a < 3; ++a) { S.mn_ord[a] = 0xffffffffu; S.mx_ord[a] = 0u; }
+        S.nonfinite = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            for (int a = 0; a < 3; ++a) {
+                S.mn_ord[a] = min(S.mn_ord[a], red[w][a]);
+                S.mx_ord[a] = max(S.mx_ord[a], red[w][3 + a]);
+            }
+            S.nonfinite += red[w][6];
         }
-        if (bad) atomicAdd(&st->nonfinite, bad);
+        double E = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            const float lo = ord2f(S.mn_ord[a]);
+            const float hi = ord2f(S.mx_ord[a]);
+            const double e = __dsub_rn((double)hi, (double)lo);
+            if (e > E) E = e;
+            S.mn[a] = __fadd_rn(lo, 0.0f);  // report -0.0 as +0.0
+        }
+        S.invalid = (S.nonfinite != 0u || P.nverts == 0 || !(E > 0.0)) ? 1u : 0u;
+        S.scale = S.invalid ? 0.0 : __ddiv_rn(2097151.0, E);
+        S.badtri = 0;
+        S.first_out = 0;
+        S.end_out = 0;
     }
 }
 
-__global__ void k_scale(QuantState *st) {
-    double E = 0.0;
-    for (int a = 0; a < 3; ++a) {
-        const float mn = ord2f(st->mn_ord[a]);
-        const float mx = ord2f(st->mx_ord[a]);
-        const double e = __dsub_rn((double)mx, (double)mn);
-        if (e > E) E = e;
-        st->mn[a] = __fadd_rn(mn, 0.0f);  // report -0.0 as +0.0
-    }
-    st->invalid = (st->nonfinite != 0u || !(E > 0.0)) ? 1u : 0u;
-    st->scale = st->invalid ? 0.0 : __ddiv_rn(2097151.0, E);
-}
-
-__global__ void k_quantise(const float *__restrict__ xyz, uint32_t nverts, const QuantState *st,
-                           int32_t *__restrict__ q) {
-    if (st->invalid) return;
-    const double S = st->scale;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < 3ull * nverts;
-         i += (uint64_t)gridDim.x * blockDim.x) {
+// one block per part
+__global__ void __launch_bounds__(256) k_quantise(const SPart *__restrict__ parts, const SState *__restrict__ st,
+                                                  int32_t *__restrict__ q) {
+    const SPart P = parts[blockIdx.x];
+    const SState &S = st[blockIdx.x];
+    if (S.invalid) return;
+    const double sc = S.scale;
+    for (uint64_t i = threadIdx.x; i < 3ull * P.nverts; i += blockDim.x) {
         const int a = (int)(i % 3);
-        const double t = __dmul_rn(__dsub_rn((double)xyz[i], (double)st->mn[a]), S);
+        const double t = __dmul_rn(__dsub_rn((double)P.xyz[i], (double)S.mn[a]), sc);
         int64_t v = (int64_t)floor(t);
         v = v < 0 ? 0 : (v > QMAX ? QMAX : v);
-        q[i] = (int32_t)v;
+        q[3ull * P.vofs + i] = (int32_t)v;
     }
 }
 
@@ -167,33 +213,40 @@ __device__ __forceinline__ void project(const View &V, int res, const int32_t *q
     W = (uint32_t)(-dq + V.wbias);
 }
 
-__global__ void k_setup(const int32_t *__restrict__ q, const uint32_t *__restrict__ tri, uint32_t ntris,
-                        uint32_t nverts, QuantState *st, const Views views, TriSetup *__restrict__ out) {
-    if (st->invalid) return;
+// grid: (triangles of all parts, directions); setup[dir * T + global triangle]
+__global__ void k_setup(const SPart *__restrict__ parts, const uint64_t *__restrict__ tofs, int nparts,
+                        uint64_t T, const int32_t *__restrict__ q, SState *__restrict__ st, const Views views,
+                        TriSetup *__restrict__ out) {
     const int dir = blockIdx.y;
     const View &V = views.v[dir];
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntris; t += gridDim.x * blockDim.x) {
-        if (tri[3ull * t] >= nverts || tri[3ull * t + 1] >= nverts || tri[3ull * t + 2] >= nverts) {
-            TriSetup bad{};
-            bad.ord = 0xffffffffu;
-            out[(uint64_t)dir * ntris + t] = bad;
-            if (dir == 0) atomicAdd(&st->badtri, 1u);
+    for (uint64_t tg = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; tg < T; tg += (uint64_t)gridDim.x * blockDim.x) {
+        const int p = find_part(tofs, nparts, tg);
+        const SPart &P = parts[p];
+        const uint32_t t = (uint32_t)(tg - P.tofs);
+        TriSetup s;
+        const uint32_t v0 = P.tri[3ull * t], v1 = P.tri[3ull * t + 1], v2 = P.tri[3ull * t + 2];
+        if (st[p].invalid || v0 >= P.nverts || v1 >= P.nverts || v2 >= P.nverts) {
+            s.ord = 0xffffffffu;
+            s.area2 = 0;
+            out[(uint64_t)dir * T + tg] = s;
+            if (!st[p].invalid && dir == 0) atomicAdd(&st[p].badtri, 1u);
             continue;
         }
+        const int32_t *qp = q + 3ull * P.vofs;
         int32_t X[3], Y[3];
         uint32_t W[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) project(V, views.res, q + 3ull * tri[3ull * t + i], X[i], Y[i], W[i]);
+        project(V, P.res, qp + 3ull * v0, X[0], Y[0], W[0]);
+        project(V, P.res, qp + 3ull * v1, X[1], Y[1], W[1]);
+        project(V, P.res, qp + 3ull * v2, X[2], Y[2], W[2]);
         int64_t a2 = (int64_t)(X[1] - X[0]) * (Y[2] - Y[0]) - (int64_t)(Y[1] - Y[0]) * (X[2] - X[0]);
         int o1 = 1, o2 = 2;
         if (a2 < 0) { o1 = 2; o2 = 1; a2 = -a2; }
-        TriSetup s;
         s.x[0] = X[0]; s.y[0] = Y[0]; s.w[0] = W[0];
         s.x[1] = X[o1]; s.y[1] = Y[o1]; s.w[1] = W[o1];
         s.x[2] = X[o2]; s.y[2] = Y[o2]; s.w[2] = W[o2];
         s.ord = a2 == 0 ? 0xffffffffu : (uint32_t)(0 | (o1 << 2) | (o2 << 4));
         s.area2 = a2;
-        out[(uint64_t)dir * ntris + t] = s;
+        out[(uint64_t)dir * T + tg] = s;
     }
 }
 
@@ -222,16 +275,19 @@ __device__ __forceinline__ void pixel_span(int32_t lo, int32_t hi, int res, int3
 }
 
 // One warp per (direction, triangle); lanes stride over the pixels of its screen bbox.
-__global__ void __launch_bounds__(256) k_raster(const TriSetup *__restrict__ setup, uint32_t ntris, int res,
-                                                const QuantState *st, unsigned long long *__restrict__ depth) {
-    if (st->invalid) return;
+__global__ void __launch_bounds__(256) k_raster(const SPart *__restrict__ parts, const uint64_t *__restrict__ tofs,
+                                                int nparts, uint64_t T, const TriSetup *__restrict__ setup,
+                                                unsigned long long *__restrict__ depth) {
     const int dir = blockIdx.y;
     const int lane = threadIdx.x & 31;
-    const uint32_t warps_per_grid = gridDim.x * (blockDim.x >> 5);
-    unsigned long long *dbuf = depth + (uint64_t)dir * res * res;
-    for (uint32_t t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < ntris; t += warps_per_grid) {
-        const TriSetup s = setup[(uint64_t)dir * ntris + t];
+    const uint64_t warps_per_grid = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t tg = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); tg < T; tg += warps_per_grid) {
+        const TriSetup s = setup[(uint64_t)dir * T + tg];
         if (s.ord == 0xffffffffu) continue;
+        const int p = find_part(tofs, nparts, tg);
+        const int res = parts[p].res;
+        const uint32_t t = (uint32_t)(tg - parts[p].tofs);
+        unsigned long long *dbuf = depth + parts[p].pofs + (uint64_t)dir * res * res;
         const int32_t xmin = min(s.x[0], min(s.x[1], s.x[2])), xmax = max(s.x[0], max(s.x[1], s.x[2]));
         const int32_t ymin = min(s.y[0], min(s.y[1], s.y[2])), ymax = max(s.y[0], max(s.y[1], s.y[2]));
         int32_t px0, px1, py0, py1;
@@ -240,8 +296,8 @@ __global__ void __launch_bounds__(256) k_raster(const TriSetup *__restrict__ set
         if (px1 < px0 || py1 < py0) continue;
         const uint32_t wdt = (uint32_t)(px1 - px0 + 1);
         const uint32_t npx = wdt * (uint32_t)(py1 - py0 + 1);
-        for (uint32_t p = lane; p < npx; p += 32) {
-            const int32_t py = py0 + (int32_t)(p / wdt), px = px0 + (int32_t)(p % wdt);
+        for (uint32_t pp = lane; pp < npx; pp += 32) {
+            const int32_t py = py0 + (int32_t)(pp / wdt), px = px0 + (int32_t)(pp % wdt);
             int64_t lam[3];
             if (!cover(s, px, py, lam)) continue;
             const uint64_t num = (uint64_t)lam[0] * s.w[0] + (uint64_t)lam[1] * s.w[1] + (uint64_t)lam[2] * s.w[2];
@@ -259,9 +315,8 @@ constexpr int TILE_WARPS = 8;
 constexpr int TILE_ROUNDS = 16;
 constexpr int TILE = TILE_WARPS * TILE_ROUNDS * 32;  // 4096
 
-__global__ void k_cover_count(const unsigned long long *__restrict__ depth, uint64_t npix, const QuantState *st,
+__global__ void k_cover_count(const unsigned long long *__restrict__ depth, uint64_t npix,
                               uint32_t *__restrict__ blockcnt) {
-    if (st->invalid) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t base = (uint64_t)blockIdx.x * TILE + (uint64_t)warp * TILE_ROUNDS * 32;
     uint32_t c = 0;
@@ -317,18 +372,90 @@ __global__ void __launch_bounds__(1024) k_scan_excl(uint32_t *a, uint32_t n, uin
     if (threadIdx.x == 0 && total) *total = carry;
 }
 
+// Multi-block exclusive scan: chunk sums, scan of the sums, chunk-local scans.
+constexpr uint32_t SCAN_CHUNK = 4096;
+
+__global__ void __launch_bounds__(1024) k_chunk_sum(const uint32_t *__restrict__ a, uint64_t n,
+                                                    uint32_t *__restrict__ sums) {
+    const uint64_t base = (uint64_t)blockIdx.x * SCAN_CHUNK;
+    uint32_t s = 0;
+    for (uint32_t r = threadIdx.x; r < SCAN_CHUNK; r += 1024)
+        if (base + r < n) s += a[base + r];
+    s = __reduce_add_sync(0xffffffffu, s);
+    __shared__ uint32_t ws[32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t v = ws[threadIdx.x];
+        v = __reduce_add_sync(0xffffffffu, v);
+        if (threadIdx.x == 0) sums[blockIdx.x] = v;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_chunk_scan(uint32_t *__restrict__ a, uint64_t n,
+                                                     const uint32_t *__restrict__ sums) {
+    __shared__ uint32_t ws[32];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = sums[blockIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t base0 = (uint64_t)blockIdx.x * SCAN_CHUNK;
+    for (uint32_t r0 = 0; r0 < SCAN_CHUNK; r0 += 1024) {
+        const uint64_t i = base0 + r0 + threadIdx.x;
+        const uint32_t v = i < n ? a[i] : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) ws[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t s = ws[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            ws[lane] = s;
+        }
+        __syncthreads();
+        const uint32_t before = carry + (warp ? ws[warp - 1] : 0u) + x - v;
+        if (i < n) a[i] = before;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = before + v;
+        __syncthreads();
+    }
+}
+
+// Exclusive scan of a[0..n) in place (total to *total); tmp holds n / SCAN_CHUNK + 1 words.
+static void scan_excl(uint32_t *a, uint64_t n, uint32_t *total, uint32_t *tmp, cudaStream_t stream) {
+    if (n <= 65536) {
+        k_scan_excl<<<1, 1024, 0, stream>>>(a, (uint32_t)n, total);
+        return;
+    }
+    const uint32_t nch = (uint32_t)((n + SCAN_CHUNK - 1) / SCAN_CHUNK);
+    k_chunk_sum<<<nch, 1024, 0, stream>>>(a, n, tmp);
+    k_scan_excl<<<1, 1024, 0, stream>>>(tmp, nch, total);
+    k_chunk_scan<<<nch, 1024, 0, stream>>>(a, n, tmp);
+}
+
+static size_t scan_tmp_words(uint64_t n) { return (size_t)(n / SCAN_CHUNK + 2); }
+
 struct Rows {
     uint64_t *morton;
     uint64_t *key;
     uint64_t *nrm;  // 3 x int16 packed little-endian in the low 48 bits
     uint32_t *rgb;  // 3 bytes packed
     uint32_t *e;
+    uint32_t *part;
     uint32_t *idx;
 };
 
 // Resolve one covered pixel of direction dir: integer barycentric interpolation of
 // the quantised vertices (floor), normal of the triangle turned toward the camera
-// (snorm16, round half to even), face colour, Morton code.
+// (snorm16, round half to even), face colour.
 __device__ void resolve_pixel(const View &V, const TriSetup &s, const int32_t *__restrict__ q,
                               const uint32_t *__restrict__ tri, const uint8_t *__restrict__ rgb, uint32_t t,
                               int32_t px, int32_t py, uint64_t &key, uint64_t &nrm_packed, uint32_t &rgb_packed) {
@@ -372,12 +499,11 @@ __device__ void resolve_pixel(const View &V, const TriSetup &s, const int32_t *_
                      : 0u;
 }
 
-__global__ void __launch_bounds__(256) k_resolve(const unsigned long long *__restrict__ depth, uint64_t npix, int res,
-                                                 const int32_t *__restrict__ q, const uint32_t *__restrict__ tri,
-                                                 const uint8_t *__restrict__ rgb, const TriSetup *__restrict__ setup,
-                                                 uint32_t ntris, const Views views, const QuantState *st,
+__global__ void __launch_bounds__(256) k_resolve(const unsigned long long *__restrict__ depth, uint64_t npix,
+                                                 const SPart *__restrict__ parts, const uint64_t *__restrict__ pofs,
+                                                 int nparts, uint64_t T, const int32_t *__restrict__ q,
+                                                 const TriSetup *__restrict__ setup, const Views views,
                                                  const uint32_t *__restrict__ blockofs, Rows rows) {
-    if (st->invalid) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t base = (uint64_t)blockIdx.x * TILE + (uint64_t)warp * TILE_ROUNDS * 32;
     __shared__ uint32_t wc[TILE_WARPS];
@@ -391,7 +517,6 @@ __global__ void __launch_bounds__(256) k_resolve(const unsigned long long *__res
     __syncthreads();
     uint32_t out = blockofs[blockIdx.x];
     for (int w = 0; w < warp; ++w) out += wc[w];
-    const uint64_t res2 = (uint64_t)res * res;
     for (int r = 0; r < TILE_ROUNDS; ++r) {
         const uint64_t i = base + (uint64_t)r * 32 + lane;
         const unsigned long long dv = i < npix ? depth[i] : ~0ull;
@@ -399,19 +524,24 @@ __global__ void __launch_bounds__(256) k_resolve(const unsigned long long *__res
         const uint32_t m = __ballot_sync(0xffffffffu, hit);
         if (hit) {
             const uint32_t o = out + __popc(m & ((1u << lane) - 1u));
-            const int dir = (int)(i / res2);
-            const uint64_t pix = i - (uint64_t)dir * res2;
-            const int32_t py = (int32_t)(pix / res), px = (int32_t)(pix % res);
+            const int p = find_part(pofs, nparts, i);
+            const SPart &P = parts[p];
+            const uint64_t res2 = (uint64_t)P.res * P.res;
+            const uint64_t local = i - P.pofs;
+            const int dir = (int)(local / res2);
+            const uint64_t pix = local - (uint64_t)dir * res2;
+            const int32_t py = (int32_t)(pix / P.res), px = (int32_t)(pix % P.res);
             const uint32_t t = (uint32_t)(dv & 0xffffffffull);
-            const TriSetup s = setup[(uint64_t)dir * ntris + t];
+            const TriSetup s = setup[(uint64_t)dir * T + P.tofs + t];
             uint64_t key, np;
             uint32_t cp;
-            resolve_pixel(views.v[dir], s, q, tri, rgb, t, px, py, key, np, cp);
+            resolve_pixel(views.v[dir], s, q + 3ull * P.vofs, P.tri, P.rgb, t, px, py, key, np, cp);
             rows.morton[o] = morton_of(key);
             rows.key[o] = key;
             rows.nrm[o] = np;
             rows.rgb[o] = cp;
-            rows.e[o] = (uint32_t)i;
+            rows.e[o] = (uint32_t)local;
+            rows.part[o] = (uint32_t)p;
             rows.idx[o] = o;
         }
         out += __popc(m);
@@ -461,7 +591,6 @@ __global__ void __launch_bounds__(256) k_rs_scatter(const uint64_t *__restrict__
         __syncwarp();
     }
     __syncthreads();
-    // exclusive prefix over warps for each digit
     {
         const int d = threadIdx.x;
         uint32_t run = 0;
@@ -484,36 +613,47 @@ __global__ void __launch_bounds__(256) k_rs_scatter(const uint64_t *__restrict__
     }
 }
 
-// Sorts (keys, vals) by the low `bits` bits of keys; bits must be a multiple of 8
-// and the number of passes even, so the result ends in (keys, vals).
-static bs_status radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *ktmp, uint32_t *vtmp, uint32_t n, int bits,
-                            uint32_t *counts, cudaStream_t stream) {
-    if (n == 0) return BS_OK;
+// Sorts (keys, vals) by the low `bits` bits of keys (bits a multiple of 16, so the
+// number of passes is even and the result ends in (keys, vals)).
+static void radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *ktmp, uint32_t *vtmp, uint32_t n, int bits,
+                       uint32_t *counts, uint32_t *scan_tmp, cudaStream_t stream) {
+    if (n == 0) return;
     const uint32_t ntiles = (n + TILE - 1) / TILE;
     uint64_t *ka = keys, *kb = ktmp;
     uint32_t *va = vals, *vb = vtmp;
     for (int shift = 0; shift < bits; shift += 8) {
         k_rs_hist<<<ntiles, 256, 0, stream>>>(ka, n, shift, counts, ntiles);
-        k_scan_excl<<<1, 1024, 0, stream>>>(counts, 256u * ntiles, nullptr);
+        scan_excl(counts, 256ull * ntiles, nullptr, scan_tmp, stream);
         k_rs_scatter<<<ntiles, 256, 0, stream>>>(ka, va, kb, vb, n, shift, counts, ntiles);
-        BS_CHECK_LAUNCH();
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
     }
-    return BS_OK;
+}
+
+// part id of each sorted row as a sort key
+__global__ void k_part_keys(const uint32_t *__restrict__ idx, const uint32_t *__restrict__ part, uint32_t n,
+                            uint64_t *__restrict__ out) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = part[idx[i]];
 }
 
 // ---------------------------------------------------------------------------
-// Dedup: keep the first row of each Morton code (rows are stable-sorted by Morton
-// code and were emitted in increasing e, so the first row has the smallest e).
+// Merge: keep the first row of each (part, Morton code).  Rows are stable-sorted by
+// (part, Morton) and were emitted in increasing e, so the first has the smallest e.
 // ---------------------------------------------------------------------------
-__global__ void k_unique_count(const uint64_t *__restrict__ m, uint32_t n, uint32_t *__restrict__ blockcnt) {
+__device__ __forceinline__ bool keep_row(const uint32_t *__restrict__ idx, const Rows &rows, uint64_t i) {
+    if (i == 0) return true;
+    const uint32_t a = idx[i], b = idx[i - 1];
+    return rows.morton[a] != rows.morton[b] || rows.part[a] != rows.part[b];
+}
+
+__global__ void k_unique_count(const uint32_t *__restrict__ idx, Rows rows, uint32_t n,
+                               uint32_t *__restrict__ blockcnt) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t base = (uint64_t)blockIdx.x * TILE + (uint64_t)warp * TILE_ROUNDS * 32;
     uint32_t c = 0;
     for (int r = 0; r < TILE_ROUNDS; ++r) {
         const uint64_t i = base + (uint64_t)r * 32 + lane;
-        c += (i < n && (i == 0 || m[i] != m[i - 1])) ? 1u : 0u;
+        c += (i < n && keep_row(idx, rows, i)) ? 1u : 0u;
     }
     c = __reduce_add_sync(0xffffffffu, c);
     __shared__ uint32_t wc[TILE_WARPS];
@@ -526,18 +666,19 @@ __global__ void k_unique_count(const uint64_t *__restrict__ m, uint32_t n, uint3
     }
 }
 
-__global__ void k_unique_write(const uint64_t *__restrict__ m, const uint32_t *__restrict__ idx, uint32_t n,
-                               const uint32_t *__restrict__ blockofs, const uint32_t *__restrict__ total,
-                               uint64_t cap, Rows rows, uint64_t *__restrict__ okey, int16_t *__restrict__ onrm,
-                               uint8_t *__restrict__ orgb, uint32_t *__restrict__ osrc) {
-    if ((uint64_t)*total > cap) return;
+// mode 0: record each part's [first_out, end_out); mode 1: write the kept rows of
+// parts that fit their capacity
+template <int MODE>
+__global__ void k_unique_pass(const uint32_t *__restrict__ idx, Rows rows, uint32_t n,
+                              const uint32_t *__restrict__ blockofs, const SPart *__restrict__ parts,
+                              SState *__restrict__ st) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t base = (uint64_t)blockIdx.x * TILE + (uint64_t)warp * TILE_ROUNDS * 32;
     __shared__ uint32_t wc[TILE_WARPS];
     uint32_t c = 0;
     for (int r = 0; r < TILE_ROUNDS; ++r) {
         const uint64_t i = base + (uint64_t)r * 32 + lane;
-        c += (i < n && (i == 0 || m[i] != m[i - 1])) ? 1u : 0u;
+        c += (i < n && keep_row(idx, rows, i)) ? 1u : 0u;
     }
     c = __reduce_add_sync(0xffffffffu, c);
     if (lane == 0) wc[warp] = c;
@@ -546,25 +687,36 @@ __global__ void k_unique_write(const uint64_t *__restrict__ m, const uint32_t *_
     for (int w = 0; w < warp; ++w) out += wc[w];
     for (int r = 0; r < TILE_ROUNDS; ++r) {
         const uint64_t i = base + (uint64_t)r * 32 + lane;
-        const bool keep = i < n && (i == 0 || m[i] != m[i - 1]);
+        const bool keep = i < n && keep_row(idx, rows, i);
         const uint32_t msk = __ballot_sync(0xffffffffu, keep);
-        if (keep) {
-            const uint32_t o = out + __popc(msk & ((1u << lane) - 1u));
+        const uint32_t o = out + __popc(msk & ((1u << lane) - 1u));
+        if (i < n) {
             const uint32_t row = idx[i];
-            okey[o] = rows.key[row];
-            if (onrm) {
-                const uint64_t np = rows.nrm[row];
-                onrm[3ull * o + 0] = (int16_t)(uint16_t)(np & 0xffffu);
-                onrm[3ull * o + 1] = (int16_t)(uint16_t)((np >> 16) & 0xffffu);
-                onrm[3ull * o + 2] = (int16_t)(uint16_t)((np >> 32) & 0xffffu);
+            const uint32_t p = rows.part[row];
+            if (MODE == 0) {
+                if (i == 0 || rows.part[idx[i - 1]] != p) st[p].first_out = o;
+                if (i == n - 1 || rows.part[idx[i + 1]] != p) st[p].end_out = (uint64_t)o + (keep ? 1u : 0u);
+            } else if (keep) {
+                const SPart &P = parts[p];
+                const uint64_t cnt = st[p].end_out - st[p].first_out;
+                if (cnt <= P.cap) {
+                    const uint64_t w = (uint64_t)o - st[p].first_out;
+                    P.okey[w] = rows.key[row];
+                    if (P.onrm) {
+                        const uint64_t np = rows.nrm[row];
+                        P.onrm[3 * w + 0] = (int16_t)(uint16_t)(np & 0xffffu);
+                        P.onrm[3 * w + 1] = (int16_t)(uint16_t)((np >> 16) & 0xffffu);
+                        P.onrm[3 * w + 2] = (int16_t)(uint16_t)((np >> 32) & 0xffffu);
+                    }
+                    if (P.orgb) {
+                        const uint32_t cp = rows.rgb[row];
+                        P.orgb[3 * w + 0] = (uint8_t)(cp & 0xffu);
+                        P.orgb[3 * w + 1] = (uint8_t)((cp >> 8) & 0xffu);
+                        P.orgb[3 * w + 2] = (uint8_t)((cp >> 16) & 0xffu);
+                    }
+                    if (P.osrc) P.osrc[w] = rows.e[row];
+                }
             }
-            if (orgb) {
-                const uint32_t cp = rows.rgb[row];
-                orgb[3ull * o + 0] = (uint8_t)(cp & 0xffu);
-                orgb[3ull * o + 1] = (uint8_t)((cp >> 8) & 0xffu);
-                orgb[3ull * o + 2] = (uint8_t)((cp >> 16) & 0xffu);
-            }
-            if (osrc) osrc[o] = rows.e[row];
         }
         out += __popc(msk);
     }
@@ -575,17 +727,33 @@ __global__ void k_unique_write(const uint64_t *__restrict__ m, const uint32_t *_
 // ---------------------------------------------------------------------------
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
-bs_status sample_visible(const bs_mesh *mesh, const bs_dir *dirs, int ndirs, int res, bs_surfels *out,
-                         cudaStream_t stream) {
-    if (!mesh || !dirs || !out) { set_error("bs_sample_visible: NULL argument"); return BS_EINVAL; }
+struct Scratch {
+    char *base = nullptr;
+    size_t off = 0;
+    char *take(size_t bytes) {
+        char *p = base + off;
+        off = align_up(off + bytes);
+        return p;
+    }
+};
+
+static bs_status alloc_async(char **p, size_t bytes, cudaStream_t stream, const char *what) {
+    cudaError_t e = cudaMallocAsync((void **)p, bytes ? bytes : 256, stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("bs_sample_visible: %s scratch allocation of %zu bytes failed: %s", what, bytes, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? BS_ENOMEM : BS_ECUDA;
+    }
+    return BS_OK;
+}
+
+bs_status sample_visible_parts(const bs_mesh *meshes, const int *res, int nparts, const bs_dir *dirs, int ndirs,
+                               bs_surfels *out, cudaStream_t stream) {
+    if (nparts < 1 || nparts > 65535) { set_error("bs_sample_visible: nparts=%d outside [1, 65535]", nparts); return BS_EINVAL; }
+    if (!meshes || !res || !dirs || !out) { set_error("bs_sample_visible: NULL argument"); return BS_EINVAL; }
     if (ndirs < 1 || ndirs > BS_MAX_DIRS) { set_error("bs_sample_visible: ndirs=%d outside [1,%d]", ndirs, BS_MAX_DIRS); return BS_EINVAL; }
-    if (res < 1 || res > BS_MAX_RES) { set_error("bs_sample_visible: res=%d outside [1,%d]", res, BS_MAX_RES); return BS_EINVAL; }
-    if (mesh->nverts == 0 || !mesh->xyz) { set_error("bs_sample_visible: empty mesh"); return BS_EINVAL; }
-    if (mesh->ntris > 0 && !mesh->tri) { set_error("bs_sample_visible: NULL triangle array"); return BS_EINVAL; }
-    if (out->cap > 0 && !out->key) { set_error("bs_sample_visible: NULL key output"); return BS_EINVAL; }
     Views views;
     views.ndirs = ndirs;
-    views.res = res;
     for (int i = 0; i < ndirs; ++i) {
         const bs_dir &d = dirs[i];
         const bool okc = d.x >= -1 && d.x <= 1 && d.y >= -1 && d.y <= 1 && d.z >= -1 && d.z <= 1;
@@ -595,124 +763,190 @@ bs_status sample_visible(const bs_mesh *mesh, const bs_dir *dirs, int ndirs, int
         }
         make_frame(d, views.v[i]);
     }
-    const uint32_t nv = mesh->nverts, nt = mesh->ntris;
-    const uint64_t npix = (uint64_t)ndirs * res * res;
-    if (npix >= (1ull << 32)) { set_error("bs_sample_visible: too many pixels"); return BS_EINVAL; }
-    const uint32_t ptiles = (uint32_t)((npix + TILE - 1) / TILE);
-    const uint32_t rs_tiles_max = ptiles;
-
-    // scratch layout
-    size_t off = 0;
-    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
-    const size_t o_st = take(sizeof(QuantState));
-    const size_t o_q = take(3ull * nv * sizeof(int32_t));
-    const size_t o_setup = take((size_t)ndirs * nt * sizeof(TriSetup));
-    const size_t o_depth = take(npix * sizeof(unsigned long long));
-    const size_t o_bc = take(((size_t)ptiles + 1) * sizeof(uint32_t));
-    const size_t o_tot = take(4 * sizeof(uint32_t));
-    const size_t o_cnt = take(256ull * rs_tiles_max * sizeof(uint32_t));
-    // rows (capacity npix; only `rows` of them used)
-    const size_t o_m = take(npix * 8), o_k = take(npix * 8), o_n = take(npix * 8);
-    const size_t o_c = take(npix * 4), o_e = take(npix * 4), o_i = take(npix * 4);
-    const size_t o_m2 = take(npix * 8), o_i2 = take(npix * 4);
-    char *ws = nullptr;
-    {
-        cudaError_t e = cudaMallocAsync((void **)&ws, off, stream);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            set_error("bs_sample_visible: scratch allocation of %zu bytes failed: %s", off, cudaGetErrorString(e));
-            return e == cudaErrorMemoryAllocation ? BS_ENOMEM : BS_ECUDA;
-        }
+    std::vector<SPart> hp((size_t)nparts);
+    std::vector<uint64_t> tofs((size_t)nparts), pofs((size_t)nparts);
+    uint64_t V = 0, T = 0, NP = 0;
+    for (int p = 0; p < nparts; ++p) {
+        const bs_mesh &m = meshes[p];
+        if (res[p] < 1 || res[p] > BS_MAX_RES) { set_error("bs_sample_visible: part %d: res=%d outside [1,%d]", p, res[p], BS_MAX_RES); return BS_EINVAL; }
+        if (m.nverts == 0 || !m.xyz) { set_error("bs_sample_visible: part %d: empty mesh", p); return BS_EINVAL; }
+        if (m.ntris > 0 && !m.tri) { set_error("bs_sample_visible: part %d: NULL triangle array", p); return BS_EINVAL; }
+        if (out[p].cap > 0 && !out[p].key) { set_error("bs_sample_visible: part %d: NULL key output", p); return BS_EINVAL; }
+        SPart &P = hp[(size_t)p];
+        P.xyz = m.xyz; P.tri = m.tri; P.rgb = m.face_rgb;
+        P.okey = out[p].key; P.onrm = out[p].nrm; P.orgb = out[p].rgb; P.osrc = out[p].src;
+        P.cap = out[p].cap;
+        P.nverts = m.nverts; P.ntris = m.ntris; P.res = res[p]; P.pad = 0;
+        P.vofs = V; P.tofs = T; P.pofs = NP;
+        tofs[(size_t)p] = T;
+        pofs[(size_t)p] = NP;
+        V += m.nverts;
+        T += m.ntris;
+        NP += (uint64_t)ndirs * res[p] * res[p];
     }
-    bs_status rc = BS_OK;
-    QuantState *st = (QuantState *)(ws + o_st);
-    int32_t *q = (int32_t *)(ws + o_q);
-    TriSetup *setup = (TriSetup *)(ws + o_setup);
-    unsigned long long *depth = (unsigned long long *)(ws + o_depth);
-    uint32_t *bc = (uint32_t *)(ws + o_bc);
-    uint32_t *tot = (uint32_t *)(ws + o_tot);
-    uint32_t *cnt = (uint32_t *)(ws + o_cnt);
-    Rows rows{(uint64_t *)(ws + o_m), (uint64_t *)(ws + o_k), (uint64_t *)(ws + o_n),
-              (uint32_t *)(ws + o_c), (uint32_t *)(ws + o_e), (uint32_t *)(ws + o_i)};
-    QuantState h{};
-    int sms = 152;
+    if (NP >= (1ull << 32)) { set_error("bs_sample_visible: %llu pixels in one call (limit 2^32)", (unsigned long long)NP); return BS_EINVAL; }
+    const uint32_t ptiles = (uint32_t)((NP + TILE - 1) / TILE);
+    int sms = 152, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+
+    // ---- phase 1: quantise, set up, raster, count covered pixels ----
+    Scratch A;
+    size_t a_bytes = 0;
+    {
+        Scratch probe;
+        probe.take((size_t)nparts * sizeof(SPart));
+        probe.take((size_t)nparts * sizeof(SState));
+        probe.take((size_t)nparts * 8);
+        probe.take((size_t)nparts * 8);
+        probe.take(3 * V * sizeof(int32_t));
+        probe.take((size_t)ndirs * T * sizeof(TriSetup));
+        probe.take(NP * sizeof(unsigned long long));
+        probe.take(((size_t)ptiles + 1) * 4);
+        probe.take(scan_tmp_words(ptiles) * 4);
+        probe.take(16);
+        a_bytes = probe.off;
+    }
+    bs_status rc = alloc_async(&A.base, a_bytes, stream, "raster");
+    if (rc != BS_OK) return rc;
+    SPart *d_parts = (SPart *)A.take((size_t)nparts * sizeof(SPart));
+    SState *d_st = (SState *)A.take((size_t)nparts * sizeof(SState));
+    uint64_t *d_tofs = (uint64_t *)A.take((size_t)nparts * 8);
+    uint64_t *d_pofs = (uint64_t *)A.take((size_t)nparts * 8);
+    int32_t *q = (int32_t *)A.take(3 * V * sizeof(int32_t));
+    TriSetup *setup = (TriSetup *)A.take((size_t)ndirs * T * sizeof(TriSetup));
+    unsigned long long *depth = (unsigned long long *)A.take(NP * sizeof(unsigned long long));
+    uint32_t *bc = (uint32_t *)A.take(((size_t)ptiles + 1) * 4);
+    uint32_t *stmp = (uint32_t *)A.take(scan_tmp_words(ptiles) * 4);
+    uint32_t *tot = (uint32_t *)A.take(16);
+    char *B = nullptr;
+    std::vector<SState> hs((size_t)nparts);
+    uint32_t nrows = 0;
     do {
-        {
-            int dev = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        }
-        QuantState init{};
-        for (int a = 0; a < 3; ++a) { init.mn_ord[a] = 0xffffffffu; init.mx_ord[a] = 0u; }
-        if ((rc = cudaMemcpyAsync(st, &init, sizeof(init), cudaMemcpyHostToDevice, stream) == cudaSuccess ? BS_OK : BS_ECUDA)) {
-            set_error("bs_sample_visible: state upload failed");
+        if (cudaMemcpyAsync(d_parts, hp.data(), (size_t)nparts * sizeof(SPart), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+            cudaMemcpyAsync(d_tofs, tofs.data(), (size_t)nparts * 8, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+            cudaMemcpyAsync(d_pofs, pofs.data(), (size_t)nparts * 8, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+            cudaMemsetAsync(depth, 0xff, NP * sizeof(unsigned long long), stream) != cudaSuccess ||
+            cudaMemsetAsync(tot, 0, 16, stream) != cudaSuccess) {
+            set_error("bs_sample_visible: upload failed: %s", cudaGetErrorString(cudaGetLastError()));
+            rc = BS_ECUDA;
             break;
         }
-        const int gb = (int)std::min<uint64_t>((nv + 255) / 256, (uint64_t)sms * 8);
-        k_bbox<<<gb, 256, 0, stream>>>(mesh->xyz, nv, st);
-        k_scale<<<1, 1, 0, stream>>>(st);
-        k_quantise<<<(int)std::min<uint64_t>((3ull * nv + 255) / 256, (uint64_t)sms * 16), 256, 0, stream>>>(mesh->xyz, nv, st, q);
-        if (cudaMemsetAsync(depth, 0xff, npix * sizeof(unsigned long long), stream) != cudaSuccess) {
-            rc = BS_ECUDA; set_error("bs_sample_visible: memset failed"); break;
+        k_bbox<<<nparts, 256, 0, stream>>>(d_parts, d_st);
+        k_quantise<<<nparts, 256, 0, stream>>>(d_parts, d_st, q);
+        if (T > 0) {
+            dim3 gs((unsigned)std::min<uint64_t>((T + 255) / 256, (uint64_t)sms * 32), ndirs);
+            k_setup<<<gs, 256, 0, stream>>>(d_parts, d_tofs, nparts, T, q, d_st, views, setup);
+            dim3 gr((unsigned)std::min<uint64_t>((T + 7) / 8, (uint64_t)sms * 64), ndirs);
+            k_raster<<<gr, 256, 0, stream>>>(d_parts, d_tofs, nparts, T, setup, depth);
         }
-        if (nt > 0) {
-            dim3 gs((unsigned)std::min<uint64_t>((nt + 255) / 256, 4096), ndirs);
-            k_setup<<<gs, 256, 0, stream>>>(q, mesh->tri, nt, nv, st, views, setup);
-            dim3 gr((unsigned)std::min<uint64_t>((nt + 7) / 8, (uint64_t)sms * 64), ndirs);
-            k_raster<<<gr, 256, 0, stream>>>(setup, nt, res, st, depth);
-        }
-        k_cover_count<<<ptiles, 256, 0, stream>>>(depth, npix, st, bc);
-        k_scan_excl<<<1, 1024, 0, stream>>>(bc, ptiles, tot + 0);
-        k_resolve<<<ptiles, 256, 0, stream>>>(depth, npix, res, q, mesh->tri, mesh->face_rgb, setup, nt, views, st, bc, rows);
-        if ((rc = cudaGetLastError() == cudaSuccess ? BS_OK : BS_ECUDA)) { set_error("bs_sample_visible: launch failed"); break; }
-        // number of rows is needed on the host to size the sort
-        uint32_t nrows = 0;
-        if (cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
-            cudaMemcpyAsync(&nrows, tot, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        k_cover_count<<<ptiles, 256, 0, stream>>>(depth, NP, bc);
+        scan_excl(bc, ptiles, tot, stmp, stream);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(&nrows, tot, 4, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
             cudaStreamSynchronize(stream) != cudaSuccess) {
-            rc = BS_ECUDA; set_error("bs_sample_visible: readback failed: %s", cudaGetErrorString(cudaGetLastError()));
+            set_error("bs_sample_visible: raster phase failed: %s", cudaGetErrorString(cudaGetLastError()));
+            rc = BS_ECUDA;
             break;
         }
-        if (h.badtri) {
-            rc = BS_EINVAL;
-            set_error("bs_sample_visible: %u triangles reference a vertex index >= nverts", h.badtri);
-            break;
-        }
-        if (h.invalid) {
-            rc = BS_EINVAL;
-            set_error(h.nonfinite ? "bs_sample_visible: non-finite vertex coordinate" : "bs_sample_visible: mesh has zero extent");
-            break;
-        }
-        if (h.invalid == 0 && nrows > 0) {
-            if ((rc = radix_sort(rows.morton, rows.idx, (uint64_t *)(ws + o_m2), (uint32_t *)(ws + o_i2), nrows, 64, cnt, stream)) != BS_OK) break;
-            const uint32_t utiles = (nrows + TILE - 1) / TILE;
-            k_unique_count<<<utiles, 256, 0, stream>>>(rows.morton, nrows, bc);
-            k_scan_excl<<<1, 1024, 0, stream>>>(bc, utiles, tot + 1);
-            k_unique_write<<<utiles, 256, 0, stream>>>(rows.morton, rows.idx, nrows, bc, tot + 1, out->cap, rows,
-                                                       out->key, out->nrm, out->rgb, out->src);
-            if ((rc = cudaGetLastError() == cudaSuccess ? BS_OK : BS_ECUDA)) { set_error("bs_sample_visible: launch failed"); break; }
-        }
-        uint32_t nout = 0;
+        // ---- phase 2: resolve, sort, merge, write ----
         if (nrows > 0) {
-            if (cudaMemcpyAsync(&nout, tot + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
-                cudaStreamSynchronize(stream) != cudaSuccess) {
-                rc = BS_ECUDA; set_error("bs_sample_visible: readback failed"); break;
+            const uint32_t rtiles = (nrows + TILE - 1) / TILE;
+            Scratch Bs;
+            {
+                Scratch probe;
+                for (int i = 0; i < 3; ++i) probe.take((size_t)nrows * 8);          // morton, key, nrm
+                for (int i = 0; i < 4; ++i) probe.take((size_t)nrows * 4);          // rgb, e, part, idx
+                probe.take((size_t)nrows * 8);                                      // sort key temp
+                probe.take((size_t)nrows * 4);                                      // sort value temp
+                probe.take((size_t)nrows * 8);                                      // part keys
+                probe.take(256ull * rtiles * 4);                                    // digit counts
+                probe.take(scan_tmp_words(256ull * rtiles) * 4);
+                probe.take(((size_t)rtiles + 1) * 4);
+                rc = alloc_async(&B, probe.off, stream, "merge");
+                if (rc != BS_OK) break;
+                Bs.base = B;
+            }
+            Rows rows;
+            rows.morton = (uint64_t *)Bs.take((size_t)nrows * 8);
+            rows.key = (uint64_t *)Bs.take((size_t)nrows * 8);
+            rows.nrm = (uint64_t *)Bs.take((size_t)nrows * 8);
+            rows.rgb = (uint32_t *)Bs.take((size_t)nrows * 4);
+            rows.e = (uint32_t *)Bs.take((size_t)nrows * 4);
+            rows.part = (uint32_t *)Bs.take((size_t)nrows * 4);
+            rows.idx = (uint32_t *)Bs.take((size_t)nrows * 4);
+            uint64_t *ktmp = (uint64_t *)Bs.take((size_t)nrows * 8);
+            uint32_t *vtmp = (uint32_t *)Bs.take((size_t)nrows * 4);
+            uint64_t *pkey = (uint64_t *)Bs.take((size_t)nrows * 8);
+            uint32_t *cnt = (uint32_t *)Bs.take(256ull * rtiles * 4);
+            uint32_t *cnt_tmp = (uint32_t *)Bs.take(scan_tmp_words(256ull * rtiles) * 4);
+            uint32_t *ubc = (uint32_t *)Bs.take(((size_t)rtiles + 1) * 4);
+            k_resolve<<<ptiles, 256, 0, stream>>>(depth, NP, d_parts, d_pofs, nparts, T, q, setup, views, bc, rows);
+            // stable: by Morton code, then by part (rows of one part stay in Morton order)
+            uint32_t *sorted_idx = rows.idx;
+            {
+                // sort a copy of the Morton codes so rows.morton stays indexable by row
+                cudaMemcpyAsync(pkey, rows.morton, (size_t)nrows * 8, cudaMemcpyDeviceToDevice, stream);
+                radix_sort(pkey, sorted_idx, ktmp, vtmp, nrows, 64, cnt, cnt_tmp, stream);
+                if (nparts > 1) {
+                    k_part_keys<<<(unsigned)std::min<uint64_t>((nrows + 255) / 256, (uint64_t)sms * 32), 256, 0, stream>>>(
+                        sorted_idx, rows.part, nrows, pkey);
+                    radix_sort(pkey, sorted_idx, ktmp, vtmp, nrows, 16, cnt, cnt_tmp, stream);
+                }
+            }
+            k_unique_count<<<rtiles, 256, 0, stream>>>(sorted_idx, rows, nrows, ubc);
+            scan_excl(ubc, rtiles, tot + 1, cnt_tmp, stream);
+            k_unique_pass<0><<<rtiles, 256, 0, stream>>>(sorted_idx, rows, nrows, ubc, d_parts, d_st);
+            k_unique_pass<1><<<rtiles, 256, 0, stream>>>(sorted_idx, rows, nrows, ubc, d_parts, d_st);
+        }
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(hs.data(), d_st, (size_t)nparts * sizeof(SState), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+            cudaStreamSynchronize(stream) != cudaSuccess) {
+            set_error("bs_sample_visible: merge phase failed: %s", cudaGetErrorString(cudaGetLastError()));
+            rc = BS_ECUDA;
+            break;
+        }
+        for (int p = 0; p < nparts && rc == BS_OK; ++p) {
+            const SState &S = hs[(size_t)p];
+            out[p].n = S.end_out - S.first_out;
+            for (int a = 0; a < 3; ++a) out[p].bbox_min[a] = S.mn[a];
+            out[p].scale = S.scale;
+        }
+        for (int p = 0; p < nparts; ++p) {
+            const SState &S = hs[(size_t)p];
+            if (S.invalid) {
+                out[p].n = 0;
+                set_error(S.nonfinite ? "bs_sample_visible: part %d: non-finite vertex coordinate"
+                                      : "bs_sample_visible: part %d: mesh has zero extent", p);
+                rc = BS_EINVAL;
+                break;
+            }
+            if (S.badtri) {
+                out[p].n = 0;
+                set_error("bs_sample_visible: part %d: %u triangles reference a vertex index >= nverts", p, S.badtri);
+                rc = BS_EINVAL;
+                break;
             }
         }
-        out->n = nout;
-        for (int a = 0; a < 3; ++a) out->bbox_min[a] = h.mn[a];
-        out->scale = h.scale;
-        if ((uint64_t)nout > out->cap) {
-            rc = BS_EOVERFLOW;
-            set_error("bs_sample_visible: %u surfels exceed capacity %llu", nout, (unsigned long long)out->cap);
+        if (rc == BS_OK) {
+            for (int p = 0; p < nparts; ++p)
+                if (out[p].n > out[p].cap) {
+                    set_error("bs_sample_visible: part %d: %llu surfels exceed capacity %llu", p,
+                              (unsigned long long)out[p].n, (unsigned long long)out[p].cap);
+                    rc = BS_EOVERFLOW;
+                    break;
+                }
         }
     } while (0);
-    cudaFreeAsync(ws, stream);
-    if (rc == BS_OK) {
-        cudaError_t e = cudaStreamSynchronize(stream);
-        if (e != cudaSuccess) { set_error("bs_sample_visible: %s", cudaGetErrorString(e)); rc = BS_ECUDA; }
-    }
+    if (B) cudaFreeAsync(B, stream);
+    cudaFreeAsync(A.base, stream);
     return rc;
+}
+
+bs_status sample_visible(const bs_mesh *mesh, const bs_dir *dirs, int ndirs, int res, bs_surfels *out,
+                         cudaStream_t stream) {
+    if (!mesh || !dirs || !out) { set_error("bs_sample_visible: NULL argument"); return BS_EINVAL; }
+    return sample_visible_parts(mesh, &res, 1, dirs, ndirs, out, stream);
 }
 
 }  // namespace bs

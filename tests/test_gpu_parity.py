@@ -302,3 +302,64 @@ def test_server_budget_admission(bs):
     for i, k in enumerate(keys):
         rp, rr = oracle.greedy(k, oracle.start_index(len(k), seed=i))
         assert np.array_equal(out[i][0], rp)
+
+
+@pytest.mark.parametrize("algo", [1, 2])
+def test_order_both_algorithms_match_oracle(bs, algo):
+    """One pick per step and exact multi-pick rounds give the same (oracle) ordering,
+    including regular-grid ties and duplicate positions."""
+    g = np.random.default_rng(12)
+    cases = []
+    m = W.torus(nu=64, nv=32)
+    ref, mn, s = oracle.sample_mesh(m, W.AXIS_DIRS, 96)
+    cases.append((ref["key"], -1, 5))
+    n1 = 40
+    X, Y = np.meshgrid(np.arange(n1), np.arange(n1), indexing="ij")
+    grid = np.stack([X.ravel() * 64, Y.ravel() * 64, np.full(n1 * n1, 77)], -1)
+    cases.append((oracle.pack(grid[np.argsort([oracle.morton3(*map(int, p)) for p in grid], kind="stable")]), 0, 0))
+    pts = g.integers(0, 300, size=(5000, 3))
+    pts[1000:1500] = pts[0:500]
+    cases.append((oracle.pack(pts), 3, 1))
+    try:
+        bs.set_tuning("order_algo", algo)
+        for key_np, start, seed in cases:
+            _check_order(bs, key_np, start=start, seed=seed)
+            k = _dev(key_np.view(np.int64))
+            batched = bs.order_batched([k, k[: len(key_np) // 3]], starts=[start, -1], seeds=[seed, seed])
+            single = bs.order(k, start=start, seed=seed)
+            assert torch.equal(batched[0][0], single[0]) and torch.equal(batched[0][1], single[1])
+    finally:
+        bs.set_tuning("order_algo", 2)
+
+
+def test_sample_batched_matches_oracle_per_part(bs):
+    """Many meshes in one bs_sample_visible_batched call: each part's surfels equal the
+    oracle's for that part alone (different sizes, resolutions, colours or none)."""
+    meshes = [W.torus(nu=48, nv=24, seed=1), W.cad_part(seed=3, nboxes=40, ncyl=10), W.torus(nu=16, nv=8),
+              W.cube(n=3), W.torus(nu=96, nv=40, seed=7, rot=W.CUBE_ROTATIONS[5])]
+    res = [64, 120, 1, 33, 256]
+    dirs = np.concatenate([W.AXIS_DIRS, W.DIAG_DIRS])
+    trip = [(_dev(m.xyz), _dev(m.tri.view(np.int32)), _dev(m.rgb) if m.rgb is not None else None) for m in meshes]
+    got = bs.sample_visible_batched(trip, res, dirs)
+    for m, r, g in zip(meshes, res, got):
+        ref, mn, s = oracle.sample_mesh(m, dirs, r)
+        _check_sample(g, ref, mn, s)
+
+
+def test_sample_batched_overflow_and_invalid(bs):
+    ms = [W.torus(nu=32, nv=16), W.torus(nu=20, nv=10, seed=2)]
+    trip = [(_dev(m.xyz), _dev(m.tri.view(np.int32)), None) for m in ms]
+    with pytest.raises(bs.BsError) as e:
+        bs.sample_visible_batched(trip, [64, 64], W.AXIS_DIRS, caps=[10, 6 * 64 * 64])
+    assert e.value.status == bs.BS_EOVERFLOW
+    bad = ms[1].xyz.copy()
+    bad[0, 0] = np.inf
+    trip[1] = (_dev(bad), trip[1][1], None)
+    with pytest.raises(bs.BsError) as e:
+        bs.sample_visible_batched(trip, [64, 64], W.AXIS_DIRS)
+    assert e.value.status == bs.BS_EINVAL and "part 1" in str(e.value)
+    tri_bad = ms[0].tri.copy()
+    tri_bad[3, 1] = ms[0].nverts
+    with pytest.raises(bs.BsError) as e:
+        bs.sample_visible(_dev(ms[0].xyz), _dev(tri_bad.view(np.int32)), None, W.AXIS_DIRS, 32)
+    assert e.value.status == bs.BS_EINVAL
