@@ -44,25 +44,22 @@ __host__ __device__ __forceinline__ uint32_t pos_x(uint64_t k) { return (uint32_
 __host__ __device__ __forceinline__ uint32_t pos_y(uint64_t k) { return (uint32_t)(k >> 21) & 0x1FFFFFu; }
 __host__ __device__ __forceinline__ uint32_t pos_z(uint64_t k) { return (uint32_t)k & 0x1FFFFFu; }
 
-// Squared distance of two packed positions (< 3 * 2^42, exact in int64).
+// Squared distance of two packed positions (< 3 * 2^42, exact in int64).  The
+// coordinate differences fit 22 bits, so each square is one 32x32->64 multiply.
 __host__ __device__ __forceinline__ int64_t dist2(uint64_t a, uint64_t b) {
-    int64_t dx = (int64_t)pos_x(a) - (int64_t)pos_x(b);
-    int64_t dy = (int64_t)pos_y(a) - (int64_t)pos_y(b);
-    int64_t dz = (int64_t)pos_z(a) - (int64_t)pos_z(b);
-    return dx * dx + dy * dy + dz * dz;
+    const int32_t dx = (int32_t)pos_x(a) - (int32_t)pos_x(b);
+    const int32_t dy = (int32_t)pos_y(a) - (int32_t)pos_y(b);
+    const int32_t dz = (int32_t)pos_z(a) - (int32_t)pos_z(b);
+    return (int64_t)dx * dx + (int64_t)dy * dy + (int64_t)dz * dz;
 }
 
 // Squared distance from q to the box [lo, hi] (packed corners), 0 inside.
 __host__ __device__ __forceinline__ int64_t box_dist2(uint64_t lo, uint64_t hi, uint64_t q) {
-    int64_t s = 0;
-    int64_t c, l, h, d;
-    c = pos_x(q); l = pos_x(lo); h = pos_x(hi);
-    d = c < l ? l - c : (c > h ? c - h : 0); s += d * d;
-    c = pos_y(q); l = pos_y(lo); h = pos_y(hi);
-    d = c < l ? l - c : (c > h ? c - h : 0); s += d * d;
-    c = pos_z(q); l = pos_z(lo); h = pos_z(hi);
-    d = c < l ? l - c : (c > h ? c - h : 0); s += d * d;
-    return s;
+    const int32_t cx = (int32_t)pos_x(q), cy = (int32_t)pos_y(q), cz = (int32_t)pos_z(q);
+    const int32_t dx = max(max((int32_t)pos_x(lo) - cx, cx - (int32_t)pos_x(hi)), 0);
+    const int32_t dy = max(max((int32_t)pos_y(lo) - cy, cy - (int32_t)pos_y(hi)), 0);
+    const int32_t dz = max(max((int32_t)pos_z(lo) - cz, cz - (int32_t)pos_z(hi)), 0);
+    return (int64_t)dx * dx + (int64_t)dy * dy + (int64_t)dz * dz;
 }
 
 // Spread the low 21 bits of v to every third bit (Morton interleave helper).

@@ -205,9 +205,20 @@ __global__ void __launch_bounds__(T) k_order_loop(const PartDesc *__restrict__ p
 // (32 groups, 32768 points) prunes the apply sweep of large parts.
 //   sgkey = (D+1) << 15 | (32767 - i_in_supergroup);   top = (D+1) << 8 | (255 - sg)
 // ---------------------------------------------------------------------------
-constexpr int CAP = 64;      // candidates per round (two per lane of the simulating warp)
-constexpr int MAXP = 64;     // picks per round
+constexpr int CAP = 128;     // candidates per round (four per lane of the simulating warp)
+constexpr int CPL = CAP / 32;
+constexpr int MAXP = 64;     // picks per round (pick sets are 64-bit masks)
 constexpr int MAX_SG = 192;  // super-groups: BS_MAX_POINTS / 32768
+constexpr int TIE_GROUPS = 8;  // groups a tie window may span
+constexpr int NB_SMEM = 2048;  // parts with at most this many buckets keep bucket records in shared memory
+constexpr size_t ROUNDS_SMEM_STATIC = 12 * 1024;  // bound on the kernel's static shared memory
+constexpr size_t SMEM_LIMIT = 227 * 1024;
+
+// shared-memory bucket capacity for a launch whose largest part has ngmax groups
+static int rounds_nbsm(int ngmax) {
+    return (size_t)NB_SMEM * 24 + (size_t)ngmax * 28 + ROUNDS_SMEM_STATIC <= SMEM_LIMIT ? NB_SMEM : 0;
+}
+static size_t rounds_smem(int ngmax) { return (size_t)rounds_nbsm(ngmax) * 24 + (size_t)ngmax * 28; }
 
 __device__ __forceinline__ uint64_t pick_mask(uint32_t np, const uint32_t *pi, const uint64_t *pk, uint64_t allow,
                                               uint32_t own_shift, uint32_t own, uint64_t lo, uint64_t hi, int64_t maxD) {
@@ -223,24 +234,29 @@ __device__ __forceinline__ uint64_t pick_mask(uint32_t np, const uint32_t *pi, c
 
 template <int T>
 __global__ void __launch_bounds__(T) k_order_rounds(const PartDesc *__restrict__ parts, int nparts,
-                                                    uint32_t *__restrict__ next_part, int ngmax) {
+                                                    uint32_t *__restrict__ next_part, int ngmax, int nbsm) {
+    static_assert(T >= CAP, "the candidate sort needs one thread per candidate");
     constexpr int NW = T / 32;
     extern __shared__ uint64_t sm[];
-    uint64_t *s_gkey = sm;
-    uint64_t *s_glo = sm + ngmax;
-    uint64_t *s_ghi = sm + 2 * ngmax;
-    uint32_t *s_glist = (uint32_t *)(sm + 3 * ngmax);
+    uint64_t *s_bkey = sm;
+    uint64_t *s_blo = sm + nbsm;
+    uint64_t *s_bhi = sm + 2 * nbsm;
+    uint64_t *s_gkey = sm + 3 * nbsm;
+    uint64_t *s_glo = s_gkey + ngmax;
+    uint64_t *s_ghi = s_gkey + 2 * ngmax;
+    uint32_t *s_glist = (uint32_t *)(s_gkey + 3 * ngmax);
     __shared__ uint64_t s_sgkey[MAX_SG], s_sglo[MAX_SG], s_sghi[MAX_SG], s_sgmask[MAX_SG];
-    __shared__ uint32_t s_sglist[MAX_SG];
+    __shared__ uint32_t s_sglist[MAX_SG], s_heavy[MAX_SG];
+    __shared__ uint32_t s_nheavy;
     __shared__ uint64_t s_ck[CAP];
     __shared__ int64_t s_cd[CAP];
     __shared__ uint32_t s_ci[CAP];
     __shared__ uint64_t s_pk[MAXP];
+    __shared__ int64_t s_pd[MAXP];
     __shared__ uint32_t s_pi[MAXP];
-    __shared__ uint32_t s_part, s_ccnt, s_gcnt, s_sgcnt, s_npick;
+    __shared__ uint32_t s_part, s_ccnt, s_gcnt, s_sgcnt, s_npick, s_icut;
     __shared__ int s_shift;
     __shared__ int64_t s_tieD;
-    __shared__ uint32_t s_icut;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     for (;;) {
@@ -250,10 +266,25 @@ __global__ void __launch_bounds__(T) k_order_rounds(const PartDesc *__restrict__
         if (p >= (uint32_t)nparts) break;
         const PartDesc P = parts[p];
         const uint32_t ng = P.ng, ns = (ng + 31) / 32;
+        const uint32_t n = P.n, nb = P.nb, m = P.m;
+        const uint64_t *__restrict__ key = P.key;
+        int64_t *__restrict__ Dg = P.D;
+        // bucket records: shared memory when they fit (generic pointers either way)
+        const bool bsm = nb <= (uint32_t)nbsm;
+        uint64_t *bkey = bsm ? s_bkey : P.bkey;
+        const uint64_t *blo_p = bsm ? s_blo : P.blo;
+        const uint64_t *bhi_p = bsm ? s_bhi : P.bhi;
         for (uint32_t g = threadIdx.x; g < ng; g += T) {
             s_gkey[g] = P.gkey[g];
             s_glo[g] = P.glo[g];
             s_ghi[g] = P.ghi[g];
+        }
+        if (bsm) {
+            for (uint32_t b = threadIdx.x; b < nb; b += T) {
+                s_bkey[b] = P.bkey[b];
+                s_blo[b] = P.blo[b];
+                s_bhi[b] = P.bhi[b];
+            }
         }
         if (threadIdx.x == 0) {
             P.perm[0] = P.start;
@@ -283,7 +314,7 @@ __global__ void __launch_bounds__(T) k_order_rounds(const PartDesc *__restrict__
         }
         __syncthreads();
         uint32_t k = 1;
-        while (k < P.m) {
+        while (k < m) {
             // (1) current maximum (every warp computes it; no barrier needed)
             uint64_t top = 0;
             for (uint32_t sg = lane; sg < ns; sg += 32) top = max(top, ((s_sgkey[sg] >> 15) << 8) | (uint64_t)(255 - sg));
@@ -292,7 +323,7 @@ __global__ void __launch_bounds__(T) k_order_rounds(const PartDesc *__restrict__
             const uint32_t sgj = 255u - (uint32_t)(top & 255u);
             const uint32_t j = sgj * 32768u + (32767u - (uint32_t)(s_sgkey[sgj] & 32767u));
             // (2) threshold: tau = D1 (1 - 2^-shift); when more than CAP points tie at D1, a tie
-            //     window instead: tau = D1 and an index cut inside the argmax's group
+            //     window instead: tau = D1 and an index cut (the lowest-index tied points fit)
             const int shift = s_shift;
             const bool tie = D1 == s_tieD;
             const int64_t tau = tie ? D1 : D1 - (D1 >> shift);
@@ -301,33 +332,39 @@ __global__ void __launch_bounds__(T) k_order_rounds(const PartDesc *__restrict__
             __syncthreads();
             // (3) gather the candidates
             if (tie) {
-                // the D1 points of the buckets of group(j) from bucket(j) on, in index order, while
-                // they fit; icut = first index left out (no point with D = D1 lies below j)
+                // D1 points in index order from j on, over up to TIE_GROUPS groups holding D1
+                // points, while they fit; icut = first index left out (no D1 point lies below j)
                 if (warp == 0) {
-                    const uint32_t g0 = j >> 10;
-                    const uint32_t b = g0 * 32 + lane;
-                    const uint64_t bk = (b < P.nb && b >= (j >> 5)) ? P.bkey[b] : 0ull;
-                    uint32_t mask = __ballot_sync(FULL, (int64_t)(bk >> 5) - 1 >= tau);
-                    uint32_t cnt = 0, icut = min(P.n, (g0 + 1) * 1024u);
-                    while (mask) {
-                        const int bb = __ffs(mask) - 1;
-                        mask &= mask - 1;
-                        const uint32_t i = (g0 * 32 + bb) * 32 + lane;
-                        const int64_t d = i < P.n ? P.D[i] : -1;
-                        const uint64_t ki = i < P.n ? P.key[i] : 0ull;
-                        const bool c = d >= tau;
-                        const uint32_t cm = __ballot_sync(FULL, c);
-                        if (cnt + __popc(cm) > (uint32_t)CAP) {
-                            icut = (g0 * 32 + bb) * 32;
-                            break;
+                    uint32_t cnt = 0, icut = n, used = 0;
+                    bool full = false;
+                    for (uint32_t g0 = j >> 10; g0 < ng && !full && used < TIE_GROUPS; ++g0) {
+                        if ((int64_t)(s_gkey[g0] >> 10) - 1 < tau) continue;
+                        ++used;
+                        const uint32_t b = g0 * 32 + lane;
+                        const uint64_t bk = (b < nb && b >= (j >> 5)) ? bkey[b] : 0ull;
+                        uint32_t mask = __ballot_sync(FULL, (int64_t)(bk >> 5) - 1 >= tau);
+                        while (mask) {
+                            const int bb = __ffs(mask) - 1;
+                            mask &= mask - 1;
+                            const uint32_t i = (g0 * 32 + bb) * 32 + lane;
+                            const int64_t d = i < n ? Dg[i] : -1;
+                            const uint64_t ki = i < n ? key[i] : 0ull;
+                            const bool c = d >= tau;
+                            const uint32_t cm = __ballot_sync(FULL, c);
+                            if (cnt + __popc(cm) > (uint32_t)CAP) {
+                                icut = (g0 * 32 + bb) * 32;
+                                full = true;
+                                break;
+                            }
+                            if (c) {
+                                const uint32_t slot = cnt + __popc(cm & ((1u << lane) - 1u));
+                                s_ci[slot] = i;
+                                s_cd[slot] = d;
+                                s_ck[slot] = ki;
+                            }
+                            cnt += __popc(cm);
                         }
-                        if (c) {
-                            const uint32_t slot = cnt + __popc(cm & ((1u << lane) - 1u));
-                            s_ci[slot] = i;
-                            s_cd[slot] = d;
-                            s_ck[slot] = ki;
-                        }
-                        cnt += __popc(cm);
+                        if (!full && used == TIE_GROUPS) icut = min(n, (g0 + 1) * 1024u);
                     }
                     if (lane == 0) { s_ccnt = cnt; s_icut = icut; }
                 }
@@ -345,28 +382,28 @@ __global__ void __launch_bounds__(T) k_order_rounds(const PartDesc *__restrict__
                 for (uint32_t li = warp; li < ngl; li += NW) {
                     const uint32_t g = s_glist[li];
                     const uint32_t b = g * 32 + lane;
-                    const uint64_t bk = b < P.nb ? P.bkey[b] : 0ull;
+                    const uint64_t bk = b < nb ? bkey[b] : 0ull;
                     uint32_t mask = __ballot_sync(FULL, (int64_t)(bk >> 5) - 1 >= tau);
                     while (mask) {
-                        // up to four buckets per pass so their loads overlap
-                        uint32_t bbs[4];
-                        int nb4 = 0;
-                        while (mask && nb4 < 4) {
-                            bbs[nb4++] = (uint32_t)(__ffs(mask) - 1);
+                        // up to eight buckets per pass so their loads overlap
+                        uint32_t bbs[8];
+                        int nb8 = 0;
+                        while (mask && nb8 < 8) {
+                            bbs[nb8++] = (uint32_t)(__ffs(mask) - 1);
                             mask &= mask - 1;
                         }
-                        int64_t d[4];
-                        uint64_t ki[4];
+                        int64_t d[8];
+                        uint64_t ki[8];
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const uint32_t i = (g * 32 + (u < nb4 ? bbs[u] : 0)) * 32 + lane;
-                            const bool ok = u < nb4 && i < P.n;
-                            d[u] = ok ? P.D[i] : -1;
-                            ki[u] = ok ? P.key[i] : 0ull;
+                        for (int u = 0; u < 8; ++u) {
+                            const uint32_t i = (g * 32 + (u < nb8 ? bbs[u] : 0)) * 32 + lane;
+                            const bool ok = u < nb8 && i < n;
+                            d[u] = ok ? Dg[i] : -1;
+                            ki[u] = ok ? key[i] : 0ull;
                         }
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            if (u < nb4 && d[u] >= tau && d[u] >= 0) {
+                        for (int u = 0; u < 8; ++u) {
+                            if (u < nb8 && d[u] >= tau && d[u] >= 0) {
                                 const uint32_t slot = atomicAdd(&s_ccnt, 1u);
                                 if (slot < CAP) {
                                     s_ci[slot] = (g * 32 + bbs[u]) * 32 + lane;
@@ -397,7 +434,7 @@ __global__ void __launch_bounds__(T) k_order_rounds(const PartDesc *__restrict__
                 continue;
             }
             // (4) candidates in index order: slot order is the lowest-index tie-break
-            {
+            if (!tie) {
                 uint32_t ci = 0, rank = 0;
                 int64_t cd = 0;
                 uint64_t ck = 0;
@@ -415,69 +452,107 @@ __global__ void __launch_bounds__(T) k_order_rounds(const PartDesc *__restrict__
                 }
                 __syncthreads();
             }
-            // (5) the greedy restricted to C, one warp, while the best stays above (tau, icut)
+            // (5) the greedy restricted to C, one warp, while the best stays above (tau, icut);
+            //     slot lane + 32u lives in lane's register u
             if (warp == 0) {
-                const uint32_t a = lane, b = lane + 32;
-                bool la = a < ccnt, lb = b < ccnt;
-                int64_t Da = la ? s_cd[a] : 0, Db = lb ? s_cd[b] : 0;
-                const uint64_t qa = la ? s_ck[a] : 0ull, qb = lb ? s_ck[b] : 0ull;
-                const uint32_t budget = min((uint32_t)MAXP, P.m - k);
+                int64_t Dc[CPL];
+                uint64_t qc[CPL];
+                bool live[CPL];
+#pragma unroll
+                for (int u = 0; u < CPL; ++u) {
+                    const uint32_t sl = lane + 32 * u;
+                    live[u] = sl < ccnt;
+                    Dc[u] = live[u] ? s_cd[sl] : 0;
+                    qc[u] = live[u] ? s_ck[sl] : 0ull;
+                }
+                const uint32_t budget = min((uint32_t)MAXP, m - k);
                 uint32_t np = 0;
                 while (np < budget) {
-                    const uint64_t ka = la ? (((uint64_t)(Da + 1) << 7) | (uint64_t)(127 - a)) : 0ull;
-                    const uint64_t kb = lb ? (((uint64_t)(Db + 1) << 7) | (uint64_t)(127 - b)) : 0ull;
-                    const uint64_t best = warp_max_u64(max(ka, kb));
+                    uint64_t kmax = 0;
+#pragma unroll
+                    for (int u = 0; u < CPL; ++u)
+                        if (live[u]) kmax = max(kmax, ((uint64_t)(Dc[u] + 1) << 8) | (uint64_t)(255 - (lane + 32 * u)));
+                    const uint64_t best = warp_max_u64(kmax);
                     if (best == 0) break;
-                    const uint32_t slot = 127u - (uint32_t)(best & 127u);
-                    const int64_t Dbest = (int64_t)(best >> 7) - 1;
+                    const uint32_t slot = 255u - (uint32_t)(best & 255u);
+                    const int64_t Dbest = (int64_t)(best >> 8) - 1;
                     const uint32_t idx = s_ci[slot];
                     if (!(Dbest > tau || (Dbest == tau && idx < icut))) break;
                     const uint64_t qbest = s_ck[slot];
                     if (lane == 0) {
                         s_pk[np] = qbest;
                         s_pi[np] = idx;
-                        P.perm[k + np] = idx;
-                        P.rad2[k + np] = Dbest;
+                        s_pd[np] = Dbest;
                     }
                     ++np;
-                    if (a == slot) la = false;
-                    else if (la) Da = min(Da, dist2(qa, qbest));
-                    if (b == slot) lb = false;
-                    else if (lb) Db = min(Db, dist2(qb, qbest));
+#pragma unroll
+                    for (int u = 0; u < CPL; ++u) {
+                        if (lane + 32 * u == slot) {
+                            live[u] = false;
+                        } else if (live[u]) {
+                            Dc[u] = min(Dc[u], dist2(qc[u], qbest));
+                            live[u] = Dc[u] >= tau;  // below tau it cannot be picked in this round
+                        }
+                    }
                 }
                 if (lane == 0) s_npick = np;
             }
             __syncthreads();
             const uint32_t np = s_npick;
             // (6) apply the round's picks to the whole part
-            for (uint32_t t = threadIdx.x; t < np; t += T) P.D[s_pi[t]] = -1;
+            for (uint32_t t = threadIdx.x; t < np; t += T) {
+                Dg[s_pi[t]] = -1;
+                P.perm[k + t] = s_pi[t];
+                P.rad2[k + t] = s_pd[t];
+            }
             if (threadIdx.x == 0) { s_sgcnt = 0; s_gcnt = 0; }
             __syncthreads();
             const uint64_t all = np >= 64 ? ~0ull : ((1ull << np) - 1ull);
             for (uint32_t sg = warp; sg < ns; sg += NW) {
-                const uint64_t m = pick_mask(np, s_pi, s_pk, all, 15, sg, s_sglo[sg], s_sghi[sg],
-                                             (int64_t)(s_sgkey[sg] >> 15) - 1);
-                if (m && lane == 0) {
-                    s_sgmask[sg] = m;
+                const uint64_t mk = pick_mask(np, s_pi, s_pk, all, 15, sg, s_sglo[sg], s_sghi[sg],
+                                              (int64_t)(s_sgkey[sg] >> 15) - 1);
+                if (mk && lane == 0) {
+                    s_sgmask[sg] = mk;
                     s_sglist[atomicAdd(&s_sgcnt, 1u)] = sg;
                 }
             }
             __syncthreads();
             const uint32_t nsgl = s_sgcnt;
+            if (threadIdx.x == 0) s_nheavy = 0;
+            __syncthreads();
             for (uint32_t li = warp; li < nsgl; li += NW) {
                 const uint32_t sg = s_sglist[li];
-                const uint32_t g = sg * 32 + lane;
-                if (g < ng) {
-                    const int64_t gD = (int64_t)(s_gkey[g] >> 10) - 1;
-                    const uint64_t lo = s_glo[g], hi = s_ghi[g];
-                    uint64_t m = s_sgmask[sg];
-                    bool rel = false;
-                    while (m && !rel) {
-                        const int t = __ffsll((long long)m) - 1;
-                        m &= m - 1;
-                        rel = (s_pi[t] >> 10) == g || box_dist2(lo, hi, s_pk[t]) < gD;
+                const uint64_t sgm = s_sgmask[sg];
+                if (__popcll((long long)sgm) <= 4) {
+                    // few picks: one lane per group walks them
+                    const uint32_t g = sg * 32 + lane;
+                    if (g < ng) {
+                        const int64_t gD = (int64_t)(s_gkey[g] >> 10) - 1;
+                        const uint64_t lo = s_glo[g], hi = s_ghi[g];
+                        uint64_t mm = sgm;
+                        bool rel = false;
+                        while (mm && !rel) {
+                            const int t = __ffsll((long long)mm) - 1;
+                            mm &= mm - 1;
+                            rel = (s_pi[t] >> 10) == g || box_dist2(lo, hi, s_pk[t]) < gD;
+                        }
+                        if (rel) s_glist[atomicAdd(&s_gcnt, 1u)] = g;
                     }
-                    if (rel) s_glist[atomicAdd(&s_gcnt, 1u)] = g;
+                } else if (lane == 0) {
+                    s_heavy[atomicAdd(&s_nheavy, 1u)] = sg;
+                }
+            }
+            __syncthreads();
+            {
+                // many picks: one warp per (super-group, group), the lanes test the picks
+                const uint32_t nh = s_nheavy;
+                for (uint32_t it = warp; it < nh * 32; it += NW) {
+                    const uint32_t sg = s_heavy[it >> 5];
+                    const uint32_t g = sg * 32 + (it & 31);
+                    if (g >= ng) continue;
+                    const uint64_t gm = pick_mask(np, s_pi, s_pk, s_sgmask[sg], 10, g, s_glo[g], s_ghi[g],
+                                                  (int64_t)(s_gkey[g] >> 10) - 1);
+                    if (gm && lane == 0) s_glist[atomicAdd(&s_gcnt, 1u)] = g;
                 }
             }
             __syncthreads();
@@ -487,61 +562,64 @@ __global__ void __launch_bounds__(T) k_order_rounds(const PartDesc *__restrict__
                 const uint64_t gm = pick_mask(np, s_pi, s_pk, s_sgmask[g >> 5], 10, g, s_glo[g], s_ghi[g],
                                               (int64_t)(s_gkey[g] >> 10) - 1);
                 const uint32_t b = g * 32 + lane;
-                const bool vb = b < P.nb;
-                uint64_t bk = vb ? P.bkey[b] : 0ull;
-                const uint64_t blo = vb ? P.blo[b] : 0ull, bhi = vb ? P.bhi[b] : 0ull;
+                const bool vb = b < nb;
+                uint64_t bk = vb ? bkey[b] : 0ull;
+                const uint64_t blo = vb ? blo_p[b] : 0ull, bhi = vb ? bhi_p[b] : 0ull;
                 const int64_t bD = (int64_t)(bk >> 5) - 1;
-                bool aff = false;
+                // picks that may lower a D in this lane's bucket
+                uint64_t bm = 0;
                 if (vb) {
-                    uint64_t m = gm;
-                    while (m && !aff) {
-                        const int t = __ffsll((long long)m) - 1;
-                        m &= m - 1;
-                        aff = (s_pi[t] >> 5) == b || box_dist2(blo, bhi, s_pk[t]) < bD;
+                    uint64_t mm = gm;
+                    while (mm) {
+                        const int t = __ffsll((long long)mm) - 1;
+                        mm &= mm - 1;
+                        if ((s_pi[t] >> 5) == b || box_dist2(blo, bhi, s_pk[t]) < bD) bm |= 1ull << t;
                     }
                 }
-                uint32_t amask = __ballot_sync(FULL, aff);
+                uint32_t amask = __ballot_sync(FULL, bm != 0);
+                const bool aff = bm != 0;
                 while (amask) {
-                    // up to four affected buckets per pass so their loads overlap
-                    uint32_t bbs[4];
-                    int nb4 = 0;
-                    while (amask && nb4 < 4) {
-                        bbs[nb4++] = (uint32_t)(__ffs(amask) - 1);
+                    // up to eight affected buckets per pass so their loads overlap
+                    uint32_t bbs[8];
+                    int nb8 = 0;
+                    while (amask && nb8 < 8) {
+                        bbs[nb8++] = (uint32_t)(__ffs(amask) - 1);
                         amask &= amask - 1;
                     }
-                    int64_t d[4];
-                    uint64_t ki[4];
+                    int64_t d[8];
+                    uint64_t ki[8];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const uint32_t i = (g * 32 + (u < nb4 ? bbs[u] : 0)) * 32 + lane;
-                        const bool ok = u < nb4 && i < P.n;
-                        d[u] = ok ? P.D[i] : -1;
-                        ki[u] = ok ? P.key[i] : 0ull;
+                    for (int u = 0; u < 8; ++u) {
+                        const uint32_t i = (g * 32 + (u < nb8 ? bbs[u] : 0)) * 32 + lane;
+                        const bool ok = u < nb8 && i < n;
+                        d[u] = ok ? Dg[i] : -1;
+                        ki[u] = ok ? key[i] : 0ull;
                     }
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        if (u >= nb4) break;
+                    for (int u = 0; u < 8; ++u) {
+                        if (u >= nb8) break;
                         const uint32_t i = (g * 32 + bbs[u]) * 32 + lane;
+                        const uint64_t mu = __shfl_sync(FULL, bm, (int)bbs[u]);
                         int64_t dd = d[u];
                         if (dd > 0) {
                             int64_t nd = dd;
-                            uint64_t m = gm;
-                            while (m) {
-                                const int t = __ffsll((long long)m) - 1;
-                                m &= m - 1;
+                            uint64_t mm = mu;
+                            while (mm) {
+                                const int t = __ffsll((long long)mm) - 1;
+                                mm &= mm - 1;
                                 nd = min(nd, dist2(ki[u], s_pk[t]));
                             }
                             if (nd < dd) {
                                 dd = nd;
-                                P.D[i] = nd;
+                                Dg[i] = nd;
                             }
                         }
-                        const uint64_t nk = i < P.n ? (((uint64_t)(dd + 1) << 5) | (uint64_t)(31 - lane)) : 0ull;
+                        const uint64_t nk = i < n ? (((uint64_t)(dd + 1) << 5) | (uint64_t)(31 - lane)) : 0ull;
                         const uint64_t nbk = warp_max_u64(nk);
                         if (lane == (int)bbs[u]) bk = nbk;
                     }
                 }
-                if (aff) P.bkey[b] = bk;
+                if (aff) bkey[b] = bk;
                 const uint64_t cand = vb ? (((bk >> 5) << 10) | (uint64_t)(1023 - (lane * 32 + (31 - (int)(bk & 31))))) : 0ull;
                 const uint64_t ngk = warp_max_u64(cand);
                 if (lane == 0) s_gkey[g] = ngk;
@@ -635,11 +713,13 @@ static cudaError_t launch_loop(const PartDesc *d_parts, int nparts, uint32_t *d_
         e = cudaFuncSetAttribute(k_order_loop<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k_order_loop<T><<<grid, T, smem, stream>>>(d_parts, nparts, d_next, ngmax);
-    } else {
-        const size_t smem = (size_t)ngmax * 28;
+    } else if constexpr (T >= CAP) {
+        const size_t smem = rounds_smem(ngmax);
         e = cudaFuncSetAttribute(k_order_rounds<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_order_rounds<T><<<grid, T, smem, stream>>>(d_parts, nparts, d_next, ngmax);
+        k_order_rounds<T><<<grid, T, smem, stream>>>(d_parts, nparts, d_next, ngmax, rounds_nbsm(ngmax));
+    } else {
+        return cudaErrorInvalidConfiguration;  // the rounds kernel needs at least CAP threads
     }
     return cudaGetLastError();
 }
@@ -652,10 +732,13 @@ static int occupancy(int ngmax) {
         const size_t smem = (size_t)ngmax * 36;
         cudaFuncSetAttribute(k_order_loop<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_order_loop<T>, T, smem);
-    } else {
-        const size_t smem = (size_t)ngmax * 28;
+    } else if constexpr (T >= CAP) {
+        const size_t smem = rounds_smem(ngmax);
         cudaFuncSetAttribute(k_order_rounds<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_order_rounds<T>, T, smem);
+    } else {
+        e = cudaSuccess;
+        blocks = 1;
     }
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -665,11 +748,34 @@ static int occupancy(int ngmax) {
 }
 
 static int pick_threads(int ngmax, bool batched) {
-    if (g_loop_threads_override) return g_loop_threads_override;
+    if (g_loop_threads_override) return g_order_algo == 2 ? std::max(g_loop_threads_override, 128) : g_loop_threads_override;
+    if (g_order_algo == 2) return ngmax <= 8 ? 256 : 512;  // measured: 16 warps per part beat more resident parts
     if (batched) return ngmax > 256 ? 256 : 128;
     if (ngmax <= 32) return 128;
     if (ngmax <= 512) return 256;
     return 512;
+}
+
+// one persistent loop launch over parts[0..nparts) with T threads per CTA
+static cudaError_t launch_set(const PartDesc *d_parts, int nparts, uint32_t *d_next, int ngmax, int T, int sms,
+                              cudaStream_t stream) {
+    int per_sm = 1;
+    switch (T) {
+        case 64: per_sm = occupancy<64>(ngmax); break;
+        case 128: per_sm = occupancy<128>(ngmax); break;
+        case 256: per_sm = occupancy<256>(ngmax); break;
+        case 512: per_sm = occupancy<512>(ngmax); break;
+        default: per_sm = occupancy<1024>(ngmax); break;
+    }
+    if (g_ctas_per_sm_override) per_sm = std::min(per_sm, g_ctas_per_sm_override);
+    const int grid = std::max(1, std::min(nparts, sms * per_sm));
+    switch (T) {
+        case 64: return launch_loop<64>(d_parts, nparts, d_next, ngmax, grid, stream);
+        case 128: return launch_loop<128>(d_parts, nparts, d_next, ngmax, grid, stream);
+        case 256: return launch_loop<256>(d_parts, nparts, d_next, ngmax, grid, stream);
+        case 512: return launch_loop<512>(d_parts, nparts, d_next, ngmax, grid, stream);
+        default: return launch_loop<1024>(d_parts, nparts, d_next, ngmax, grid, stream);
+    }
 }
 
 // Orders nparts parts.  host descriptors: keys, outputs, n, m, start, scale filled in.
@@ -738,25 +844,8 @@ bs_status order_parts(std::vector<PartDesc> &hp, cudaStream_t stream, bool batch
         int dev = 0, sms = 152;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const int T = pick_threads((int)ngmax, batched);
-        int per_sm = 1;
-        switch (T) {
-            case 64: per_sm = occupancy<64>(ngmax); break;
-            case 128: per_sm = occupancy<128>(ngmax); break;
-            case 256: per_sm = occupancy<256>(ngmax); break;
-            case 512: per_sm = occupancy<512>(ngmax); break;
-            default: per_sm = occupancy<1024>(ngmax); break;
-        }
-        if (g_ctas_per_sm_override) per_sm = std::min(per_sm, g_ctas_per_sm_override);
-        const int grid = std::max(1, std::min(nparts, sms * per_sm));
         timing_mark(1, 0, stream);
-        switch (T) {
-            case 64: e = launch_loop<64>(d_parts, nparts, d_next, ngmax, grid, stream); break;
-            case 128: e = launch_loop<128>(d_parts, nparts, d_next, ngmax, grid, stream); break;
-            case 256: e = launch_loop<256>(d_parts, nparts, d_next, ngmax, grid, stream); break;
-            case 512: e = launch_loop<512>(d_parts, nparts, d_next, ngmax, grid, stream); break;
-            default: e = launch_loop<1024>(d_parts, nparts, d_next, ngmax, grid, stream); break;
-        }
+        e = launch_set(d_parts, nparts, d_next, (int)ngmax, pick_threads((int)ngmax, batched), sms, stream);
         timing_mark(1, 1, stream);
         if (e != cudaSuccess) {
             set_error("bs_order: loop launch failed: %s", cudaGetErrorString(e));

@@ -120,7 +120,7 @@ def test_order_torus_parity(bs):
     _check_order(bs, ref["key"], seed=0, scale=s)
 
 
-@pytest.mark.parametrize("n", [1, 2, 3, 31, 32, 33, 1023, 1024, 1025, 2047, 5000, 33 * 1024 + 17])
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 32, 33, 1023, 1024, 1025, 2047, 5000, 33 * 1024 + 17, 65536, 65569])
 def test_order_ragged_sizes(bs, n):
     g = np.random.default_rng(n)
     pts = np.unique(g.integers(0, 1 << 21, size=(n + n // 10 + 5, 3)), axis=0)[:n]
@@ -167,7 +167,7 @@ def test_order_truncated(bs, max_count):
 
 def test_order_batched_matches_single_and_oracle(bs):
     g = np.random.default_rng(2)
-    sizes = [1, 5, 32, 1000, 3000, 1025, 20000, 7]
+    sizes = [1, 5, 32, 1000, 3000, 1025, 20000, 7, 70001]
     keys_np = []
     for n in sizes:
         pts = np.unique(g.integers(0, 1 << 18, size=(n + 10, 3)), axis=0)[:n]
@@ -175,14 +175,14 @@ def test_order_batched_matches_single_and_oracle(bs):
     keys = [_dev(k.view(np.int64)) for k in keys_np]
     seeds = list(range(len(keys)))
     res = bs.order_batched(keys, seeds=seeds, part_ids=[11 * i for i in range(len(keys))],
-                           max_counts=[0, 0, 0, 500, 0, 0, 0, 3], scales=[2.0] * len(keys))
+                           max_counts=[0, 0, 0, 500, 0, 0, 0, 3, 0], scales=[2.0] * len(keys))
     for i, (perm, rad2, radius) in enumerate(res):
         s = oracle.start_index(sizes[i], seed=seeds[i], part_id=11 * i)
-        rp, rr = oracle.greedy(keys_np[i], s, max_count=[0, 0, 0, 500, 0, 0, 0, 3][i])
+        rp, rr = oracle.greedy(keys_np[i], s, max_count=[0, 0, 0, 500, 0, 0, 0, 3, 0][i])
         assert np.array_equal(_np(perm, np.uint32), rp), i
         assert np.array_equal(_np(rad2), rr), i
         assert np.array_equal(_np(radius).view(np.uint32), oracle.radius(rr, 2.0).view(np.uint32)), i
-        p1, r1, _ = bs.order(keys[i], seed=seeds[i], part_id=11 * i, max_count=[0, 0, 0, 500, 0, 0, 0, 3][i])
+        p1, r1, _ = bs.order(keys[i], seed=seeds[i], part_id=11 * i, max_count=[0, 0, 0, 500, 0, 0, 0, 3, 0][i])
         assert torch.equal(p1, perm) and torch.equal(r1, rad2)
 
 
