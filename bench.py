@@ -215,7 +215,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--parts", type=int, default=4096)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--plain-parts", type=int, default=64, help="parts timed one launch each for the plain path")
+    ap.add_argument("--plain-parts", type=int, default=512, help="parts timed one launch each for the plain path")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
@@ -399,6 +399,7 @@ def main():
                     raise bs.BsError(st, "bs_order", bs.last_error())
         plain()
         ms_p = timed(plain, 1)
+        plain_ms = ms_p
         sub_parts = (bs.Surfels * len(sub))(*[parts[i] for i in sub])
         sub_opts = (bs.OrderOpts * len(sub))(*[opts[i] for i in sub])
         spp = (C.c_void_p * len(sub))(*[pp[i] for i in sub])
@@ -438,7 +439,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d_bytes),
                     "d2h_bytes_per_step": int(d2h_bytes)},
             "gpu_launches": args.steps * (nsample_kernels + 3),
-            "roofline": {"bound": "hbm", "kernel": "k_order_loop", "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "hbm", "kernel": "k_order_rounds", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                          "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured" else "fallback 6800 GB/s",
                          "algorithmic_bytes_per_launch": bytes_launch, "loop_ms_per_launch": loop_avg},
