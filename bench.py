@@ -399,7 +399,6 @@ def main():
                     raise bs.BsError(st, "bs_order", bs.last_error())
         plain()
         ms_p = timed(plain, 1)
-        plain_ms = ms_p
         sub_parts = (bs.Surfels * len(sub))(*[parts[i] for i in sub])
         sub_opts = (bs.OrderOpts * len(sub))(*[opts[i] for i in sub])
         spp = (C.c_void_p * len(sub))(*[pp[i] for i in sub])

@@ -195,11 +195,12 @@ bs_server *bs_server_create(uint64_t device_budget_bytes, int max_inflight, bs_s
 bs_status bs_server_submit(bs_server *srv, const uint64_t *key, uint64_t n, double scale,
                            const bs_order_opts *opts, uint64_t *ticket);
 
-/* Drives the server (admits queued requests, launches work, retires finished
- * ones) and, if the ticket's result is ready, copies it to the HOST arrays
- * perm/rad2/radius (m entries; rad2/radius may be NULL) and releases it.
+/* If the ticket's result is ready, copies it to the HOST arrays perm/rad2/radius
+ * (m entries; rad2/radius may be NULL) and releases it.  With perm == NULL the
+ * call only reports the status (BS_OK when ready) and keeps the result.
  * BS_ENOTREADY while the request is queued or running; BS_EINVAL for an
- * unknown ticket. */
+ * unknown or already collected ticket.  The server's own host thread admits,
+ * launches and retires requests; polling does not drive it. */
 bs_status bs_server_poll(bs_server *srv, uint64_t ticket, uint32_t *perm, int64_t *rad2, float *radius);
 
 /* Per-ticket timestamps in seconds on the server's monotonic clock:

@@ -310,6 +310,10 @@ class Server:
     def poll(self, ticket: int):
         """(perm u32, rad2 i64, radius f32) numpy arrays, or None while not ready."""
         m = self._m[ticket]
+        st = self._lib.bs_server_poll(self._h, ticket, None, None, None)
+        if st == BS_ENOTREADY:
+            return None
+        _check(st, "bs_server_poll")
         perm = np.empty(m, np.uint32)
         rad2 = np.empty(m, np.int64)
         radius = np.empty(m, np.float32)

@@ -270,6 +270,7 @@ static void launch_batch(bs_server *S, SrvSlot &slot, std::vector<SrvReq *> &bat
         int64_t *dr = (int64_t *)(r->dmem + align256(r->n * 8) + align256(r->m * 4));
         float *df = (float *)(r->dmem + align256(r->n * 8) + align256(r->m * 4) + align256(r->m * 8));
         cudaMemcpyAsync(dk, r->key.data(), r->n * 8, cudaMemcpyHostToDevice, slot.stream);
+        std::vector<uint64_t>().swap(r->key);  // a pageable-source copy has been staged when the call returns
         PartDesc p;
         memset(&p, 0, sizeof(p));
         p.key = dk; p.perm = dp; p.rad2 = dr; p.radius = df; p.scale = r->scale;
@@ -417,7 +418,8 @@ bs_status bs_server_poll(bs_server *S, uint64_t ticket, uint32_t *perm, int64_t 
         return r->err == BS_OK ? BS_ECUDA : r->err;
     }
     if (r->state == 4) { set_error("bs_server_poll: ticket %llu already collected", (unsigned long long)ticket); return BS_EINVAL; }
-    if (perm) memcpy(perm, r->perm.data(), r->m * 4);
+    if (!perm) return BS_OK;  // status query only
+    memcpy(perm, r->perm.data(), r->m * 4);
     if (rad2) memcpy(rad2, r->rad2.data(), r->m * 8);
     if (radius) memcpy(radius, r->radius.data(), r->m * 4);
     r->state = 4;
