@@ -61,6 +61,9 @@ def _load():
             lib.or_greedy.argtypes = [P, C.c_uint64, C.c_uint64, C.c_uint64, P, P, P, P, C.c_int]
             lib.or_greedy.restype = C.c_int
             lib.or_radius.argtypes = [P, C.c_uint64, C.c_double, P]
+            lib.or_sampled.argtypes = [P, C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32,
+                                       C.c_uint32, P, P, P]
+            lib.or_sampled.restype = C.c_int
             lib.or_num_threads.restype = C.c_int
             _lib = lib
     return _lib
@@ -179,6 +182,21 @@ def greedy(key: np.ndarray, start: int, max_count: int = 0, nthreads: int | None
     if stats:
         return perm, rad2, int(vis[0]), int(imp[0])
     return perm, rad2
+
+
+def sampled(key: np.ndarray, start: int, max_count: int = 0, seed: int = 0, part_id: int = 0,
+            sample_size: int = 200, step: int = 500, rounds: bool = False):
+    """The paper's randomised progressive sampling (Sec. 3.2): (perm u32, rad2 i64[, round of each pick])."""
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    n = k.shape[0]
+    m = n if max_count == 0 or max_count > n else max_count
+    perm = np.zeros(m, np.uint32)
+    rad2 = np.zeros(m, np.int64)
+    rnd = np.zeros(m, np.uint32)
+    if _load().or_sampled(_p(k), n, start, max_count, seed & (2**64 - 1), part_id, sample_size, step,
+                          _p(perm), _p(rad2), _p(rnd)) != 0:
+        raise ValueError("bad sampled arguments")
+    return (perm, rad2, rnd) if rounds else (perm, rad2)
 
 
 def radius(rad2: np.ndarray, scale: float) -> np.ndarray:

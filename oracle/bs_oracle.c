@@ -534,3 +534,104 @@ int or_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* The paper's randomised progressive sampling (Sec. 3.2): start from a random */
+/* surfel; each round draw a random subset of the remaining input set, append */
+/* the candidate(s) farthest from every surfel chosen before the round, and   */
+/* remove them; after every `step` rounds one more candidate is taken per     */
+/* round (the speed-up heuristic of Sec. 3.2); stop at max_count or when the  */
+/* input set is empty.  Vicinity removal is not used (no threshold is given). */
+/* Reading of the unstated details:                                          */
+/*  - remaining set: array R of indices, removal by swap with the last entry; */
+/*    picks are removed in the order they are appended;                      */
+/*  - round t draws sample_size positions with replacement, position u is    */
+/*    (w * |R|) >> 32 with w = word 0 of Philox4x32-10(ctr = {part_id, t, u, */
+/*    1}, key = {seed_lo, seed_hi}); sample_size = 0 takes the whole set;     */
+/*  - the round takes the m_t = 1 + t / step (step = 0: 1) distinct sampled  */
+/*    points with the largest distance to the chosen set, ties to the lowest */
+/*    index, in that order; distances are not refreshed inside a round;     */
+/*  - rad2 of a pick is its squared distance to every earlier pick.          */
+/* ------------------------------------------------------------------------ */
+int or_sampled(const uint64_t *key, uint64_t n, uint64_t s, uint64_t max_count, uint64_t seed, uint32_t part_id,
+               uint32_t sample_size, uint32_t step, uint32_t *perm, int64_t *rad2, uint32_t *round_of)
+{
+    if (n == 0 || s >= n) return 1;
+    uint64_t m = (max_count == 0 || max_count > n) ? n : max_count;
+    int64_t *D = (int64_t *)malloc(n * sizeof(int64_t));
+    uint32_t *R = (uint32_t *)malloc(n * sizeof(uint32_t));
+    uint32_t *pos = (uint32_t *)malloc(n * sizeof(uint32_t));
+    uint32_t *cand = (uint32_t *)malloc((sample_size ? sample_size : n) * sizeof(uint32_t));
+    uint8_t *mark = (uint8_t *)calloc(n, 1);
+    if (!D || !R || !pos || !cand || !mark) { free(D); free(R); free(pos); free(cand); free(mark); return 1; }
+    uint64_t L = n;
+    for (uint64_t i = 0; i < n; i++) { R[i] = (uint32_t)i; pos[i] = (uint32_t)i; }
+    /* remove x from the remaining set */
+#define OR_REMOVE(x)                                   \
+    do {                                               \
+        uint32_t p_ = pos[(x)], y_ = R[L - 1];         \
+        R[p_] = y_;                                    \
+        pos[y_] = p_;                                  \
+        L--;                                           \
+    } while (0)
+    perm[0] = (uint32_t)s;
+    rad2[0] = INT64_MAX;
+    if (round_of) round_of[0] = 0;
+    OR_REMOVE((uint32_t)s);
+    for (uint64_t i = 0; i < n; i++) D[i] = d2key(key[i], key[s]);
+    uint64_t out = 1;
+    uint32_t seed_key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (uint32_t t = 0; out < m && L > 0; t++) {
+        /* the round's random subset of the remaining set */
+        uint64_t nc = 0;
+        if (sample_size == 0) {
+            for (uint64_t u = 0; u < L; u++) cand[nc++] = R[u];
+        } else {
+            for (uint32_t u = 0; u < sample_size; u++) {
+                uint32_t ctr[4] = {part_id, t, u, 1u}, w[4];
+                or_philox4x32_10(ctr, seed_key, w);
+                uint64_t p = ((uint64_t)w[0] * L) >> 32;
+                uint32_t c = R[p];
+                if (!mark[c]) { mark[c] = 1; cand[nc++] = c; }
+            }
+            for (uint64_t u = 0; u < nc; u++) mark[cand[u]] = 0;
+        }
+        uint64_t mt = 1 + (step ? t / step : 0);
+        uint64_t first = out;
+        /* the mt candidates farthest from the surfels chosen before this round */
+        for (uint64_t r = 0; r < mt && out < m && r < nc; r++) {
+            uint64_t best = nc;
+            for (uint64_t u = 0; u < nc; u++) {
+                uint32_t c = cand[u];
+                if (mark[c]) continue;
+                if (best == nc || D[c] > D[cand[best]] || (D[c] == D[cand[best]] && c < cand[best])) best = u;
+            }
+            uint32_t c = cand[best];
+            mark[c] = 1;
+            int64_t r2 = D[c];
+            for (uint64_t q = first; q < out; q++) {
+                int64_t d = d2key(key[c], key[perm[q]]);
+                if (d < r2) r2 = d;
+            }
+            perm[out] = c;
+            rad2[out] = r2;
+            if (round_of) round_of[out] = t;
+            out++;
+        }
+        for (uint64_t q = first; q < out; q++) {
+            mark[perm[q]] = 0;
+            OR_REMOVE(perm[q]);
+        }
+        /* distances of every point to the chosen set */
+        for (uint64_t q = first; q < out; q++) {
+            uint64_t j = perm[q];
+            for (uint64_t i = 0; i < n; i++) {
+                int64_t d = d2key(key[i], key[j]);
+                if (d < D[i]) D[i] = d;
+            }
+        }
+    }
+#undef OR_REMOVE
+    free(D); free(R); free(pos); free(cand); free(mark);
+    return 0;
+}
