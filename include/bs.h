@@ -91,12 +91,23 @@ typedef struct {
  *      key = {seed & 0xffffffff, seed >> 32}), unless start >= 0.
  *  start     : explicit starting index (< n), or -1 for the Philox start.
  *  max_count : order only the first max_count surfels (0 = all); the result is
- *      exactly the prefix of the full ordering (Sec. 3.2 stops at a target count). */
+ *      exactly the prefix of the full ordering (Sec. 3.2 stops at a target count).
+ *  variant 1 (the paper's randomised progressive sampling, Sec. 3.2): the remaining
+ *      set is an index array with swap-with-last removal; round t draws sample_size
+ *      positions with replacement, position u = (w * |R|) >> 32 with w = word 0 of
+ *      Philox4x32-10(ctr = {part_id, t, u, 1}, key = seed), and appends the
+ *      1 + t / sample_step distinct sampled points farthest from the surfels chosen
+ *      before the round (ties to the lowest index), removing them in that order.
+ *      rad2[k] is then the squared distance of pick k to every earlier pick. */
 typedef struct {
     uint64_t seed;
     uint32_t part_id;
     int64_t start;
     uint64_t max_count;
+    int32_t variant;       /* 0: exact greedy permutation; 1: the randomised sampler of Sec. 3.2 */
+    uint32_t sample_size;  /* variant 1: random subset size per round, 1..256 (paper: ~200) */
+    uint32_t sample_step;  /* variant 1: one more pick per round after every sample_step rounds
+                              (paper: k = 500); 0 = always one pick per round */
 } bs_order_opts;
 
 /* bs_sample_visible -- initial surfel set (Sec. 3.1).

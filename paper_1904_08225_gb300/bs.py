@@ -48,7 +48,8 @@ class Surfels(C.Structure):
 
 
 class OrderOpts(C.Structure):
-    _fields_ = [("seed", C.c_uint64), ("part_id", C.c_uint32), ("start", C.c_int64), ("max_count", C.c_uint64)]
+    _fields_ = [("seed", C.c_uint64), ("part_id", C.c_uint32), ("start", C.c_int64), ("max_count", C.c_uint64),
+                ("variant", C.c_int32), ("sample_size", C.c_uint32), ("sample_step", C.c_uint32)]
 
 
 _lib = None
@@ -197,12 +198,14 @@ def sample_visible_batched(meshes, res, dirs, stream=None, caps=None):
     return res_list
 
 
-def _opts(seed=0, part_id=0, start=-1, max_count=0) -> OrderOpts:
-    return OrderOpts(int(seed) & (2**64 - 1), int(part_id), int(start), int(max_count))
+def _opts(seed=0, part_id=0, start=-1, max_count=0, variant=0, sample_size=200, sample_step=500) -> OrderOpts:
+    return OrderOpts(int(seed) & (2**64 - 1), int(part_id), int(start), int(max_count), int(variant),
+                     int(sample_size) if variant == 1 else 0, int(sample_step) if variant == 1 else 0)
 
 
 def order(key, start: int = -1, seed: int = 0, part_id: int = 0, max_count: int = 0, scale: float = 1.0,
-          stream=None, want_radius: bool = True, out=None):
+          stream=None, want_radius: bool = True, out=None, variant: int = 0, sample_size: int = 200,
+          sample_step: int = 500):
     """Exact greedy permutation of one part (bs_order).  key: CUDA int64 tensor (N,).
 
     Returns (perm int32 view of u32 (m,), rad2 int64 (m,), radius float32 (m,) or None).
@@ -218,7 +221,7 @@ def order(key, start: int = -1, seed: int = 0, part_id: int = 0, max_count: int 
     else:
         perm, rad2, radius = out
     s = Surfels(key.data_ptr(), None, None, None, n, n, (C.c_float * 3)(), float(scale))
-    o = _opts(seed, part_id, start, max_count)
+    o = _opts(seed, part_id, start, max_count, variant, sample_size, sample_step)
     st = lib.bs_order(C.byref(s), C.byref(o), _ptr(perm), _ptr(rad2), _ptr(radius), _stream(stream))
     _check(st, "bs_order")
     return perm, rad2, radius
@@ -246,7 +249,7 @@ def order_noalloc(key, start: int = -1, seed: int = 0, part_id: int = 0, max_cou
 
 
 def order_batched(keys, starts=None, seeds=None, part_ids=None, max_counts=None, scales=None, stream=None,
-                  want_radius: bool = True, outs=None):
+                  want_radius: bool = True, outs=None, variants=None, sample_size: int = 200, sample_step: int = 500):
     """bs_order_batched over a list of CUDA int64 key tensors; returns a list of (perm, rad2, radius)."""
     torch = _torch()
     lib = load()
@@ -272,7 +275,8 @@ def order_batched(keys, starts=None, seeds=None, part_ids=None, max_counts=None,
         else:
             perm, rad2, radius = outs[i]
         parts[i] = Surfels(k.data_ptr(), None, None, None, n, n, (C.c_float * 3)(), float(scales[i]))
-        opts[i] = _opts(seeds[i], part_ids[i], starts[i], max_counts[i])
+        opts[i] = _opts(seeds[i], part_ids[i], starts[i], max_counts[i], variants[i] if variants else 0,
+                        sample_size, sample_step)
         pp[i] = perm.data_ptr()
         rp[i] = rad2.data_ptr()
         fp[i] = radius.data_ptr() if radius is not None else None
@@ -296,10 +300,10 @@ class Server:
         self._m = {}
 
     def submit(self, key: np.ndarray, scale: float = 1.0, start: int = -1, seed: int = 0, part_id: int = 0,
-               max_count: int = 0) -> int:
+               max_count: int = 0, variant: int = 0, sample_size: int = 200, sample_step: int = 500) -> int:
         k = np.ascontiguousarray(key, dtype=np.uint64)
         t = C.c_uint64(0)
-        o = _opts(seed, part_id, start, max_count)
+        o = _opts(seed, part_id, start, max_count, variant, sample_size, sample_step)
         st = self._lib.bs_server_submit(self._h, k.ctypes.data_as(C.c_void_p), k.shape[0], float(scale), C.byref(o),
                                         C.byref(t))
         _check(st, "bs_server_submit")

@@ -46,7 +46,17 @@ static bs_status make_part(const bs_surfels *s, const bs_order_opts *opts, uint3
         start = start_from_seed(s->n, opts->seed, opts->part_id);
     }
     const uint64_t m = (opts->max_count == 0 || opts->max_count > s->n) ? s->n : opts->max_count;
+    if (opts->variant != 0 && opts->variant != 1) { set_error("bs_order: variant=%d not 0 or 1", opts->variant); return BS_EINVAL; }
+    if (opts->variant == 1 && (opts->sample_size < 1 || opts->sample_size > 256)) {
+        set_error("bs_order: sample_size=%u outside [1, 256]", opts->sample_size);
+        return BS_EINVAL;
+    }
     memset(&p, 0, sizeof(p));
+    p.variant = (uint32_t)opts->variant;
+    p.sample_size = opts->sample_size;
+    p.sample_step = opts->sample_step;
+    p.part_id = opts->part_id;
+    p.seed = opts->seed;
     p.key = s->key;
     p.perm = perm;
     p.rad2 = rad2;
@@ -218,7 +228,7 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 static size_t req_bytes(uint64_t n) {
     // key + outputs + ordering scratch (D, bucket and group records) + slack
     const uint64_t nb = (n + 31) / 32, ng = (nb + 31) / 32;
-    return (size_t)(n * 8 + n * 4 + n * 8 + n * 4) + (size_t)(n * 8 + nb * 32 + ng * 32) + 4096;
+    return (size_t)(n * 8 + n * 4 + n * 8 + n * 4) + (size_t)(n * 8 + n * 8 + nb * 32 + ng * 32) + 4096;
 }
 
 static void retire(bs_server *S, SrvSlot &slot) {
@@ -276,6 +286,11 @@ static void launch_batch(bs_server *S, SrvSlot &slot, std::vector<SrvReq *> &bat
         p.key = dk; p.perm = dp; p.rad2 = dr; p.radius = df; p.scale = r->scale;
         p.n = (uint32_t)r->n; p.m = (uint32_t)r->m;
         p.start = (uint32_t)(r->opts.start >= 0 ? (uint64_t)r->opts.start : start_from_seed(r->n, r->opts.seed, r->opts.part_id));
+        p.variant = (uint32_t)r->opts.variant;
+        p.sample_size = r->opts.sample_size;
+        p.sample_step = r->opts.sample_step;
+        p.part_id = r->opts.part_id;
+        p.seed = r->opts.seed;
         parts.push_back(p);
         run.push_back(r);
         r->state = 1;
@@ -373,6 +388,11 @@ bs_status bs_server_submit(bs_server *S, const uint64_t *key, uint64_t n, double
     if (!S || !key || !opts || !ticket) { set_error("bs_server_submit: NULL argument"); return BS_EINVAL; }
     if (n == 0 || n > BS_MAX_POINTS) { set_error("bs_server_submit: n=%llu outside [1,%u]", (unsigned long long)n, BS_MAX_POINTS); return BS_EINVAL; }
     if (opts->start >= 0 && (uint64_t)opts->start >= n) { set_error("bs_server_submit: start >= n"); return BS_EINVAL; }
+    if (opts->variant != 0 && opts->variant != 1) { set_error("bs_server_submit: variant must be 0 or 1"); return BS_EINVAL; }
+    if (opts->variant == 1 && (opts->sample_size < 1 || opts->sample_size > 256)) {
+        set_error("bs_server_submit: sample_size outside [1, 256]");
+        return BS_EINVAL;
+    }
     if (!(scale > 0.0)) { set_error("bs_server_submit: scale must be > 0"); return BS_EINVAL; }
     SrvReq *r = new (std::nothrow) SrvReq();
     if (!r) return BS_ENOMEM;

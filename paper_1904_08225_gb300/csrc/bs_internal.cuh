@@ -116,8 +116,11 @@ struct PartDesc {
     int64_t *D;
     uint64_t *bkey, *bq, *blo, *bhi;
     uint64_t *gkey, *gq, *glo, *ghi;
+    uint32_t *R, *pos;  // variant 1: remaining set (index array) and each index's position in it
     double scale;
+    uint64_t seed;
     uint32_t n, m, start, nb, ng;
+    uint32_t variant, sample_size, sample_step, part_id;
 };
 
 }  // namespace bs

@@ -60,6 +60,10 @@ __global__ void __launch_bounds__(256) k_order_init(const PartDesc *__restrict__
         if (valid) {
             d = i == P.start ? -1 : dist2(k, qs);
             P.D[i] = d;
+            if (P.variant == 1) {
+                P.R[i] = i;
+                P.pos[i] = i;
+            }
         }
         const uint64_t nk = valid ? (((uint64_t)(d + 1) << 5) | (uint64_t)(31 - lane)) : 0ull;
         const uint64_t bk = warp_max_u64(nk);
@@ -210,8 +214,10 @@ constexpr int CPL = CAP / 32;
 constexpr int MAXP = 64;     // picks per round (pick sets are 64-bit masks)
 constexpr int MAX_SG = 192;  // super-groups: BS_MAX_POINTS / 32768
 constexpr int TIE_GROUPS = 8;  // groups a tie window may span
+constexpr int SMAX = 256;      // variant 1: largest random subset per round
+constexpr int SPL = SMAX / 32;
 constexpr int NB_SMEM = 2048;  // parts with at most this many buckets keep bucket records in shared memory
-constexpr size_t ROUNDS_SMEM_STATIC = 12 * 1024;  // bound on the kernel's static shared memory
+constexpr size_t ROUNDS_SMEM_STATIC = 18 * 1024;  // bound on the kernel's static shared memory
 constexpr size_t SMEM_LIMIT = 227 * 1024;
 
 // shared-memory bucket capacity for a launch whose largest part has ngmax groups
@@ -235,7 +241,7 @@ __device__ __forceinline__ uint64_t pick_mask(uint32_t np, const uint32_t *pi, c
 template <int T>
 __global__ void __launch_bounds__(T) k_order_rounds(const PartDesc *__restrict__ parts, int nparts,
                                                     uint32_t *__restrict__ next_part, int ngmax, int nbsm) {
-    static_assert(T >= CAP, "the candidate sort needs one thread per candidate");
+    static_assert(T >= CAP && T >= SMAX, "the candidate and sample sorts need one thread per entry");
     constexpr int NW = T / 32;
     extern __shared__ uint64_t sm[];
     uint64_t *s_bkey = sm;
@@ -254,6 +260,10 @@ __global__ void __launch_bounds__(T) k_order_rounds(const PartDesc *__restrict__
     __shared__ uint64_t s_pk[MAXP];
     __shared__ int64_t s_pd[MAXP];
     __shared__ uint32_t s_pi[MAXP];
+    __shared__ uint32_t s_sc[SMAX];   // variant 1: the round's sample (index), sorted by index
+    __shared__ int64_t s_sd[SMAX];    //            its distance to the chosen set
+    __shared__ uint64_t s_sk[SMAX];   //            its position
+    __shared__ uint32_t s_ppos[MAXP], s_tail[MAXP];
     __shared__ uint32_t s_part, s_ccnt, s_gcnt, s_sgcnt, s_npick, s_icut;
     __shared__ int s_shift;
     __shared__ int64_t s_tieD;
@@ -291,8 +301,14 @@ __global__ void __launch_bounds__(T) k_order_rounds(const PartDesc *__restrict__
             P.rad2[0] = INT64_MAX;
             s_shift = 3;
             s_tieD = -2;
+            if (P.variant == 1) {  // remove the start from the remaining set (swap with the last)
+                const uint32_t y = P.R[n - 1];
+                P.R[P.start] = y;
+                P.pos[y] = P.start;
+            }
         }
         __syncthreads();
+        uint32_t round_t = 0;
         for (uint32_t sg = warp; sg < ns; sg += NW) {
             const uint32_t g = sg * 32 + lane;
             const bool vg = g < ng;
@@ -315,6 +331,107 @@ __global__ void __launch_bounds__(T) k_order_rounds(const PartDesc *__restrict__
         __syncthreads();
         uint32_t k = 1;
         while (k < m) {
+          if (P.variant == 1) {
+            // (S1) the round's random subset of the remaining set R[0, n - k)
+            const uint32_t L = n - k, S = P.sample_size;
+            uint32_t c = 0, slot = 0;
+            int64_t cd = 0;
+            uint64_t ck = 0;
+            if (threadIdx.x < S) {
+                const uint32_t ctr[4] = {P.part_id, round_t, threadIdx.x, 1u};
+                const uint32_t kk[2] = {(uint32_t)P.seed, (uint32_t)(P.seed >> 32)};
+                uint32_t w[4];
+                philox4x32_10(ctr, kk, w);
+                c = P.R[(uint32_t)(((uint64_t)w[0] * L) >> 32)];
+                s_sc[threadIdx.x] = c;
+                cd = Dg[c];
+                ck = key[c];
+            }
+            __syncthreads();
+            // (S2) sorted by index (equal entries adjacent): slot = #smaller + #equal before
+            if (threadIdx.x < S) {
+                for (uint32_t u = 0; u < S; ++u) {
+                    const uint32_t o = s_sc[u];
+                    slot += (o < c || (o == c && u < threadIdx.x)) ? 1u : 0u;
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x < S) {
+                s_sc[slot] = c;
+                s_sd[slot] = cd;
+                s_sk[slot] = ck;
+            }
+            __syncthreads();
+            // (S3) the m_t = 1 + t / step distinct samples farthest from the chosen set
+            //      (distances as of the round start), ties to the lowest index
+            if (warp == 0) {
+                uint32_t cs[SPL];
+                int64_t ds[SPL];
+                bool live[SPL];
+#pragma unroll
+                for (int u = 0; u < SPL; ++u) {
+                    const uint32_t sl = lane + 32 * u;
+                    live[u] = sl < S;
+                    cs[u] = live[u] ? s_sc[sl] : 0u;
+                    ds[u] = live[u] ? s_sd[sl] : 0;
+                }
+                const uint32_t mt = 1u + (P.sample_step ? round_t / P.sample_step : 0u);
+                const uint32_t budget = min(min(mt, (uint32_t)MAXP), m - k);
+                uint32_t np = 0;
+                while (np < budget) {
+                    uint64_t kmax = 0;
+#pragma unroll
+                    for (int u = 0; u < SPL; ++u)
+                        if (live[u]) kmax = max(kmax, ((uint64_t)(ds[u] + 1) << 8) | (uint64_t)(255 - (lane + 32 * u)));
+                    const uint64_t best = warp_max_u64(kmax);
+                    if (best == 0) break;
+                    const uint32_t sl = 255u - (uint32_t)(best & 255u);
+                    const uint32_t cb = s_sc[sl];
+                    if (lane == 0) {
+                        s_pi[np] = cb;
+                        s_pk[np] = s_sk[sl];
+                        s_pd[np] = (int64_t)(best >> 8) - 1;
+                    }
+                    ++np;
+#pragma unroll
+                    for (int u = 0; u < SPL; ++u)
+                        if (cs[u] == cb) live[u] = false;
+                }
+                if (lane == 0) s_npick = np;
+            }
+            __syncthreads();
+            const uint32_t npk = s_npick;
+            // (S4) rad2 of a pick: its distance to every earlier pick; gather what the removal needs
+            int64_t r2 = 0;
+            if (threadIdx.x < npk) {
+                r2 = s_pd[threadIdx.x];
+                const uint64_t q = s_pk[threadIdx.x];
+                for (uint32_t u = 0; u < threadIdx.x; ++u) r2 = min(r2, dist2(q, s_pk[u]));
+                s_ppos[threadIdx.x] = P.pos[s_pi[threadIdx.x]];
+                s_tail[threadIdx.x] = P.R[L - npk + threadIdx.x];
+            }
+            __syncthreads();
+            if (threadIdx.x < npk) s_pd[threadIdx.x] = r2;
+            // (S5) remove the picks in pick order, each swapped with the current last entry;
+            //      the last entries all lie in the tail window [L - npk, L) held in s_tail
+            if (threadIdx.x == 0) {
+                const uint32_t base = L - npk;
+                for (uint32_t q = 0; q < npk; ++q) {
+                    const uint32_t pp = s_ppos[q];
+                    const uint32_t y = s_tail[L - q - 1 - base];
+                    if (pp >= base) {
+                        s_tail[pp - base] = y;
+                    } else {
+                        P.R[pp] = y;
+                        P.pos[y] = pp;
+                    }
+                    for (uint32_t r = q + 1; r < npk; ++r)
+                        if (s_pi[r] == y) s_ppos[r] = pp;
+                }
+            }
+            ++round_t;
+            __syncthreads();
+          } else {
             // (1) current maximum (every warp computes it; no barrier needed)
             uint64_t top = 0;
             for (uint32_t sg = lane; sg < ns; sg += 32) top = max(top, ((s_sgkey[sg] >> 15) << 8) | (uint64_t)(255 - sg));
@@ -497,7 +614,9 @@ __global__ void __launch_bounds__(T) k_order_rounds(const PartDesc *__restrict__
                 }
                 if (lane == 0) s_npick = np;
             }
+            if (threadIdx.x == 0 && !tie && ccnt < CAP / 4 && shift > 1) s_shift = shift - 1;
             __syncthreads();
+          }
             const uint32_t np = s_npick;
             // (6) apply the round's picks to the whole part
             for (uint32_t t = threadIdx.x; t < np; t += T) {
@@ -633,7 +752,6 @@ __global__ void __launch_bounds__(T) k_order_rounds(const PartDesc *__restrict__
                 const uint64_t sk = warp_max_u64(cand);
                 if (lane == 0) s_sgkey[sg] = sk;
             }
-            if (threadIdx.x == 0 && !tie && ccnt < CAP / 4 && shift > 1) s_shift = shift - 1;
             k += np;
             __syncthreads();
         }
@@ -706,14 +824,14 @@ bs_status order_last_launch_ms(int which, double *ms) {
 
 template <int T>
 static cudaError_t launch_loop(const PartDesc *d_parts, int nparts, uint32_t *d_next, int ngmax, int grid,
-                               cudaStream_t stream) {
+                               cudaStream_t stream, int algo) {
     cudaError_t e;
-    if (g_order_algo == 1) {
+    if (algo == 1) {
         const size_t smem = (size_t)ngmax * 36;
         e = cudaFuncSetAttribute(k_order_loop<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k_order_loop<T><<<grid, T, smem, stream>>>(d_parts, nparts, d_next, ngmax);
-    } else if constexpr (T >= CAP) {
+    } else if constexpr (T >= CAP && T >= SMAX) {
         const size_t smem = rounds_smem(ngmax);
         e = cudaFuncSetAttribute(k_order_rounds<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -725,14 +843,14 @@ static cudaError_t launch_loop(const PartDesc *d_parts, int nparts, uint32_t *d_
 }
 
 template <int T>
-static int occupancy(int ngmax) {
+static int occupancy(int ngmax, int algo) {
     int blocks = 0;
     cudaError_t e;
-    if (g_order_algo == 1) {
+    if (algo == 1) {
         const size_t smem = (size_t)ngmax * 36;
         cudaFuncSetAttribute(k_order_loop<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_order_loop<T>, T, smem);
-    } else if constexpr (T >= CAP) {
+    } else if constexpr (T >= CAP && T >= SMAX) {
         const size_t smem = rounds_smem(ngmax);
         cudaFuncSetAttribute(k_order_rounds<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_order_rounds<T>, T, smem);
@@ -747,9 +865,9 @@ static int occupancy(int ngmax) {
     return std::max(blocks, 1);
 }
 
-static int pick_threads(int ngmax, bool batched) {
-    if (g_loop_threads_override) return g_order_algo == 2 ? std::max(g_loop_threads_override, 128) : g_loop_threads_override;
-    if (g_order_algo == 2) return ngmax <= 8 ? 256 : 512;  // measured: 16 warps per part beat more resident parts
+static int pick_threads(int ngmax, bool batched, int algo) {
+    if (g_loop_threads_override) return algo == 2 ? std::max(g_loop_threads_override, 256) : g_loop_threads_override;
+    if (algo == 2) return ngmax <= 8 ? 256 : 512;  // measured: 16 warps per part beat more resident parts
     if (batched) return ngmax > 256 ? 256 : 128;
     if (ngmax <= 32) return 128;
     if (ngmax <= 512) return 256;
@@ -758,23 +876,23 @@ static int pick_threads(int ngmax, bool batched) {
 
 // one persistent loop launch over parts[0..nparts) with T threads per CTA
 static cudaError_t launch_set(const PartDesc *d_parts, int nparts, uint32_t *d_next, int ngmax, int T, int sms,
-                              cudaStream_t stream) {
+                              cudaStream_t stream, int algo) {
     int per_sm = 1;
     switch (T) {
-        case 64: per_sm = occupancy<64>(ngmax); break;
-        case 128: per_sm = occupancy<128>(ngmax); break;
-        case 256: per_sm = occupancy<256>(ngmax); break;
-        case 512: per_sm = occupancy<512>(ngmax); break;
-        default: per_sm = occupancy<1024>(ngmax); break;
+        case 64: per_sm = occupancy<64>(ngmax, algo); break;
+        case 128: per_sm = occupancy<128>(ngmax, algo); break;
+        case 256: per_sm = occupancy<256>(ngmax, algo); break;
+        case 512: per_sm = occupancy<512>(ngmax, algo); break;
+        default: per_sm = occupancy<1024>(ngmax, algo); break;
     }
     if (g_ctas_per_sm_override) per_sm = std::min(per_sm, g_ctas_per_sm_override);
     const int grid = std::max(1, std::min(nparts, sms * per_sm));
     switch (T) {
-        case 64: return launch_loop<64>(d_parts, nparts, d_next, ngmax, grid, stream);
-        case 128: return launch_loop<128>(d_parts, nparts, d_next, ngmax, grid, stream);
-        case 256: return launch_loop<256>(d_parts, nparts, d_next, ngmax, grid, stream);
-        case 512: return launch_loop<512>(d_parts, nparts, d_next, ngmax, grid, stream);
-        default: return launch_loop<1024>(d_parts, nparts, d_next, ngmax, grid, stream);
+        case 64: return launch_loop<64>(d_parts, nparts, d_next, ngmax, grid, stream, algo);
+        case 128: return launch_loop<128>(d_parts, nparts, d_next, ngmax, grid, stream, algo);
+        case 256: return launch_loop<256>(d_parts, nparts, d_next, ngmax, grid, stream, algo);
+        case 512: return launch_loop<512>(d_parts, nparts, d_next, ngmax, grid, stream, algo);
+        default: return launch_loop<1024>(d_parts, nparts, d_next, ngmax, grid, stream, algo);
     }
 }
 
@@ -793,6 +911,7 @@ bs_status order_parts(std::vector<PartDesc> &hp, cudaStream_t stream, bool batch
         p.ng = (p.nb + 31) / 32;
         ngmax = std::max(ngmax, p.ng);
         total += align_up((size_t)p.n * 8) + 4 * align_up((size_t)p.nb * 8) + 4 * align_up((size_t)p.ng * 8);
+        if (p.variant == 1) total += 2 * align_up((size_t)p.n * 4);
         if (!p.rad2) total += align_up((size_t)p.m * 8);
     }
     const size_t desc_bytes = align_up((size_t)nparts * sizeof(PartDesc));
@@ -824,6 +943,10 @@ bs_status order_parts(std::vector<PartDesc> &hp, cudaStream_t stream, bool batch
         p.glo = (uint64_t *)take((size_t)p.ng * 8);
         p.ghi = (uint64_t *)take((size_t)p.ng * 8);
         if (!p.rad2) p.rad2 = (int64_t *)take((size_t)p.m * 8);
+        if (p.variant == 1) {
+            p.R = (uint32_t *)take((size_t)p.n * 4);
+            p.pos = (uint32_t *)take((size_t)p.n * 4);
+        }
         gofs[r] = total_groups;
         total_groups += p.ng;
         sorted[r] = p;
@@ -844,8 +967,12 @@ bs_status order_parts(std::vector<PartDesc> &hp, cudaStream_t stream, bool batch
         int dev = 0, sms = 152;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        // the one-pick-per-step kernel only knows the exact greedy permutation
+        bool sampled = false;
+        for (const auto &q : sorted) sampled |= q.variant == 1;
+        const int algo = sampled ? 2 : g_order_algo;
         timing_mark(1, 0, stream);
-        e = launch_set(d_parts, nparts, d_next, (int)ngmax, pick_threads((int)ngmax, batched), sms, stream);
+        e = launch_set(d_parts, nparts, d_next, (int)ngmax, pick_threads((int)ngmax, batched, algo), sms, stream, algo);
         timing_mark(1, 1, stream);
         if (e != cudaSuccess) {
             set_error("bs_order: loop launch failed: %s", cudaGetErrorString(e));
@@ -923,6 +1050,10 @@ bs_status noalloc_scratch(char **out) {
 }  // namespace
 
 bs_status order_part_noalloc(PartDesc p, cudaStream_t stream) {
+    if (p.variant != 0) {
+        set_error("bs_order_noalloc: only the exact ordering (variant 0) runs without allocation");
+        return BS_EINVAL;
+    }
     if (p.n > NOALLOC_MAX_POINTS) {
         set_error("bs_order_noalloc: n=%u exceeds the fixed scratch limit of %u points", p.n, NOALLOC_MAX_POINTS);
         return BS_EOVERFLOW;
@@ -950,13 +1081,13 @@ bs_status order_part_noalloc(PartDesc p, cudaStream_t stream) {
     if (e == cudaSuccess) e = cudaMemsetAsync(d_next, 0, 8, stream);  // d_next[0] counter, d_next[1] = gofs[0] = 0
     if (e != cudaSuccess) { set_error("bs_order_noalloc: descriptor upload failed: %s", cudaGetErrorString(e)); return BS_ECUDA; }
     k_order_init<<<(p.ng + 7) / 8, 256, 0, stream>>>(d_desc, d_next + 1, 1, p.ng);
-    const int T = pick_threads((int)p.ng, false);
+    const int T = pick_threads((int)p.ng, false, g_order_algo);
     switch (T) {
-        case 64: e = launch_loop<64>(d_desc, 1, d_next, (int)p.ng, 1, stream); break;
-        case 128: e = launch_loop<128>(d_desc, 1, d_next, (int)p.ng, 1, stream); break;
-        case 256: e = launch_loop<256>(d_desc, 1, d_next, (int)p.ng, 1, stream); break;
-        case 512: e = launch_loop<512>(d_desc, 1, d_next, (int)p.ng, 1, stream); break;
-        default: e = launch_loop<1024>(d_desc, 1, d_next, (int)p.ng, 1, stream); break;
+        case 64: e = launch_loop<64>(d_desc, 1, d_next, (int)p.ng, 1, stream, g_order_algo); break;
+        case 128: e = launch_loop<128>(d_desc, 1, d_next, (int)p.ng, 1, stream, g_order_algo); break;
+        case 256: e = launch_loop<256>(d_desc, 1, d_next, (int)p.ng, 1, stream, g_order_algo); break;
+        case 512: e = launch_loop<512>(d_desc, 1, d_next, (int)p.ng, 1, stream, g_order_algo); break;
+        default: e = launch_loop<1024>(d_desc, 1, d_next, (int)p.ng, 1, stream, g_order_algo); break;
     }
     if (e == cudaSuccess && p.radius) {
         k_radius<<<dim3(std::min<uint32_t>((p.m + 255) / 256, 64), 1), 256, 0, stream>>>(d_desc, 1);

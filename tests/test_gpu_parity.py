@@ -363,3 +363,57 @@ def test_sample_batched_overflow_and_invalid(bs):
     with pytest.raises(bs.BsError) as e:
         bs.sample_visible(_dev(ms[0].xyz), _dev(tri_bad.view(np.int32)), None, W.AXIS_DIRS, 32)
     assert e.value.status == bs.BS_EINVAL
+
+
+@pytest.mark.parametrize("sample_size,step,max_count", [(200, 500, 5000), (200, 20, 6000), (1, 0, 800),
+                                                        (256, 3, 0), (37, 7, 0)])
+def test_sampled_variant_matches_oracle(bs, sample_size, step, max_count):
+    """The paper's randomised progressive sampler (Sec. 3.2) on the GPU equals the oracle's."""
+    m = W.torus(nu=64, nv=32, seed=4)
+    ref, mn, s = oracle.sample_mesh(m, W.AXIS_DIRS, 80)
+    key_np = ref["key"]
+    if max_count == 0:
+        key_np = key_np[::4].copy()  # full orderings on a smaller part
+    key = _dev(key_np.view(np.int64))
+    for seed in (0, 99):
+        perm, rad2, radius = bs.order(key, seed=seed, part_id=3, max_count=max_count, scale=s, variant=1,
+                                      sample_size=sample_size, sample_step=step)
+        st = oracle.start_index(len(key_np), seed=seed, part_id=3)
+        rp, rr = oracle.sampled(key_np, st, max_count=max_count, seed=seed, part_id=3, sample_size=sample_size,
+                                step=step)
+        assert np.array_equal(_np(perm, np.uint32), rp)
+        assert np.array_equal(_np(rad2), rr)
+        assert np.array_equal(_np(radius).view(np.uint32), oracle.radius(rr, s).view(np.uint32))
+
+
+def test_sampled_and_exact_in_one_batch_and_server(bs):
+    g = np.random.default_rng(21)
+    keys_np = [oracle.pack(np.unique(g.integers(0, 1 << 20, size=(n + 9, 3)), axis=0)[:n]) for n in (3000, 900, 70001, 5)]
+    keys = [_dev(k.view(np.int64)) for k in keys_np]
+    variants = [1, 0, 1, 1]
+    res = bs.order_batched(keys, seeds=[5] * 4, part_ids=[0, 1, 2, 3], max_counts=[0, 0, 4000, 0],
+                           variants=variants, sample_size=200, sample_step=50)
+    for i, (perm, rad2, _) in enumerate(res):
+        st = oracle.start_index(len(keys_np[i]), seed=5, part_id=i)
+        if variants[i] == 1:
+            rp, rr = oracle.sampled(keys_np[i], st, max_count=[0, 0, 4000, 0][i], seed=5, part_id=i, sample_size=200,
+                                    step=50)
+        else:
+            rp, rr = oracle.greedy(keys_np[i], st)
+        assert np.array_equal(_np(perm, np.uint32), rp), i
+        assert np.array_equal(_np(rad2), rr), i
+    with bs.Server(budget_bytes=1 << 30) as srv:
+        t = srv.submit(keys_np[0], seed=5, part_id=0, variant=1, sample_size=200, sample_step=50)
+        r = None
+        while r is None:
+            r = srv.poll(t)
+            time.sleep(0.0005)
+    rp, rr = oracle.sampled(keys_np[0], oracle.start_index(len(keys_np[0]), seed=5), seed=5, part_id=0,
+                            sample_size=200, step=50)
+    assert np.array_equal(r[0], rp) and np.array_equal(r[1], rr)
+    with pytest.raises(bs.BsError) as e:
+        bs.order(keys[0], variant=1, sample_size=0)
+    assert e.value.status == bs.BS_EINVAL
+    with pytest.raises(bs.BsError) as e:
+        bs.order(keys[0], variant=1, sample_size=257)
+    assert e.value.status == bs.BS_EINVAL
