@@ -64,6 +64,10 @@ def _load():
             lib.or_sampled.argtypes = [P, C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32,
                                        C.c_uint32, P, P, P]
             lib.or_sampled.restype = C.c_int
+            lib.or_prefix_median_nn.argtypes = [P, P, C.c_uint64]
+            lib.or_prefix_median_nn.restype = C.c_int64
+            lib.or_prefix_for_radius.argtypes = [P, C.c_uint64, C.c_int64]
+            lib.or_prefix_for_radius.restype = C.c_uint64
             lib.or_num_threads.restype = C.c_int
             _lib = lib
     return _lib
@@ -197,6 +201,19 @@ def sampled(key: np.ndarray, start: int, max_count: int = 0, seed: int = 0, part
                           _p(perm), _p(rad2), _p(rnd)) != 0:
         raise ValueError("bad sampled arguments")
     return (perm, rad2, rnd) if rounds else (perm, rad2)
+
+
+def prefix_median_nn(key: np.ndarray, perm: np.ndarray, pm: int) -> int:
+    """Sec. 4.1 r_m^2: lower-median squared nearest-neighbour distance inside the first pm surfels."""
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    p = np.ascontiguousarray(perm, dtype=np.uint32)
+    return int(_load().or_prefix_median_nn(_p(k), _p(p), pm))
+
+
+def prefix_for_radius(rad2: np.ndarray, r2: int) -> int:
+    """Sec. 4.1: shortest prefix whose reach sqrt(rad2[p]) is at most r (m if none)."""
+    r = np.ascontiguousarray(rad2, dtype=np.int64)
+    return int(_load().or_prefix_for_radius(_p(r), r.shape[0], r2))
 
 
 def radius(rad2: np.ndarray, scale: float) -> np.ndarray:

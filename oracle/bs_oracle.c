@@ -635,3 +635,45 @@ int or_sampled(const uint64_t *key, uint64_t n, uint64_t s, uint64_t max_count, 
     free(D); free(R); free(pos); free(cand); free(mark);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Prefix selection (Sec. 4.1).                                              */
+/* r_m: the median of the nearest-neighbour distances inside the first pm    */
+/* surfels of an ordering (the lower median, the ceil(pm/2)-th smallest      */
+/* squared distance; 0 for pm < 2).                                          */
+/* Exact prefix for a radius: prefix p (entries 0..p-1) reaches every point  */
+/* within sqrt(rad2[p]); the shortest prefix whose reach is at most r is     */
+/* the smallest p >= 1 with rad2[p] <= r^2, or m if no ordered entry has it. */
+/* ------------------------------------------------------------------------ */
+static int cmp_i64(const void *a, const void *b)
+{
+    int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+int64_t or_prefix_median_nn(const uint64_t *key, const uint32_t *perm, uint64_t pm)
+{
+    if (pm < 2) return 0;
+    int64_t *nn = (int64_t *)malloc(pm * sizeof(int64_t));
+    if (!nn) return -1;
+    for (uint64_t a = 0; a < pm; a++) {
+        int64_t best = INT64_MAX;
+        for (uint64_t b = 0; b < pm; b++) {
+            if (a == b) continue;
+            int64_t d = d2key(key[perm[a]], key[perm[b]]);
+            if (d < best) best = d;
+        }
+        nn[a] = best;
+    }
+    qsort(nn, pm, sizeof(int64_t), cmp_i64);
+    int64_t r = nn[(pm + 1) / 2 - 1];
+    free(nn);
+    return r;
+}
+
+uint64_t or_prefix_for_radius(const int64_t *rad2, uint64_t m, int64_t r2)
+{
+    for (uint64_t p = 1; p < m; p++)
+        if (rad2[p] <= r2) return p;
+    return m;
+}
