@@ -157,6 +157,26 @@ bs_status bs_sample_visible_batched(const bs_mesh *meshes, const int *res, int n
 bs_status bs_order(const bs_surfels *s, const bs_order_opts *opts, uint32_t *perm, int64_t *rad2,
                    float *radius, void *cuda_stream);
 
+/* ---- Prefix selection at render time (Sec. 4.1). ---- */
+
+/* r_m^2: the median squared nearest-neighbour distance inside the first pm surfels
+ * of an ordering (the lower median, i.e. the ceil(pm/2)-th smallest; 0 for pm < 2).
+ * s->key and perm (at least pm entries) are device arrays; *rm2 is written on the
+ * host.  O(pm^2) work; pm <= min(n, 65536).  Synchronises the stream. */
+bs_status bs_prefix_median_nn(const bs_surfels *s, const uint32_t *perm, uint64_t pm, int64_t *rm2,
+                              void *cuda_stream);
+
+/* The shortest prefix of an exact ordering whose surfels, drawn with radius r,
+ * reach every point of the part: the smallest p >= 1 with rad2[p] <= r2 (a prefix
+ * of length p reaches every point within sqrt(rad2[p])), or m when no ordered entry
+ * qualifies.  rad2: device output of bs_order (variant 0), m entries; *p on the
+ * host.  Synchronises the stream. */
+bs_status bs_prefix_for_radius(const int64_t *rad2, uint64_t m, int64_t r2, uint64_t *p, void *cuda_stream);
+
+/* The paper's estimate of that prefix length, p(r) = pm * (r_m / r)^2, from the
+ * squared radii rm2 = r_m^2 and r2 = r^2 (same units); +inf for r2 <= 0. */
+double bs_prefix_estimate(uint64_t pm, int64_t rm2, int64_t r2);
+
 /* bs_order_batched -- bs_order for many independent parts in one persistent
  * launch (the per-node preprocessing of Sec. 3.4 run for a whole scene).
  *  parts : HOST array of nparts descriptors (device keys inside).

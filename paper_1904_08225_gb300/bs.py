@@ -24,7 +24,7 @@ INT64_MAX = (1 << 63) - 1
 # symbols include/bs.h declares; the library must export every one
 EXPORTS = ["bs_sample_visible", "bs_sample_visible_batched", "bs_order", "bs_order_noalloc", "bs_order_batched", "bs_server_create", "bs_server_submit",
            "bs_server_poll", "bs_server_times", "bs_server_destroy", "bs_set_tuning", "bs_last_launch_ms",
-           "bs_last_error"]
+           "bs_prefix_median_nn", "bs_prefix_for_radius", "bs_prefix_estimate", "bs_last_error"]
 
 
 class BsError(RuntimeError):
@@ -84,10 +84,14 @@ def load(build_if_stale: bool = True) -> C.CDLL:
             lib.bs_server_destroy.argtypes = [P]
             lib.bs_set_tuning.argtypes = [C.c_char_p, C.c_int]
             lib.bs_last_launch_ms.argtypes = [C.c_char_p, C.POINTER(C.c_double)]
+            lib.bs_prefix_median_nn.argtypes = [C.POINTER(Surfels), P, C.c_uint64, C.POINTER(C.c_int64), P]
+            lib.bs_prefix_for_radius.argtypes = [P, C.c_uint64, C.c_int64, C.POINTER(C.c_uint64), P]
+            lib.bs_prefix_estimate.argtypes = [C.c_uint64, C.c_int64, C.c_int64]
             lib.bs_last_error.restype = C.c_char_p
             for fn in EXPORTS[:-1]:
-                if fn != "bs_server_create" and fn != "bs_server_destroy":
+                if fn not in ("bs_server_create", "bs_server_destroy", "bs_prefix_estimate"):
                     getattr(lib, fn).restype = C.c_int
+            lib.bs_prefix_estimate.restype = C.c_double
             _lib = lib
     return _lib
 
@@ -127,6 +131,30 @@ def last_launch_ms(kernel: str) -> float:
     ms = C.c_double(0.0)
     _check(load().bs_last_launch_ms(kernel.encode(), C.byref(ms)), "bs_last_launch_ms")
     return ms.value
+
+
+def prefix_median_nn(key, perm, pm: int, stream=None) -> int:
+    """Sec. 4.1 r_m^2 (lower-median squared NN distance inside the first pm surfels)."""
+    lib = load()
+    s = Surfels(key.data_ptr(), None, None, None, key.shape[0], key.shape[0], (C.c_float * 3)(), 1.0)
+    out = C.c_int64(0)
+    _check(lib.bs_prefix_median_nn(C.byref(s), C.c_void_p(perm.data_ptr()), int(pm), C.byref(out), _stream(stream)),
+           "bs_prefix_median_nn")
+    return out.value
+
+
+def prefix_for_radius(rad2, r2: int, stream=None) -> int:
+    """Sec. 4.1: shortest prefix of an exact ordering reaching every point within sqrt(r2)."""
+    lib = load()
+    out = C.c_uint64(0)
+    _check(lib.bs_prefix_for_radius(C.c_void_p(rad2.data_ptr()), rad2.shape[0], int(r2), C.byref(out),
+                                    _stream(stream)), "bs_prefix_for_radius")
+    return out.value
+
+
+def prefix_estimate(pm: int, rm2: int, r2: int) -> float:
+    """The paper's p(r) = pm (r_m / r)^2."""
+    return load().bs_prefix_estimate(int(pm), int(rm2), int(r2))
 
 
 def sample_visible(xyz, tri, rgb, dirs, res: int, stream=None, cap: int | None = None):

@@ -1,6 +1,7 @@
 // bs_api.cu -- the extern "C" entry points of libbs (declared in include/bs.h):
 // argument validation, start-index selection, and the serving loop.
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
@@ -137,6 +138,21 @@ bs_status bs_order(const bs_surfels *s, const bs_order_opts *opts, uint32_t *per
     bs_status st = make_part(s, opts, perm, rad2, radius, parts[0]);
     if (st != BS_OK) return st;
     return order_parts(parts, (cudaStream_t)cuda_stream, false);
+}
+
+bs_status bs_prefix_median_nn(const bs_surfels *s, const uint32_t *perm, uint64_t pm, int64_t *rm2, void *cuda_stream) {
+    clear_error();
+    return prefix_median_nn(s, perm, pm, rm2, (cudaStream_t)cuda_stream);
+}
+
+bs_status bs_prefix_for_radius(const int64_t *rad2, uint64_t m, int64_t r2, uint64_t *p, void *cuda_stream) {
+    clear_error();
+    return prefix_for_radius(rad2, m, r2, p, (cudaStream_t)cuda_stream);
+}
+
+double bs_prefix_estimate(uint64_t pm, int64_t rm2, int64_t r2) {
+    if (r2 <= 0) return (double)INFINITY;
+    return (double)pm * (double)rm2 / (double)r2;
 }
 
 bs_status bs_order_noalloc(const bs_surfels *s, const bs_order_opts *opts, uint32_t *perm, int64_t *rad2,

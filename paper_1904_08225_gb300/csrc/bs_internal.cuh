@@ -125,12 +125,15 @@ struct PartDesc {
 
 }  // namespace bs
 
+#include <algorithm>
 #include <vector>
 
 namespace bs {
 
 bs_status order_parts(std::vector<PartDesc> &parts, cudaStream_t stream, bool batched);
 bs_status order_part_noalloc(PartDesc part, cudaStream_t stream);
+bs_status prefix_median_nn(const bs_surfels *s, const uint32_t *perm, uint64_t pm, int64_t *rm2, cudaStream_t stream);
+bs_status prefix_for_radius(const int64_t *rad2, uint64_t m, int64_t r2, uint64_t *p, cudaStream_t stream);
 void order_set_tuning(int threads, int ctas_per_sm);
 void order_set_kernel_timing(bool on);
 void order_set_algo(int algo);

@@ -1,0 +1,106 @@
+// bs_prefix.cu -- prefix selection at render time (Sec. 4.1): the median nearest-
+// neighbour distance r_m inside the first p_m surfels of an ordering, and the shortest
+// prefix whose surfels reach every point of the part within a radius.
+#include "bs_internal.cuh"
+
+namespace bs {
+
+// nn[a] = squared distance from prefix point a to its nearest other prefix point
+__global__ void __launch_bounds__(256) k_prefix_nn(const uint64_t *__restrict__ key, const uint32_t *__restrict__ perm,
+                                                   uint32_t pm, int64_t *__restrict__ nn) {
+    __shared__ int64_t red[8];
+    for (uint32_t a = blockIdx.x; a < pm; a += gridDim.x) {
+        const uint64_t qa = key[perm[a]];
+        int64_t best = INT64_MAX;
+        for (uint32_t b = threadIdx.x; b < pm; b += blockDim.x)
+            if (b != a) best = min(best, dist2(qa, key[perm[b]]));
+        const uint32_t hi = __reduce_min_sync(0xffffffffu, (uint32_t)((uint64_t)best >> 32));
+        const uint32_t lo = __reduce_min_sync(0xffffffffu, (uint32_t)((uint64_t)best >> 32) == hi ? (uint32_t)best : 0xffffffffu);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (int64_t)(((uint64_t)hi << 32) | lo);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int64_t v = red[0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = min(v, red[w]);
+            nn[a] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// the (rank+1)-th smallest of v[0..n) (values in [0, 2^62)), by a bitwise radix select in one block
+__global__ void __launch_bounds__(1024) k_select(const int64_t *__restrict__ v, uint32_t n, uint32_t rank,
+                                                 int64_t *__restrict__ out) {
+    __shared__ uint32_t red[32];
+    uint64_t prefix = 0;
+    uint32_t k = rank;
+    for (int bit = 61; bit >= 0; --bit) {
+        const uint64_t himask = bit == 61 ? 0ull : (~0ull << (bit + 1));
+        uint32_t c = 0;
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+            const uint64_t x = (uint64_t)v[i];
+            c += ((x & himask) == (prefix & himask) && ((x >> bit) & 1ull) == 0) ? 1u : 0u;
+        }
+        c = __reduce_add_sync(0xffffffffu, c);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+        __syncthreads();
+        uint32_t total = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) total += red[w];
+        __syncthreads();
+        if (k >= total) {
+            k -= total;
+            prefix |= 1ull << bit;
+        }
+    }
+    if (threadIdx.x == 0) *out = (int64_t)prefix;
+}
+
+// count of k in [1, m) with rad2[k] > r2
+__global__ void k_count_above(const int64_t *__restrict__ rad2, uint64_t m, int64_t r2,
+                              unsigned long long *__restrict__ count) {
+    uint32_t c = 0;
+    for (uint64_t k = 1 + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < m; k += (uint64_t)gridDim.x * blockDim.x)
+        c += rad2[k] > r2 ? 1u : 0u;
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, (unsigned long long)c);
+}
+
+bs_status prefix_median_nn(const bs_surfels *s, const uint32_t *perm, uint64_t pm, int64_t *rm2, cudaStream_t stream) {
+    if (!s || !s->key || !perm || !rm2) { set_error("bs_prefix_median_nn: NULL argument"); return BS_EINVAL; }
+    if (pm > s->n || pm > 65536) { set_error("bs_prefix_median_nn: pm=%llu exceeds n or 65536", (unsigned long long)pm); return BS_EINVAL; }
+    if (pm < 2) { *rm2 = 0; return BS_OK; }
+    int64_t *buf = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&buf, (pm + 1) * sizeof(int64_t), stream);
+    if (e != cudaSuccess) { cudaGetLastError(); set_error("bs_prefix_median_nn: scratch allocation failed"); return BS_ENOMEM; }
+    k_prefix_nn<<<(unsigned)std::min<uint64_t>(pm, 4096), 256, 0, stream>>>(s->key, perm, (uint32_t)pm, buf);
+    k_select<<<1, 1024, 0, stream>>>(buf, (uint32_t)pm, (uint32_t)((pm + 1) / 2 - 1), buf + pm);
+    int64_t h = 0;
+    e = cudaMemcpyAsync(&h, buf + pm, 8, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    cudaFreeAsync(buf, stream);
+    if (e != cudaSuccess) { set_error("bs_prefix_median_nn: %s", cudaGetErrorString(e)); return BS_ECUDA; }
+    *rm2 = h;
+    return BS_OK;
+}
+
+bs_status prefix_for_radius(const int64_t *rad2, uint64_t m, int64_t r2, uint64_t *p, cudaStream_t stream) {
+    if (!rad2 || !p || m == 0) { set_error("bs_prefix_for_radius: NULL argument or m = 0"); return BS_EINVAL; }
+    if (r2 < 0) { set_error("bs_prefix_for_radius: negative squared radius"); return BS_EINVAL; }
+    unsigned long long *cnt = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&cnt, 8, stream);
+    if (e != cudaSuccess) { cudaGetLastError(); set_error("bs_prefix_for_radius: scratch allocation failed"); return BS_ENOMEM; }
+    unsigned long long h = 0;
+    e = cudaMemsetAsync(cnt, 0, 8, stream);
+    if (e == cudaSuccess && m > 1) {
+        k_count_above<<<(unsigned)std::min<uint64_t>((m + 255) / 256, 1216), 256, 0, stream>>>(rad2, m, r2, cnt);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, cnt, 8, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    cudaFreeAsync(cnt, stream);
+    if (e != cudaSuccess) { set_error("bs_prefix_for_radius: %s", cudaGetErrorString(e)); return BS_ECUDA; }
+    // rad2[1..m) does not increase: the entries above r2 are exactly [1, 1 + h)
+    *p = std::min<uint64_t>(1 + h, m);
+    return BS_OK;
+}
+
+}  // namespace bs

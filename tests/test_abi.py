@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared():
     src = open(os.path.join(ROOT, "include", "bs.h")).read()
-    decl = r"^(?:bs_status|bs_server\s*\*|void|const char\s*\*)\s*(bs_[a-z_]+)\s*\("
+    decl = r"^(?:bs_status|bs_server\s*\*|void|double|const char\s*\*)\s*(bs_[a-z_]+)\s*\("
     return sorted(set(re.findall(decl, src, flags=re.M)))
 
 

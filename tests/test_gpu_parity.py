@@ -417,3 +417,35 @@ def test_sampled_and_exact_in_one_batch_and_server(bs):
     with pytest.raises(bs.BsError) as e:
         bs.order(keys[0], variant=1, sample_size=257)
     assert e.value.status == bs.BS_EINVAL
+
+
+def test_prefix_selection_matches_oracle(bs):
+    """Sec. 4.1 prefix selection: r_m of a prefix and the shortest covering prefix."""
+    m = W.torus(nu=64, nv=32, seed=1)
+    ref, mn, s = oracle.sample_mesh(m, W.AXIS_DIRS, 96)
+    key_np = ref["key"]
+    key = _dev(key_np.view(np.int64))
+    perm, rad2, _ = bs.order(key, seed=0)
+    P, R = _np(perm, np.uint32), _np(rad2)
+    for pm in [1, 2, 3, 100, 1000, 4097]:
+        assert bs.prefix_median_nn(key, perm, pm) == oracle.prefix_median_nn(key_np, P, pm), pm
+    for r2 in [0, 1, 17, int(R[5000]), int(R[5000]) - 1, int(R[1]), int(R[1]) + 1, 10**15]:
+        assert bs.prefix_for_radius(rad2, r2) == oracle.prefix_for_radius(R, r2), r2
+    part = rad2[:300]
+    assert bs.prefix_for_radius(part, 0) == oracle.prefix_for_radius(R[:300], 0) == 300
+    rm2 = bs.prefix_median_nn(key, perm, 1000)
+    assert bs.prefix_estimate(1000, rm2, rm2) == 1000.0
+    assert bs.prefix_estimate(1000, rm2, 4 * rm2) == 250.0
+
+
+def test_prefix_line_closed_form(bs):
+    m, h = 10, 5
+    n = 2**m + 1
+    p = np.zeros((n, 3), np.int64)
+    p[:, 2] = np.arange(n) * h
+    key = _dev(oracle.pack(p).view(np.int64))
+    perm, rad2, _ = bs.order(key, start=0)
+    for j in range(1, m + 1):
+        gap = 2 ** (m - j) * h
+        assert bs.prefix_median_nn(key, perm, 2**j + 1) == gap * gap
+        assert bs.prefix_for_radius(rad2, gap * gap) == 2 ** (j - 1) + 1
