@@ -129,6 +129,22 @@ def dist_setup():
     return world, rank, local
 
 
+def rank_specs(nparts: int, seed: int, rank: int):
+    """Each rank orders its own seeded batch (weak scaling: parts are independent, no
+    data-path collective)."""
+    return W.batch_parts(nparts, seed=seed + 7919 * rank)
+
+
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The step time the job is charged: the slowest rank's."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------------------
 # reference arm / CPU baseline: the oracle as it stands, on a bounded sample
 # ---------------------------------------------------------------------------
@@ -222,7 +238,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip plain / served / cpu baseline legs")
     args = ap.parse_args()
     world, rank, local = dist_setup()
-    specs = W.batch_parts(args.parts, seed=args.seed + 7919 * rank)
+    specs = rank_specs(args.parts, args.seed, rank)
     if args.impl == "reference":
         return reference_arm(args, specs, world, rank)
 
@@ -346,12 +362,7 @@ def main():
             fn()
         e1.record(stream)
         barrier()
-        ms = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(e0.elapsed_time(e1), dist, dev)
 
     for _ in range(args.warmup):
         step()
@@ -368,11 +379,7 @@ def main():
         loop_ms.append(bs.last_launch_ms("order_loop"))
     e1.record(stream)
     barrier()
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     clk = clocks.stop()
     bs.set_tuning("kernel_timing", 0)
     ms_step = ms / args.steps
