@@ -203,9 +203,13 @@ struct SrvReq {
     std::vector<int64_t> rad2;
     std::vector<float> radius;
     double t[3];
-    int state;  // 0 queued, 1 running, 2 done, 3 failed
+    int state;  // 0 queued, 1 running, 5 copying its result, 2 done, 3 failed, 4 collected
     bs_status err;
+    uint32_t flag;          // index of its completion flag in the slot
+    cudaEvent_t copied;     // recorded on the copy stream after its result copies
 };
+
+constexpr uint32_t SLOT_FLAGS = 4096;  // requests per launch (one completion flag each)
 
 struct SrvSlot {
     cudaStream_t stream = nullptr;
@@ -213,6 +217,8 @@ struct SrvSlot {
     std::vector<SrvReq *> reqs;
     char *stage = nullptr;  // pinned host staging for results
     size_t stage_cap = 0;
+    uint32_t *flags_h = nullptr;  // host-mapped completion flags, set by the ordering kernel
+    uint32_t *flags_d = nullptr;  // the same memory as the device sees it
     bool busy = false;
 };
 
@@ -227,6 +233,7 @@ struct bs_server {
     std::deque<bs::SrvReq *> queue;
     std::unordered_map<uint64_t, bs::SrvReq *> all;
     std::vector<bs::SrvSlot> slots;
+    cudaStream_t copy = nullptr;  // device-to-host copies of finished requests
     uint64_t next_ticket = 1;
     bool stop = false;
     std::thread driver;
@@ -247,23 +254,48 @@ static size_t req_bytes(uint64_t n) {
     return (size_t)(n * 8 + n * 4 + n * 8 + n * 4) + (size_t)(n * 8 + n * 8 + nb * 32 + ng * 32) + 4096;
 }
 
+// Releases a finished launch: device memory and budget (every request's result has
+// been copied by then, see driver_loop).
 static void retire(bs_server *S, SrvSlot &slot) {
-    const double t = S->now();
     for (SrvReq *r : slot.reqs) {
-        if (r->state == 1) {
-            memcpy(r->perm.data(), slot.stage + r->stage_off, r->m * 4);
-            memcpy(r->rad2.data(), slot.stage + r->stage_off + align256(r->m * 4), r->m * 8);
-            memcpy(r->radius.data(), slot.stage + r->stage_off + align256(r->m * 4) + align256(r->m * 8), r->m * 4);
-            r->state = 2;
-        }
-        r->t[2] = t;
         if (r->dmem) cudaFreeAsync(r->dmem, slot.stream);
         r->dmem = nullptr;
+        if (r->copied) {
+            cudaEventDestroy(r->copied);
+            r->copied = nullptr;
+        }
         S->used -= r->bytes;
         S->inflight -= 1;
     }
     slot.reqs.clear();
     slot.busy = false;
+}
+
+// Starts the device-to-host copy of a request whose part has finished (its flag is
+// set) on the copy stream, while the rest of the launch keeps running.
+static void start_copy(bs_server *S, SrvSlot &slot, SrvReq *r) {
+    const uint32_t *dp = (const uint32_t *)(r->dmem + align256(r->n * 8));
+    const int64_t *dr = (const int64_t *)(r->dmem + align256(r->n * 8) + align256(r->m * 4));
+    const float *df = (const float *)(r->dmem + align256(r->n * 8) + align256(r->m * 4) + align256(r->m * 8));
+    char *st = slot.stage + r->stage_off;
+    cudaMemcpyAsync(st, dp, r->m * 4, cudaMemcpyDeviceToHost, S->copy);
+    cudaMemcpyAsync(st + align256(r->m * 4), dr, r->m * 8, cudaMemcpyDeviceToHost, S->copy);
+    cudaMemcpyAsync(st + align256(r->m * 4) + align256(r->m * 8), df, r->m * 4, cudaMemcpyDeviceToHost, S->copy);
+    if (!r->copied && cudaEventCreateWithFlags(&r->copied, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        r->copied = nullptr;
+    }
+    if (r->copied) cudaEventRecord(r->copied, S->copy);
+    r->state = 5;
+}
+
+static void finish_copy(bs_server *S, SrvSlot &slot, SrvReq *r) {
+    const char *st = slot.stage + r->stage_off;
+    memcpy(r->perm.data(), st, r->m * 4);
+    memcpy(r->rad2.data(), st + align256(r->m * 4), r->m * 8);
+    memcpy(r->radius.data(), st + align256(r->m * 4) + align256(r->m * 8), r->m * 4);
+    r->t[2] = S->now();
+    r->state = 2;
 }
 
 static void launch_batch(bs_server *S, SrvSlot &slot, std::vector<SrvReq *> &batch) {
@@ -300,6 +332,9 @@ static void launch_batch(bs_server *S, SrvSlot &slot, std::vector<SrvReq *> &bat
         PartDesc p;
         memset(&p, 0, sizeof(p));
         p.key = dk; p.perm = dp; p.rad2 = dr; p.radius = df; p.scale = r->scale;
+        r->flag = (uint32_t)parts.size();
+        slot.flags_h[r->flag] = 0u;
+        p.done = slot.flags_d + r->flag;
         p.n = (uint32_t)r->n; p.m = (uint32_t)r->m;
         p.start = (uint32_t)(r->opts.start >= 0 ? (uint64_t)r->opts.start : start_from_seed(r->n, r->opts.seed, r->opts.part_id));
         p.variant = (uint32_t)r->opts.variant;
@@ -313,14 +348,8 @@ static void launch_batch(bs_server *S, SrvSlot &slot, std::vector<SrvReq *> &bat
     }
     if (!parts.empty()) {
         bs_status st = order_parts(parts, slot.stream, true);
-        for (size_t i = 0; i < run.size(); ++i) {
-            SrvReq *r = run[i];
-            if (st != BS_OK) { r->state = 3; r->err = st; continue; }
-            cudaMemcpyAsync(slot.stage + r->stage_off, parts[i].perm, r->m * 4, cudaMemcpyDeviceToHost, slot.stream);
-            cudaMemcpyAsync(slot.stage + r->stage_off + align256(r->m * 4), parts[i].rad2, r->m * 8, cudaMemcpyDeviceToHost, slot.stream);
-            cudaMemcpyAsync(slot.stage + r->stage_off + align256(r->m * 4) + align256(r->m * 8), parts[i].radius, r->m * 4,
-                            cudaMemcpyDeviceToHost, slot.stream);
-        }
+        if (st != BS_OK)
+            for (SrvReq *r : run) { r->state = 3; r->err = st; r->t[2] = S->now(); }
     }
     cudaEventRecord(slot.done, slot.stream);
     slot.reqs = batch;
@@ -333,7 +362,21 @@ static void driver_loop(bs_server *S) {
     while (!S->stop) {
         bool progressed = false;
         for (SrvSlot &slot : S->slots) {
-            if (slot.busy && cudaEventQuery(slot.done) == cudaSuccess) {
+            if (!slot.busy) continue;
+            bool all_done = true;
+            for (SrvReq *r : slot.reqs) {
+                if (r->state == 1 && ((volatile uint32_t *)slot.flags_h)[r->flag] != 0u) {
+                    start_copy(S, slot, r);
+                    progressed = true;
+                }
+                if (r->state == 5 && (!r->copied || cudaEventQuery(r->copied) == cudaSuccess)) {
+                    if (!r->copied) cudaStreamSynchronize(S->copy);
+                    finish_copy(S, slot, r);
+                    progressed = true;
+                }
+                all_done &= r->state == 2 || r->state == 3 || r->state == 4;
+            }
+            if (all_done && cudaEventQuery(slot.done) == cudaSuccess) {
                 retire(S, slot);
                 progressed = true;
             }
@@ -342,7 +385,7 @@ static void driver_loop(bs_server *S) {
         for (SrvSlot &slot : S->slots) {
             if (slot.busy || S->queue.empty()) continue;
             std::vector<SrvReq *> batch;
-            while (!S->queue.empty() && S->inflight < S->max_inflight) {
+            while (!S->queue.empty() && S->inflight < S->max_inflight && batch.size() < SLOT_FLAGS) {
                 SrvReq *r = S->queue.front();
                 if (S->used + r->bytes > S->budget) break;  // FIFO admission under the memory budget
                 S->queue.pop_front();
@@ -380,15 +423,25 @@ bs_server *bs_server_create(uint64_t device_budget_bytes, int max_inflight, bs_s
     S->max_inflight = max_inflight ? max_inflight : 4096;
     S->t0 = std::chrono::steady_clock::now();
     S->slots.resize(4);
+    if (cudaStreamCreateWithFlags(&S->copy, cudaStreamNonBlocking) != cudaSuccess) {
+        set_error("bs_server_create: stream creation failed: %s", cudaGetErrorString(cudaGetLastError()));
+        if (st) *st = BS_ECUDA;
+        delete S;
+        return nullptr;
+    }
     for (SrvSlot &slot : S->slots) {
         if (cudaStreamCreateWithFlags(&slot.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&slot.done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreateWithFlags(&slot.done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaHostAlloc((void **)&slot.flags_h, SLOT_FLAGS * sizeof(uint32_t), cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostGetDevicePointer((void **)&slot.flags_d, slot.flags_h, 0) != cudaSuccess) {
             set_error("bs_server_create: stream/event creation failed: %s", cudaGetErrorString(cudaGetLastError()));
             if (st) *st = BS_ECUDA;
             for (SrvSlot &s2 : S->slots) {
                 if (s2.stream) cudaStreamDestroy(s2.stream);
                 if (s2.done) cudaEventDestroy(s2.done);
+                if (s2.flags_h) cudaFreeHost(s2.flags_h);
             }
+            cudaStreamDestroy(S->copy);
             delete S;
             return nullptr;
         }
@@ -430,6 +483,8 @@ bs_status bs_server_submit(bs_server *S, const uint64_t *key, uint64_t n, double
     r->state = 0;
     r->err = BS_OK;
     r->dmem = nullptr;
+    r->flag = 0;
+    r->copied = nullptr;
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->queue.size() >= S->max_queue) { delete r; set_error("bs_server_submit: queue full"); return BS_EBUSY; }
     r->ticket = S->next_ticket++;
@@ -448,7 +503,7 @@ bs_status bs_server_poll(bs_server *S, uint64_t ticket, uint32_t *perm, int64_t 
     auto it = S->all.find(ticket);
     if (it == S->all.end()) { set_error("bs_server_poll: unknown ticket %llu", (unsigned long long)ticket); return BS_EINVAL; }
     SrvReq *r = it->second;
-    if (r->state == 0 || r->state == 1) return BS_ENOTREADY;
+    if (r->state == 0 || r->state == 1 || r->state == 5) return BS_ENOTREADY;
     if (r->state == 3) {
         set_error("bs_server_poll: request %llu failed", (unsigned long long)ticket);
         return r->err == BS_OK ? BS_ECUDA : r->err;
@@ -473,7 +528,7 @@ bs_status bs_server_times(bs_server *S, uint64_t ticket, double t[3]) {
     auto it = S->all.find(ticket);
     if (it == S->all.end()) { set_error("bs_server_times: unknown ticket"); return BS_EINVAL; }
     SrvReq *r = it->second;
-    if (r->state < 2) return BS_ENOTREADY;
+    if (r->state != 2 && r->state != 3 && r->state != 4) return BS_ENOTREADY;
     t[0] = r->t[0]; t[1] = r->t[1]; t[2] = r->t[2];
     return BS_OK;
 }
@@ -488,14 +543,16 @@ void bs_server_destroy(bs_server *S) {
     for (SrvSlot &slot : S->slots) {
         if (slot.busy) {
             cudaEventSynchronize(slot.done);
+            cudaStreamSynchronize(S->copy);
             retire(S, slot);
         }
         if (slot.stage) cudaFreeHost(slot.stage);
+        if (slot.flags_h) cudaFreeHost(slot.flags_h);
         cudaEventDestroy(slot.done);
         cudaStreamDestroy(slot.stream);
     }
+    cudaStreamDestroy(S->copy);
     for (auto &kv : S->all) delete kv.second;
-    for (SrvReq *r : S->queue) (void)r;  // queued requests are owned by `all`
     delete S;
 }
 

@@ -117,6 +117,7 @@ struct PartDesc {
     uint64_t *bkey, *bq, *blo, *bhi;
     uint64_t *gkey, *gq, *glo, *ghi;
     uint32_t *R, *pos;  // variant 1: remaining set (index array) and each index's position in it
+    uint32_t *done;     // optional completion flag (device view of host-mapped memory), set to 1 at the end
     double scale;
     uint64_t seed;
     uint32_t n, m, start, nb, ng;

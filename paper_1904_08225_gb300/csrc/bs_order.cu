@@ -755,6 +755,19 @@ __global__ void __launch_bounds__(T) k_order_rounds(const PartDesc *__restrict__
             k += np;
             __syncthreads();
         }
+        // the part's radii, then its completion flag (host-mapped memory, after a
+        // system-scope fence so the host sees every output of the part first)
+        if (P.radius)
+            for (uint32_t q = threadIdx.x; q < m; q += T) {
+                const int64_t r2 = P.rad2[q];
+                P.radius[q] = r2 == INT64_MAX ? __int_as_float(0x7f800000)
+                                              : (float)__ddiv_rn(__dsqrt_rn((double)r2), P.scale);
+            }
+        __syncthreads();
+        if (threadIdx.x == 0 && P.done) {
+            __threadfence_system();
+            *(volatile uint32_t *)P.done = 1u;
+        }
         __syncthreads();
     }
 }
@@ -968,8 +981,9 @@ bs_status order_parts(std::vector<PartDesc> &hp, cudaStream_t stream, bool batch
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         // the one-pick-per-step kernel only knows the exact greedy permutation
+        // (and only the rounds kernel publishes per-part completion flags)
         bool sampled = false;
-        for (const auto &q : sorted) sampled |= q.variant == 1;
+        for (const auto &q : sorted) sampled |= q.variant == 1 || q.done != nullptr;
         const int algo = sampled ? 2 : g_order_algo;
         timing_mark(1, 0, stream);
         e = launch_set(d_parts, nparts, d_next, (int)ngmax, pick_threads((int)ngmax, batched, algo), sms, stream, algo);
@@ -982,7 +996,7 @@ bs_status order_parts(std::vector<PartDesc> &hp, cudaStream_t stream, bool batch
         bool any_radius = false;
         uint32_t mmax = 0;
         for (auto &p : sorted) { any_radius |= p.radius != nullptr; mmax = std::max(mmax, p.m); }
-        if (any_radius) {
+        if (any_radius && algo == 1) {  // the rounds kernel writes radii at the end of each part
             dim3 g(std::min<uint32_t>((mmax + 255) / 256, 64), std::min(nparts, 65535));
             timing_mark(2, 0, stream);
             k_radius<<<g, 256, 0, stream>>>(d_parts, nparts);
