@@ -210,6 +210,7 @@ struct SrvReq {
 };
 
 constexpr uint32_t SLOT_FLAGS = 4096;  // requests per launch (one completion flag each)
+constexpr size_t SLOT_STAGE_BYTES = 64ull << 20;  // pinned result staging per launch slot, grown on demand
 
 struct SrvSlot {
     cudaStream_t stream = nullptr;
@@ -422,7 +423,7 @@ bs_server *bs_server_create(uint64_t device_budget_bytes, int max_inflight, bs_s
     S->budget = device_budget_bytes;
     S->max_inflight = max_inflight ? max_inflight : 4096;
     S->t0 = std::chrono::steady_clock::now();
-    S->slots.resize(4);
+    S->slots.resize(16);  // launches in flight at once: each holds the requests queued when it started
     if (cudaStreamCreateWithFlags(&S->copy, cudaStreamNonBlocking) != cudaSuccess) {
         set_error("bs_server_create: stream creation failed: %s", cudaGetErrorString(cudaGetLastError()));
         if (st) *st = BS_ECUDA;
@@ -433,18 +434,21 @@ bs_server *bs_server_create(uint64_t device_budget_bytes, int max_inflight, bs_s
         if (cudaStreamCreateWithFlags(&slot.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&slot.done, cudaEventDisableTiming) != cudaSuccess ||
             cudaHostAlloc((void **)&slot.flags_h, SLOT_FLAGS * sizeof(uint32_t), cudaHostAllocMapped) != cudaSuccess ||
-            cudaHostGetDevicePointer((void **)&slot.flags_d, slot.flags_h, 0) != cudaSuccess) {
+            cudaHostGetDevicePointer((void **)&slot.flags_d, slot.flags_h, 0) != cudaSuccess ||
+            cudaHostAlloc((void **)&slot.stage, SLOT_STAGE_BYTES, cudaHostAllocDefault) != cudaSuccess) {
             set_error("bs_server_create: stream/event creation failed: %s", cudaGetErrorString(cudaGetLastError()));
             if (st) *st = BS_ECUDA;
             for (SrvSlot &s2 : S->slots) {
                 if (s2.stream) cudaStreamDestroy(s2.stream);
                 if (s2.done) cudaEventDestroy(s2.done);
                 if (s2.flags_h) cudaFreeHost(s2.flags_h);
+                if (s2.stage) cudaFreeHost(s2.stage);
             }
             cudaStreamDestroy(S->copy);
             delete S;
             return nullptr;
         }
+        slot.stage_cap = SLOT_STAGE_BYTES;
     }
     S->driver = std::thread(driver_loop, S);
     if (st) *st = BS_OK;
