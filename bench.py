@@ -49,6 +49,11 @@ IMPROVED_FIT = (-1.06, 0.74)
 BYTES_PER_VISIT = 16   # 8 B key + 8 B D read
 BYTES_PER_IMPROVE = 8  # 8 B D write
 BYTES_OUT = 16         # perm 4 + rad2 8 + radius 4
+# DRAM bytes (read + write) of one k_order_rounds launch per surfel ordered, from an ncu
+# capture of the 1024-part batch (state far above L2, so traffic grows with the surfels):
+# profiles/k_order_rounds_traffic_batch1024_tori.md.  Must be re-measured (or set to None)
+# whenever k_order_rounds changes.
+DRAM_BYTES_PER_SURFEL = 435.6
 
 
 def algorithmic_bytes(n: int) -> float:
@@ -447,7 +452,9 @@ def main():
                     "d2h_bytes_per_step": int(d2h_bytes)},
             "gpu_launches": args.steps * (nsample_kernels + 3),
             "roofline": {"bound": "hbm", "kernel": "k_order_rounds", "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": (DRAM_BYTES_PER_SURFEL * float(total)) if DRAM_BYTES_PER_SURFEL else None,
+                         "traffic_source": "ncu dram__bytes_read+write of the 1024-part batch, scaled by surfels",
                          "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured" else "fallback 6800 GB/s",
                          "algorithmic_bytes_per_launch": bytes_launch, "loop_ms_per_launch": loop_avg},
             "clocks": clk,
