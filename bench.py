@@ -241,6 +241,8 @@ def main():
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[250.0, 500.0, 1000.0, 2000.0])
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--no-extras", action="store_true", help="skip plain / served / cpu baseline legs")
+    ap.add_argument("--scene-lines", type=int, default=20, help="production lines of the scene leg (0 skips it)")
+    ap.add_argument("--scene-per-line", type=int, default=2500)
     args = ap.parse_args()
     world, rank, local = dist_setup()
     specs = rank_specs(args.parts, args.seed, rank)
@@ -432,6 +434,8 @@ def main():
         }
         extras["served"] = serve_leg(bs, key_all, coff, ns, out_structs, args)
         extras["paper_table2_shape"] = table2_leg(bs, timed)
+        if args.scene_lines > 0:
+            extras["scene"] = scene_leg(args)
         extras["cpu_baseline"] = cpu_baseline(specs, args)
 
     if rank == 0:
@@ -521,6 +525,21 @@ def serve_leg(bs, key_all, coff, ns, out_structs, args):
             "sweep": sweep,
             "requests_from": "surfel arrays of the batch parts with 1k-1M surfels, seeded choice and start",
             "headline": "highest offered rate the server keeps up with (>= 90% of offered surfels/s)"}
+
+
+def scene_leg(args):
+    """Scene scale: every node of a production-line scene (one per part, per group of 50
+    parts and per line) regenerated on the device, sampled from the 6 axis directions and
+    ordered with the min(200k, triangles / 2) bound; end-to-end wall time of the whole scene
+    (one run, after a one-line warm-up)."""
+    from paper_1904_08225_gb300 import scene
+    scene.run(args.seed, lines=1, per_line=min(args.scene_per_line, 100))
+    r = scene.run(args.seed, lines=args.scene_lines, per_line=args.scene_per_line)
+    return {"lines": args.scene_lines, "parts": args.scene_lines * args.scene_per_line, "nodes": r.nodes,
+            "triangles": r.triangles, "surfels_sampled": r.surfels_sampled, "surfels_ordered": r.surfels_ordered,
+            "seconds": r.seconds, "ordered_per_s": r.surfels_ordered / r.seconds,
+            "per_level": {str(k): v for k, v in sorted(r.per_level.items())},
+            "level_res": scene.LEVEL_RES, "dirs": "6 axis"}
 
 
 def table2_leg(bs, timed):

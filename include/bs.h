@@ -242,6 +242,25 @@ bs_status bs_server_times(bs_server *srv, uint64_t ticket, double t[3]);
 /* Waits for all in-flight work, frees device memory and the server. */
 void bs_server_destroy(bs_server *srv);
 
+/* ---- Scene-scale workload (the production-line scene of Sec. 5). ---- */
+
+/* Generates nparts CAD-like parts (nboxes boxes of 2x2-quad faces and ncyl 32-segment
+ * cylinders each) on the device from a seed, concatenated in the given order into
+ * one mesh: vertices xyz (nparts * (54 nboxes + 98 ncyl) * 3 float32), triangles
+ * (nparts * (48 nboxes + 192 ncyl) * 3 uint32; indices into that mesh, or into each
+ * part's own vertices when local_indices != 0), per-face RGB8 (all DEVICE, owned by the
+ * caller).  part_ids, lines, slots: HOST arrays (the part's Philox counter, its line
+ * and its slot in the line: placement + (slot * dx, line * dy, 0)).  size_table
+ * (1024 log-uniform sizes), cos32 and sin32 (32-segment ring) are HOST tables.
+ * Every parameter comes from Philox4x32-10(ctr = {part_lo, part_hi, primitive, k},
+ * key = seed) and every vertex from single float32 operations in a fixed order, so a
+ * host implementation reproduces the mesh bit for bit.  Stream-ordered.  BS_EINVAL for
+ * NULL arrays, negative counts, nboxes == ncyl == 0 or 2^32 vertices or more. */
+bs_status bs_scene_generate(uint64_t seed, const uint64_t *part_ids, const int32_t *lines, const int32_t *slots,
+                            int nparts, int nboxes, int ncyl, const float *size_table, const float *cos32,
+                            const float *sin32, float dx, float dy, int local_indices, float *xyz, uint32_t *tri,
+                            uint8_t *rgb, void *cuda_stream);
+
 /* Launch-shape knobs for the autotuner (results never depend on them):
  *  "order_threads"      threads per ordering CTA (64, 128, 256, 512, 1024; 0 = auto)
  *  "order_ctas_per_sm"  cap on resident ordering CTAs per SM (0 = occupancy limit)

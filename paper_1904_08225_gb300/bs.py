@@ -24,7 +24,8 @@ INT64_MAX = (1 << 63) - 1
 # symbols include/bs.h declares; the library must export every one
 EXPORTS = ["bs_sample_visible", "bs_sample_visible_batched", "bs_order", "bs_order_noalloc", "bs_order_batched", "bs_server_create", "bs_server_submit",
            "bs_server_poll", "bs_server_times", "bs_server_destroy", "bs_set_tuning", "bs_last_launch_ms",
-           "bs_prefix_median_nn", "bs_prefix_for_radius", "bs_prefix_estimate", "bs_last_error"]
+           "bs_prefix_median_nn", "bs_prefix_for_radius", "bs_prefix_estimate", "bs_scene_generate",
+           "bs_last_error"]
 
 
 class BsError(RuntimeError):
@@ -87,6 +88,8 @@ def load(build_if_stale: bool = True) -> C.CDLL:
             lib.bs_prefix_median_nn.argtypes = [C.POINTER(Surfels), P, C.c_uint64, C.POINTER(C.c_int64), P]
             lib.bs_prefix_for_radius.argtypes = [P, C.c_uint64, C.c_int64, C.POINTER(C.c_uint64), P]
             lib.bs_prefix_estimate.argtypes = [C.c_uint64, C.c_int64, C.c_int64]
+            lib.bs_scene_generate.argtypes = [C.c_uint64, P, P, P, C.c_int, C.c_int, C.c_int, P, P, P, C.c_float,
+                                              C.c_float, C.c_int, P, P, P, P]
             lib.bs_last_error.restype = C.c_char_p
             for fn in EXPORTS[:-1]:
                 if fn not in ("bs_server_create", "bs_server_destroy", "bs_prefix_estimate"):
@@ -131,6 +134,34 @@ def last_launch_ms(kernel: str) -> float:
     ms = C.c_double(0.0)
     _check(load().bs_last_launch_ms(kernel.encode(), C.byref(ms)), "bs_last_launch_ms")
     return ms.value
+
+
+def scene_generate(seed: int, parts, nboxes: int = 200, ncyl: int = 50, stream=None, device=None,
+                   local_indices: bool = False):
+    """bs_scene_generate: CUDA tensors (xyz, tri as int32 view, rgb) of the concatenated parts.
+
+    parts: list of (part_id, line, slot).  Tables and placement steps come from workloads."""
+    torch = _torch()
+    from . import workloads as W
+    lib = load()
+    n = len(parts)
+    pid = np.array([p[0] for p in parts], np.uint64)
+    ln = np.array([p[1] for p in parts], np.int32)
+    sl = np.array([p[2] for p in parts], np.int32)
+    V = n * (W.BOX_VERTS * nboxes + W.CYL_VERTS * ncyl)
+    T = n * (W.BOX_TRIS * nboxes + W.CYL_TRIS * ncyl)
+    dev = device or torch.device("cuda")
+    xyz = torch.empty((V, 3), dtype=torch.float32, device=dev)
+    tri = torch.empty((T, 3), dtype=torch.int32, device=dev)
+    rgb = torch.empty((T, 3), dtype=torch.uint8, device=dev)
+    st = lib.bs_scene_generate(int(seed) & (2**64 - 1), pid.ctypes.data_as(C.c_void_p), ln.ctypes.data_as(C.c_void_p),
+                               sl.ctypes.data_as(C.c_void_p), n, nboxes, ncyl,
+                               W.SIZE_TABLE.ctypes.data_as(C.c_void_p), W.COS32.ctypes.data_as(C.c_void_p),
+                               W.SIN32.ctypes.data_as(C.c_void_p), float(W.SCENE_DX), float(W.SCENE_DY),
+                               int(local_indices), C.c_void_p(xyz.data_ptr()), C.c_void_p(tri.data_ptr()), C.c_void_p(rgb.data_ptr()),
+                               _stream(stream))
+    _check(st, "bs_scene_generate")
+    return xyz, tri, rgb
 
 
 def prefix_median_nn(key, perm, pm: int, stream=None) -> int:
@@ -201,27 +232,31 @@ def sample_visible_batched(meshes, res, dirs, stream=None, caps=None):
     rarr = (C.c_int * P)(*[int(r) for r in res])
     outs = (Surfels * P)()
     keep = []
+    capl = [int(caps[i]) if caps is not None else len(d) * int(res[i]) ** 2 for i in range(P)]
+    ofs = np.concatenate([[0], np.cumsum(capl)]).astype(np.int64)
+    dev = meshes[0][0].device if P else None
+    tot = int(ofs[-1])
+    # one allocation per field; part i owns rows ofs[i]:ofs[i+1]
+    key = torch.empty(tot, dtype=torch.int64, device=dev)
+    nrm = torch.empty((tot, 3), dtype=torch.int16, device=dev)
+    col = torch.empty((tot, 3), dtype=torch.uint8, device=dev)
+    src = torch.empty(tot, dtype=torch.int32, device=dev)
     for i, (xyz, tri, rgb) in enumerate(meshes):
         xyz, tri = xyz.contiguous(), tri.contiguous()
         rgb = rgb.contiguous() if rgb is not None else None
         keep.append((xyz, tri, rgb))
         marr[i] = Mesh(xyz.data_ptr(), xyz.shape[0], tri.data_ptr() if tri.numel() else None, tri.shape[0],
                        rgb.data_ptr() if rgb is not None else None)
-        cap = caps[i] if caps is not None else len(d) * int(res[i]) ** 2
-        dev = xyz.device
-        key = torch.empty(cap, dtype=torch.int64, device=dev)
-        nrm = torch.empty((cap, 3), dtype=torch.int16, device=dev)
-        col = torch.empty((cap, 3), dtype=torch.uint8, device=dev)
-        src = torch.empty(cap, dtype=torch.int32, device=dev)
-        keep.append((key, nrm, col, src))
-        outs[i] = Surfels(key.data_ptr(), nrm.data_ptr(), col.data_ptr(), src.data_ptr(), 0, cap, (C.c_float * 3)(), 0.0)
+        o = int(ofs[i])
+        outs[i] = Surfels(key.data_ptr() + 8 * o, nrm.data_ptr() + 6 * o, col.data_ptr() + 3 * o,
+                          src.data_ptr() + 4 * o, 0, capl[i], (C.c_float * 3)(), 0.0)
     st = lib.bs_sample_visible_batched(marr, rarr, P, darr, len(d), outs, _stream(stream))
     _check(st, "bs_sample_visible_batched")
     res_list = []
     for i in range(P):
-        key, nrm, col, src = keep[2 * i + 1]
+        o = int(ofs[i])
         n = int(outs[i].n)
-        res_list.append(dict(key=key[:n], nrm=nrm[:n], rgb=col[:n], src=src[:n], n=n,
+        res_list.append(dict(key=key[o:o + n], nrm=nrm[o:o + n], rgb=col[o:o + n], src=src[o:o + n], n=n,
                              bbox_min=np.array(list(outs[i].bbox_min), np.float32), scale=float(outs[i].scale)))
     return res_list
 
@@ -293,13 +328,21 @@ def order_batched(keys, starts=None, seeds=None, part_ids=None, max_counts=None,
     rp = (C.c_void_p * P)()
     fp = (C.c_void_p * P)()
     result = []
+    ms = [k.shape[0] if mc == 0 or mc > k.shape[0] else mc for k, mc in zip(keys, max_counts)]
+    if outs is None and P:
+        # one allocation per output field; part i owns entries mo[i]:mo[i+1]
+        mo = np.concatenate([[0], np.cumsum(ms)]).astype(np.int64)
+        dev = keys[0].device
+        perm_all = torch.empty(int(mo[-1]), dtype=torch.int32, device=dev)
+        rad2_all = torch.empty(int(mo[-1]), dtype=torch.int64, device=dev)
+        radius_all = torch.empty(int(mo[-1]), dtype=torch.float32, device=dev) if want_radius else None
     for i, k in enumerate(keys):
         n = k.shape[0]
-        m = n if max_counts[i] == 0 or max_counts[i] > n else max_counts[i]
+        m = ms[i]
         if outs is None:
-            perm = torch.empty(m, dtype=torch.int32, device=k.device)
-            rad2 = torch.empty(m, dtype=torch.int64, device=k.device)
-            radius = torch.empty(m, dtype=torch.float32, device=k.device) if want_radius else None
+            a, b = int(mo[i]), int(mo[i + 1])
+            perm, rad2 = perm_all[a:b], rad2_all[a:b]
+            radius = radius_all[a:b] if want_radius else None
         else:
             perm, rad2, radius = outs[i]
         parts[i] = Surfels(k.data_ptr(), None, None, None, n, n, (C.c_float * 3)(), float(scales[i]))

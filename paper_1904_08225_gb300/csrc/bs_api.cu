@@ -150,6 +150,15 @@ bs_status bs_prefix_for_radius(const int64_t *rad2, uint64_t m, int64_t r2, uint
     return prefix_for_radius(rad2, m, r2, p, (cudaStream_t)cuda_stream);
 }
 
+bs_status bs_scene_generate(uint64_t seed, const uint64_t *part_ids, const int32_t *lines, const int32_t *slots,
+                            int nparts, int nboxes, int ncyl, const float *size_table, const float *cos32,
+                            const float *sin32, float dx, float dy, int local_indices, float *xyz, uint32_t *tri,
+                            uint8_t *rgb, void *cuda_stream) {
+    clear_error();
+    return scene_generate(seed, part_ids, lines, slots, nparts, nboxes, ncyl, size_table, cos32, sin32, dx, dy,
+                          local_indices, xyz, tri, rgb, (cudaStream_t)cuda_stream);
+}
+
 double bs_prefix_estimate(uint64_t pm, int64_t rm2, int64_t r2) {
     if (r2 <= 0) return (double)INFINITY;
     return (double)pm * (double)rm2 / (double)r2;

@@ -127,6 +127,7 @@ struct PartDesc {
 }  // namespace bs
 
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 namespace bs {
@@ -135,6 +136,10 @@ bs_status order_parts(std::vector<PartDesc> &parts, cudaStream_t stream, bool ba
 bs_status order_part_noalloc(PartDesc part, cudaStream_t stream);
 bs_status prefix_median_nn(const bs_surfels *s, const uint32_t *perm, uint64_t pm, int64_t *rm2, cudaStream_t stream);
 bs_status prefix_for_radius(const int64_t *rad2, uint64_t m, int64_t r2, uint64_t *p, cudaStream_t stream);
+bs_status scene_generate(uint64_t seed, const uint64_t *part_ids, const int32_t *lines, const int32_t *slots, int nparts,
+                         int nboxes, int ncyl, const float *size_table, const float *cos32, const float *sin32,
+                         float dx, float dy, int local_indices, float *xyz, uint32_t *tri, uint8_t *rgb,
+                         cudaStream_t stream);
 void order_set_tuning(int threads, int ctas_per_sm);
 void order_set_kernel_timing(bool on);
 void order_set_algo(int algo);

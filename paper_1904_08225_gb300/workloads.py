@@ -163,9 +163,10 @@ def _cylinder(centre, axis: int, radius: float, length: float, nseg: int = 32, n
     c0, c1 = nrings * nseg, nrings * nseg + 1
     j = np.arange(nseg)
     j1 = (j + 1) % nseg
-    cap0 = np.stack([np.full(nseg, c0), j1, j], -1)
+    # caps wound like the side quads, so the surface is closed and consistently oriented
+    cap0 = np.stack([np.full(nseg, c0), j, j1], -1)
     top = (nrings - 1) * nseg
-    cap1 = np.stack([np.full(nseg, c1), top + j, top + j1], -1)
+    cap1 = np.stack([np.full(nseg, c1), top + j1, top + j], -1)
     return verts, np.concatenate([side, cap0, cap1]).astype(np.uint32)
 
 
@@ -300,3 +301,161 @@ def request_trace(nreq: int, rate_hz: float, seed: int = 0, n_median: float = 30
     n = np.clip(np.exp(g.normal(np.log(n_median), 1.0, nreq)), n_lo, n_hi).astype(np.int64)
     seeds = g.integers(0, 2**31, nreq)
     return t, n, seeds
+
+
+# ---------------------------------------------------------------------------
+# Scene-scale workload: production lines of CAD-like parts, regenerated from a seed.
+#
+# The same parts are produced on the device by bs_scene_generate (libbs) and here on
+# the host (for the oracle's checks); both follow this float32 recipe exactly:
+#   * random words: w(part, prim, k) = Philox4x32-10(ctr = {part_lo, part_hi, prim, k},
+#     key = {seed_lo, seed_hi}); uniform u(x) = float32(x >> 8) * 2^-24 (exact);
+#   * sizes: SIZE_TABLE[x >> 22], 1024 log-uniform values in [0.01, 0.3] (host-made);
+#   * box b: centre (u(w0[0]), u(w0[1]), u(w0[2])), sizes SIZE_TABLE[w1[a] >> 22],
+#     h = s * 0.5, lo = c - h, mid = lo + h, hi = c + h; 6 faces of 2x2 quads
+#     (9 vertices, 8 triangles each), one RGB8 per face from w2, w3 bytes;
+#   * cylinder: axis w0[0] % 3, centre (u(w0[1]), u(w0[2]), u(w0[3])), radius
+#     SIZE_TABLE[w1[0] >> 22], length SIZE_TABLE[w1[1] >> 22], ring point j =
+#     (COS32[j] * r + c, SIN32[j] * r + c) across the axis, levels c - L*0.5, c, c + L*0.5;
+#     3 rings of 32 + 2 cap centres, 128 side + 64 cap triangles, colours from w2;
+#   * placement: part p of line l at slot i adds (i * SCENE_DX, l * SCENE_DY, 0).
+# All additions and multiplications are single float32 operations in this order.
+# ---------------------------------------------------------------------------
+SIZE_TABLE = np.exp(np.log(0.01) + (np.arange(1024) + 0.5) / 1024 * (np.log(0.3) - np.log(0.01))).astype(np.float32)
+COS32 = np.cos(2.0 * np.pi * np.arange(32) / 32).astype(np.float32)
+SIN32 = np.sin(2.0 * np.pi * np.arange(32) / 32).astype(np.float32)
+SCENE_DX = np.float32(1.25)
+SCENE_DY = np.float32(1.75)
+BOX_VERTS, BOX_TRIS, CYL_VERTS, CYL_TRIS = 54, 48, 98, 192
+
+
+def philox4x32_10(c0, c1, c2, c3, k0, k1):
+    """Philox4x32-10 (Salmon et al., SC'11) on numpy uint32 arrays (broadcast)."""
+    M0, M1 = np.uint64(0xD2511F53), np.uint64(0xCD9E8D57)
+    W0, W1 = np.uint32(0x9E3779B9), np.uint32(0xBB67AE85)
+    x = [np.asarray(c, dtype=np.uint32).copy() for c in (c0, c1, c2, c3)]
+    x = np.broadcast_arrays(*x)
+    x = [a.copy() for a in x]
+    k0 = np.uint32(k0)
+    k1 = np.uint32(k1)
+    with np.errstate(over="ignore"):
+        for _ in range(10):
+            p0 = M0 * x[0].astype(np.uint64)
+            p1 = M1 * x[2].astype(np.uint64)
+            y0 = (p1 >> np.uint64(32)).astype(np.uint32) ^ x[1] ^ k0
+            y1 = p1.astype(np.uint32)
+            y2 = (p0 >> np.uint64(32)).astype(np.uint32) ^ x[3] ^ k1
+            y3 = p0.astype(np.uint32)
+            x = [y0, y1, y2, y3]
+            k0 = np.uint32(k0 + W0)
+            k1 = np.uint32(k1 + W1)
+    return x
+
+
+def _u(x):
+    return (x >> np.uint32(8)).astype(np.float32) * np.float32(2.0 ** -24)
+
+
+def scene_part(seed: int, part: int, line: int, slot: int, nboxes: int = 200, ncyl: int = 50) -> Mesh:
+    """One scene part (float32 recipe above), placed at its line and slot."""
+    f = np.float32
+    s_lo, s_hi = seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF
+    p_lo, p_hi = part & 0xFFFFFFFF, (part >> 32) & 0xFFFFFFFF
+    off = np.array([f(slot) * SCENE_DX, f(line) * SCENE_DY, f(0.0)], np.float32)
+    vs, ts, cs = [], [], []
+    base = 0
+    prim = np.arange(nboxes, dtype=np.uint32)
+    w0 = philox4x32_10(p_lo, p_hi, prim, 0, s_lo, s_hi)
+    w1 = philox4x32_10(p_lo, p_hi, prim, 1, s_lo, s_hi)
+    w2 = philox4x32_10(p_lo, p_hi, prim, 2, s_lo, s_hi)
+    w3 = philox4x32_10(p_lo, p_hi, prim, 3, s_lo, s_hi)
+    c = np.stack([_u(w0[0]), _u(w0[1]), _u(w0[2])], -1)
+    sz = np.stack([SIZE_TABLE[w1[a] >> np.uint32(22)] for a in range(3)], -1)
+    h = sz * f(0.5)
+    lo = c - h
+    mid = lo + h
+    hi = c + h
+    grid = np.stack([lo, mid, hi], 1)  # (nb, 3 levels, 3 axes)
+    colbytes = np.stack([w2[0], w2[1], w2[2], w2[3], w3[0], w3[1]], -1)  # 6 words -> 6 faces
+    # faces: (axis fixed, level, axes varying u, v) in the order of workloads._box
+    faces = [(0, 0, 1, 2), (0, 2, 2, 1), (1, 0, 2, 0), (1, 2, 0, 2), (2, 0, 0, 1), (2, 2, 1, 0)]
+    tri9 = _grid_tris(3, 3, False, False)
+    for b in range(nboxes):
+        for fi, (ax, lev, ua, va) in enumerate(faces):
+            v = np.zeros((3, 3, 3), np.float32)
+            for i in range(3):
+                for j in range(3):
+                    v[i, j, ax] = grid[b, lev, ax]
+                    v[i, j, ua] = grid[b, i, ua]
+                    v[i, j, va] = grid[b, j, va]
+            vs.append(v.reshape(-1, 3) + off)
+            ts.append(tri9 + base)
+            base += 9
+            cw = int(colbytes[b, fi])
+            cs.append(np.tile(np.array([cw & 255, (cw >> 8) & 255, (cw >> 16) & 255], np.uint8), (8, 1)))
+    prim = np.arange(nboxes, nboxes + ncyl, dtype=np.uint32)
+    w0 = philox4x32_10(p_lo, p_hi, prim, 0, s_lo, s_hi)
+    w1 = philox4x32_10(p_lo, p_hi, prim, 1, s_lo, s_hi)
+    w2 = philox4x32_10(p_lo, p_hi, prim, 2, s_lo, s_hi)
+    for q in range(ncyl):
+        axis = int(w0[0][q] % 3)
+        cc = np.array([_u(w0[1][q]), _u(w0[2][q]), _u(w0[3][q])], np.float32)
+        r = SIZE_TABLE[w1[0][q] >> 22]
+        L = SIZE_TABLE[w1[1][q] >> 22]
+        a1, a2 = (axis + 1) % 3, (axis + 2) % 3
+        hl = L * f(0.5)
+        levels = [cc[axis] - hl, cc[axis], cc[axis] + hl]
+        v = np.zeros((98, 3), np.float32)
+        for k, z in enumerate(levels):
+            v[k * 32:(k + 1) * 32, a1] = COS32 * r + cc[a1]
+            v[k * 32:(k + 1) * 32, a2] = SIN32 * r + cc[a2]
+            v[k * 32:(k + 1) * 32, axis] = z
+        v[96, a1], v[96, a2], v[96, axis] = cc[a1], cc[a2], levels[0]
+        v[97, a1], v[97, a2], v[97, axis] = cc[a1], cc[a2], levels[2]
+        side = _grid_tris(3, 32, False, True)
+        j = np.arange(32)
+        j1 = (j + 1) % 32
+        cap0 = np.stack([np.full(32, 96), j, j1], -1)
+        cap1 = np.stack([np.full(32, 97), 64 + j1, 64 + j], -1)
+        vs.append(v + off)
+        ts.append(np.concatenate([side, cap0, cap1]).astype(np.uint32) + base)
+        base += 98
+        cw = [int(w2[t][q]) for t in range(3)]
+        cs.append(np.concatenate([np.tile(np.array([cw[0] & 255, (cw[0] >> 8) & 255, (cw[0] >> 16) & 255], np.uint8), (128, 1)),
+                                  np.tile(np.array([cw[1] & 255, (cw[1] >> 8) & 255, (cw[1] >> 16) & 255], np.uint8), (32, 1)),
+                                  np.tile(np.array([cw[2] & 255, (cw[2] >> 8) & 255, (cw[2] >> 16) & 255], np.uint8), (32, 1))]))
+    return Mesh(np.concatenate(vs).astype(np.float32), np.concatenate(ts), np.concatenate(cs))
+
+
+@dataclass
+class SceneNode:
+    """A node of the scene hierarchy: a range of consecutive parts of one line."""
+    line: int
+    first: int      # first slot in the line
+    count: int      # number of parts
+    level: int      # 0 = one part, 1 = a group of parts, 2 = a whole line
+
+    def parts(self, per_line: int):
+        return [(self.line * per_line + s, self.line, s) for s in range(self.first, self.first + self.count)]
+
+
+def scene_nodes(lines: int = 20, per_line: int = 2500, group: int = 50) -> list[SceneNode]:
+    """Hierarchy of the scene: every part (level 0), groups of `group` consecutive parts
+    (level 1) and whole lines (level 2).  Every node holds more than 10k triangles, the
+    paper's threshold for giving a subtree its own approximation (Sec. 3.4)."""
+    nodes = []
+    for l in range(lines):
+        for s in range(per_line):
+            nodes.append(SceneNode(l, s, 1, 0))
+        for s in range(0, per_line, group):
+            nodes.append(SceneNode(l, s, min(group, per_line - s), 1))
+        nodes.append(SceneNode(l, 0, per_line, 2))
+    return nodes
+
+
+def scene_node_mesh(seed: int, node: SceneNode, per_line: int, nboxes: int = 200, ncyl: int = 50) -> Mesh:
+    """Host mesh of a node: its parts concatenated in slot order."""
+    ms = [scene_part(seed, p, l, s, nboxes, ncyl) for p, l, s in node.parts(per_line)]
+    vofs = np.cumsum([0] + [m.nverts for m in ms])
+    return Mesh(np.concatenate([m.xyz for m in ms]), np.concatenate([m.tri + np.uint32(o) for m, o in zip(ms, vofs)]),
+                np.concatenate([m.rgb for m in ms]))

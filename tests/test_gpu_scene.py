@@ -1,0 +1,126 @@
+"""Scene scale on the GPU: the device generator against its host mirror, and every level of
+node of a scene sampled and ordered against the oracle.
+
+Scenes are production lines of parts; nodes are single parts, groups of consecutive parts and
+whole lines (Sec. 3.4's hierarchy).  Each node keeps min(200k, triangles / 2) surfels, the
+bound of the paper's evaluation (Sec. 5).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1904_08225_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+I64MAX = np.iinfo(np.int64).max
+
+
+@pytest.fixture(scope="module")
+def bs():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1904_08225_gb300 import bs as _bs
+    _bs.load()
+    return _bs
+
+
+def _host(t):
+    return t.cpu().numpy()
+
+
+@pytest.mark.parametrize("nboxes,ncyl", [(200, 50), (7, 3), (0, 4), (5, 0)])
+def test_generator_matches_host_mirror(bs, nboxes, ncyl):
+    seed = 0x1234_5678_9ABC
+    parts = [(0, 0, 0), (2_499, 0, 2_499), (31_337, 12, 1_337), (2**40 + 5, 3, 17)]
+    xyz, tri, rgb = bs.scene_generate(seed, parts, nboxes, ncyl)
+    xyz_l, tri_l, rgb_l = bs.scene_generate(seed, parts, nboxes, ncyl, local_indices=True)
+    vp = W.BOX_VERTS * nboxes + W.CYL_VERTS * ncyl
+    tp = W.BOX_TRIS * nboxes + W.CYL_TRIS * ncyl
+    assert xyz.shape == (vp * len(parts), 3) and tri.shape == (tp * len(parts), 3)
+    X, T, Rg = _host(xyz), _host(tri).view(np.uint32), _host(rgb)
+    TL = _host(tri_l).view(np.uint32)
+    assert np.array_equal(_host(xyz_l).view(np.uint32), X.view(np.uint32))
+    assert np.array_equal(_host(rgb_l), Rg)
+    for q, (p, l, s) in enumerate(parts):
+        m = W.scene_part(seed, p, l, s, nboxes, ncyl)
+        assert np.array_equal(X[q * vp:(q + 1) * vp].view(np.uint32), m.xyz.view(np.uint32)), q
+        assert np.array_equal(T[q * tp:(q + 1) * tp], m.tri + np.uint32(q * vp)), q
+        assert np.array_equal(TL[q * tp:(q + 1) * tp], m.tri), q
+        assert np.array_equal(Rg[q * tp:(q + 1) * tp], m.rgb), q
+
+
+def test_generator_node_mesh(bs):
+    nodes = W.scene_nodes(lines=2, per_line=12, group=5)
+    for nd in [n for n in nodes if n.level > 0][:3]:
+        xyz, tri, rgb = bs.scene_generate(9, nd.parts(12), 30, 10)
+        m = W.scene_node_mesh(9, nd, 12, 30, 10)
+        assert np.array_equal(_host(xyz).view(np.uint32), m.xyz.view(np.uint32))
+        assert np.array_equal(_host(tri).view(np.uint32), m.tri)
+        assert np.array_equal(_host(rgb), m.rgb)
+
+
+def test_generator_rejects_bad_arguments(bs):
+    with pytest.raises(bs.BsError):
+        bs.scene_generate(0, [(0, 0, 0)], 0, 0)
+
+
+def _check_node(seed, idx, node, per_line, nboxes, ncyl, res, got):
+    """Oracle of one node: host mesh -> Sec. 3.1 sampling -> exact ordering with the node bound."""
+    from paper_1904_08225_gb300 import scene
+    m = W.scene_node_mesh(seed, node, per_line, nboxes, ncyl)
+    sv, _, _ = oracle.sample_mesh(m, W.AXIS_DIRS, res)
+    key, perm, rad2 = got
+    assert np.array_equal(key, sv["key"]), idx
+    mc = scene.node_bound(m.ntris, len(key))
+    st = oracle.start_index(len(key), seed=seed, part_id=idx)
+    p, r = oracle.greedy(sv["key"], st, max_count=mc)
+    assert np.array_equal(perm, p), idx
+    assert np.array_equal(rad2, r), idx
+    return len(key), mc
+
+
+def test_reduced_scene_every_node(bs):
+    """Every node of a 2-line scene (leaves, groups, lines) against the oracle."""
+    from paper_1904_08225_gb300 import scene
+    seed, lines, per_line, group, nb, nc = 21, 2, 7, 3, 20, 5
+    level_res = {0: 96, 1: 256, 2: 1024}
+    nodes = W.scene_nodes(lines, per_line, group)
+    out = scene.run(seed, lines, per_line, group, nb, nc, keep=range(len(nodes)), leaf_wave=5, group_wave=2,
+                    level_res=level_res)
+    assert out.nodes == len(nodes) and sorted(out.kept) == list(range(len(nodes)))
+    assert set(out.per_level) == {0, 1, 2}
+    for i, nd in enumerate(nodes):
+        _check_node(seed, i, nd, per_line, nb, nc, level_res[nd.level], out.kept[i])
+
+
+def _invariants(key, perm, rad2, picks):
+    P = oracle.unpack(key[perm])
+    assert len(np.unique(perm)) == len(perm) and perm.max() < len(key)
+    assert rad2[0] == I64MAX and np.all(np.diff(rad2[1:]) <= 0)
+    for k in picks:
+        assert rad2[k] == ((P[:k] - P[k]) ** 2).sum(1).min(), k
+
+
+def test_full_scene_seeded_subset(bs):
+    """The 20-line x 2,500-part scene (~1G triangles): a seeded subset of leaves and groups
+    against the oracle, every line node against the ordering invariants."""
+    from paper_1904_08225_gb300 import scene
+    seed, lines, per_line, group = 5, 20, 2500, 50
+    nodes = W.scene_nodes(lines, per_line, group)
+    g = np.random.default_rng(seed)
+    leaves = [i for i, n in enumerate(nodes) if n.level == 0]
+    groups = [i for i, n in enumerate(nodes) if n.level == 1]
+    line_ids = [i for i, n in enumerate(nodes) if n.level == 2]
+    pick_leaves = sorted(g.choice(leaves, 40, replace=False).tolist())
+    pick_groups = sorted(g.choice(groups, 2, replace=False).tolist())
+    out = scene.run(seed, lines, per_line, group, keep=pick_leaves + pick_groups + line_ids)
+    assert out.nodes == len(nodes)
+    assert out.per_level[0]["nodes"] == lines * per_line
+    assert out.triangles == sum(n.count for n in nodes) * (W.BOX_TRIS * 200 + W.CYL_TRIS * 50)
+    for i in pick_leaves + pick_groups:
+        _check_node(seed, i, nodes[i], per_line, 200, 50, scene.LEVEL_RES[nodes[i].level], out.kept[i])
+    for i in line_ids:
+        key, perm, rad2 = out.kept[i]
+        assert len(perm) == scene.node_bound(nodes[i].count * 19_200, len(key))
+        _invariants(key, perm, rad2, [1, 2, 17, len(perm) // 2, len(perm) - 1])
