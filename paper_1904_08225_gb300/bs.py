@@ -137,10 +137,11 @@ def last_launch_ms(kernel: str) -> float:
 
 
 def scene_generate(seed: int, parts, nboxes: int = 200, ncyl: int = 50, stream=None, device=None,
-                   local_indices: bool = False):
+                   local_indices: bool = False, out=None):
     """bs_scene_generate: CUDA tensors (xyz, tri as int32 view, rgb) of the concatenated parts.
 
-    parts: list of (part_id, line, slot).  Tables and placement steps come from workloads."""
+    parts: list of (part_id, line, slot).  Tables and placement steps come from workloads.
+    out: optional (xyz, tri, rgb) contiguous tensors of the right sizes to write into."""
     torch = _torch()
     from . import workloads as W
     lib = load()
@@ -151,9 +152,15 @@ def scene_generate(seed: int, parts, nboxes: int = 200, ncyl: int = 50, stream=N
     V = n * (W.BOX_VERTS * nboxes + W.CYL_VERTS * ncyl)
     T = n * (W.BOX_TRIS * nboxes + W.CYL_TRIS * ncyl)
     dev = device or torch.device("cuda")
-    xyz = torch.empty((V, 3), dtype=torch.float32, device=dev)
-    tri = torch.empty((T, 3), dtype=torch.int32, device=dev)
-    rgb = torch.empty((T, 3), dtype=torch.uint8, device=dev)
+    if out is None:
+        xyz = torch.empty((V, 3), dtype=torch.float32, device=dev)
+        tri = torch.empty((T, 3), dtype=torch.int32, device=dev)
+        rgb = torch.empty((T, 3), dtype=torch.uint8, device=dev)
+    else:
+        xyz, tri, rgb = out
+        if (xyz.numel() != 3 * V or tri.numel() != 3 * T or rgb.numel() != 3 * T or not xyz.is_contiguous()
+                or not tri.is_contiguous() or not rgb.is_contiguous()):
+            raise ValueError("scene_generate: out tensors of the wrong size or not contiguous")
     st = lib.bs_scene_generate(int(seed) & (2**64 - 1), pid.ctypes.data_as(C.c_void_p), ln.ctypes.data_as(C.c_void_p),
                                sl.ctypes.data_as(C.c_void_p), n, nboxes, ncyl,
                                W.SIZE_TABLE.ctypes.data_as(C.c_void_p), W.COS32.ctypes.data_as(C.c_void_p),
@@ -259,6 +266,108 @@ def sample_visible_batched(meshes, res, dirs, stream=None, caps=None):
         res_list.append(dict(key=key[o:o + n], nrm=nrm[o:o + n], rgb=col[o:o + n], src=src[o:o + n], n=n,
                              bbox_min=np.array(list(outs[i].bbox_min), np.float32), scale=float(outs[i].scale)))
     return res_list
+
+
+def _np_dtype(ct) -> np.dtype:
+    """numpy structured dtype with the layout of a ctypes Structure (pointers as uintp)."""
+    names, formats, offsets = [], [], []
+    for name, t in ct._fields_:
+        names.append(name)
+        offsets.append(getattr(ct, name).offset)
+        if t is C.c_void_p:
+            formats.append(np.uintp)
+        elif issubclass(t, C.Array):
+            formats.append((np.dtype(t._type_), t._length_))
+        else:
+            formats.append(np.dtype(t))
+    return np.dtype(dict(names=names, formats=formats, offsets=offsets, itemsize=C.sizeof(ct)))
+
+
+def _struct_array(ct, n: int):
+    """(numpy structured array, ctypes array over the same memory) of n zeroed structs."""
+    a = np.zeros(n, _np_dtype(ct))
+    return a, (ct * n).from_buffer(a)
+
+
+def sample_visible_packed(xyz, tri, rgb, vofs, nverts, tofs, ntris, res, dirs, caps=None, stream=None):
+    """bs_sample_visible_batched over parts that share packed buffers (no per-part tensors).
+
+    Part i: vertices xyz[vofs[i]:vofs[i]+nverts[i]], triangles tri[tofs[i]:tofs[i]+ntris[i]]
+    with indices local to its vertices, face colours rgb[tofs[i]:...] (or rgb None).
+    Returns dict(key, nrm, rgb, src: flat CUDA tensors; ofs int64 (P+1): part i's rows start
+    at ofs[i]; n int64 (P,); bbox_min float32 (P,3); scale float64 (P,))."""
+    torch = _torch()
+    lib = load()
+    vofs, nverts = np.asarray(vofs, np.int64), np.asarray(nverts, np.int64)
+    tofs, ntris = np.asarray(tofs, np.int64), np.asarray(ntris, np.int64)
+    P = len(vofs)
+    d = np.asarray(dirs, dtype=np.int8).reshape(-1, 3)
+    darr = (Dir * len(d))(*[Dir(int(a), int(b), int(c)) for a, b, c in d])
+    resv = np.broadcast_to(np.asarray(res, np.int64), (P,))
+    capv = (len(d) * resv * resv) if caps is None else np.broadcast_to(np.asarray(caps, np.int64), (P,))
+    ofs = np.concatenate([[0], np.cumsum(capv)]).astype(np.int64)
+    dev = xyz.device
+    tot = int(ofs[-1])
+    key = torch.empty(tot, dtype=torch.int64, device=dev)
+    nrm = torch.empty((tot, 3), dtype=torch.int16, device=dev)
+    col = torch.empty((tot, 3), dtype=torch.uint8, device=dev)
+    src = torch.empty(tot, dtype=torch.int32, device=dev)
+    mnp, marr = _struct_array(Mesh, P)
+    mnp["xyz"] = xyz.data_ptr() + 12 * vofs
+    mnp["nverts"] = nverts
+    mnp["tri"] = tri.data_ptr() + 12 * tofs
+    mnp["ntris"] = ntris
+    mnp["face_rgb"] = 0 if rgb is None else rgb.data_ptr() + 3 * tofs
+    onp, oarr = _struct_array(Surfels, P)
+    onp["key"] = key.data_ptr() + 8 * ofs[:-1]
+    onp["nrm"] = nrm.data_ptr() + 6 * ofs[:-1]
+    onp["rgb"] = col.data_ptr() + 3 * ofs[:-1]
+    onp["src"] = src.data_ptr() + 4 * ofs[:-1]
+    onp["cap"] = capv
+    rarr = (C.c_int * P)(*resv.tolist())
+    st = lib.bs_sample_visible_batched(marr, rarr, P, darr, len(d), oarr, _stream(stream))
+    _check(st, "bs_sample_visible_batched")
+    return dict(key=key, nrm=nrm, rgb=col, src=src, ofs=ofs, n=onp["n"].astype(np.int64),
+                bbox_min=onp["bbox_min"].copy(), scale=onp["scale"].copy())
+
+
+def order_packed(key, kofs, n, max_counts=None, seeds=0, part_ids=None, scales=1.0, starts=-1, stream=None,
+                 want_radius: bool = True, variant: int = 0, sample_size: int = 200, sample_step: int = 500):
+    """bs_order_batched over parts stored in one flat key tensor: part i is key[kofs[i]:kofs[i]+n[i]].
+
+    Returns (perm, rad2, radius-or-None flat tensors, mofs int64 (P+1)): part i's outputs are
+    entries mofs[i]:mofs[i+1]."""
+    torch = _torch()
+    lib = load()
+    kofs, n = np.asarray(kofs, np.int64)[:len(n)], np.asarray(n, np.int64)
+    P = len(n)
+    mc = np.zeros(P, np.int64) if max_counts is None else np.broadcast_to(np.asarray(max_counts, np.int64), (P,))
+    m = np.where((mc == 0) | (mc > n), n, mc)
+    mofs = np.concatenate([[0], np.cumsum(m)]).astype(np.int64)
+    dev = key.device
+    perm = torch.empty(int(mofs[-1]), dtype=torch.int32, device=dev)
+    rad2 = torch.empty(int(mofs[-1]), dtype=torch.int64, device=dev)
+    radius = torch.empty(int(mofs[-1]), dtype=torch.float32, device=dev) if want_radius else None
+    snp, sarr = _struct_array(Surfels, P)
+    snp["key"] = key.data_ptr() + 8 * kofs
+    snp["n"] = n
+    snp["cap"] = n
+    snp["scale"] = np.broadcast_to(np.asarray(scales, np.float64), (P,))
+    onp, oarr = _struct_array(OrderOpts, P)
+    onp["seed"] = np.broadcast_to(np.asarray(seeds, np.uint64), (P,))
+    onp["part_id"] = np.arange(P) if part_ids is None else np.asarray(part_ids, np.uint32)
+    onp["start"] = np.broadcast_to(np.asarray(starts, np.int64), (P,))
+    onp["max_count"] = mc
+    onp["variant"] = variant
+    onp["sample_size"] = sample_size if variant == 1 else 0
+    onp["sample_step"] = sample_step if variant == 1 else 0
+    pp = np.ascontiguousarray(perm.data_ptr() + 4 * mofs[:-1], dtype=np.uintp)
+    rp = np.ascontiguousarray(rad2.data_ptr() + 8 * mofs[:-1], dtype=np.uintp)
+    fp = np.ascontiguousarray((radius.data_ptr() + 4 * mofs[:-1]) if want_radius else np.zeros(P), dtype=np.uintp)
+    st = lib.bs_order_batched(sarr, P, oarr, C.c_void_p(pp.ctypes.data), C.c_void_p(rp.ctypes.data),
+                              C.c_void_p(fp.ctypes.data), _stream(stream))
+    _check(st, "bs_order_batched")
+    return perm, rad2, radius, mofs
 
 
 def _opts(seed=0, part_id=0, start=-1, max_count=0, variant=0, sample_size=200, sample_step=500) -> OrderOpts:

@@ -5,7 +5,7 @@
 // launches; a single part is the one-part case.
 //
 // Pipeline (all on the caller's stream):
-//   k_bbox -> k_scale -> k_quantise              node-local 21-bit integer positions (block per part)
+//   k_bbox -> k_scale -> k_quantise              node-local 21-bit integer positions (8192-vertex chunks)
 //   k_setup   (dir x triangle, all parts)        snapped screen coords, winding, area
 //   k_raster  (warp per dir x triangle)          64-bit atomicMin(depth << 32 | tri)
 //   k_cover_count -> scan -> k_resolve           covered pixels in (part, emission) order
@@ -118,21 +118,43 @@ __device__ __forceinline__ float ord2f(uint32_t o) {
     return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
 }
 
-// one block per part
-__global__ void __launch_bounds__(256) k_bbox(const SPart *__restrict__ parts, SState *__restrict__ st) {
-    const SPart P = parts[blockIdx.x];
+// Vertices are processed in chunks of VCHUNK per block, so one large part uses the whole
+// GPU; chunk c of the call belongs to part find_part(cofs, nparts, c).
+constexpr uint32_t VCHUNK = 8192;
+
+__global__ void k_bbox_init(SState *__restrict__ st, int nparts) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nparts) return;
+    SState &S = st[p];
+    for (int a = 0; a < 3; ++a) { S.mn_ord[a] = 0xffffffffu; S.mx_ord[a] = 0u; }
+    S.nonfinite = 0;
+    S.badtri = 0;
+    S.first_out = 0;
+    S.end_out = 0;
+}
+
+// per chunk: min / max of the order-preserving encodings, count of non-finite coordinates
+__global__ void __launch_bounds__(256) k_bbox(const SPart *__restrict__ parts, const uint64_t *__restrict__ cofs,
+                                              int nparts, SState *__restrict__ st) {
+    const int p = find_part(cofs, nparts, blockIdx.x);
+    const SPart P = parts[p];
+    const uint64_t v0 = (blockIdx.x - cofs[p]) * (uint64_t)VCHUNK;
+    const uint64_t v1 = min((uint64_t)P.nverts, v0 + VCHUNK);
     uint32_t mn[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, mx[3] = {0u, 0u, 0u}, bad = 0;
-    for (uint32_t i = threadIdx.x; i < P.nverts; i += blockDim.x) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const float f = P.xyz[3ull * i + a];
-            if (!isfinite(f)) {
-                ++bad;
-            } else {
-                const uint32_t o = f2ord(f);
-                mn[a] = min(mn[a], o);
-                mx[a] = max(mx[a], o);
-            }
+    for (uint64_t e = 3 * v0 + threadIdx.x; e < 3 * v1; e += blockDim.x) {
+        const float f = P.xyz[e];
+        const int a = (int)(e % 3);
+        if (!isfinite(f)) {
+            ++bad;
+        } else {
+            const uint32_t o = f2ord(f);
+            // branch-free per-axis update keeps the loads independent
+            mn[0] = a == 0 ? min(mn[0], o) : mn[0];
+            mn[1] = a == 1 ? min(mn[1], o) : mn[1];
+            mn[2] = a == 2 ? min(mn[2], o) : mn[2];
+            mx[0] = a == 0 ? max(mx[0], o) : mx[0];
+            mx[1] = a == 1 ? max(mx[1], o) : mx[1];
+            mx[2] = a == 2 ? max(mx[2], o) : mx[2];
         }
     }
     __shared__ uint32_t red[8][7];
@@ -148,41 +170,46 @@ __global__ void __launch_bounds__(256) k_bbox(const SPart *__restrict__ parts, S
         red[warp][6] = bad;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        SState &S = st[blockIdx.x];
-        for (int a = 0; a < 3; ++a) { S.mn_ord[a] = 0xffffffffu; S.mx_ord[a] = 0u; }
-        S.nonfinite = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            for (int a = 0; a < 3; ++a) {
-                S.mn_ord[a] = min(S.mn_ord[a], red[w][a]);
-                S.mx_ord[a] = max(S.mx_ord[a], red[w][3 + a]);
-            }
-            S.nonfinite += red[w][6];
+    if (threadIdx.x < 7) {
+        uint32_t v = red[0][threadIdx.x];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            const uint32_t x = red[w][threadIdx.x];
+            v = threadIdx.x < 3 ? min(v, x) : (threadIdx.x < 6 ? max(v, x) : v + x);
         }
-        double E = 0.0;
-        for (int a = 0; a < 3; ++a) {
-            const float lo = ord2f(S.mn_ord[a]);
-            const float hi = ord2f(S.mx_ord[a]);
-            const double e = __dsub_rn((double)hi, (double)lo);
-            if (e > E) E = e;
-            S.mn[a] = __fadd_rn(lo, 0.0f);  // report -0.0 as +0.0
-        }
-        S.invalid = (S.nonfinite != 0u || P.nverts == 0 || !(E > 0.0)) ? 1u : 0u;
-        S.scale = S.invalid ? 0.0 : __ddiv_rn(2097151.0, E);
-        S.badtri = 0;
-        S.first_out = 0;
-        S.end_out = 0;
+        SState &S = st[p];
+        if (threadIdx.x < 3) atomicMin(&S.mn_ord[threadIdx.x], v);
+        else if (threadIdx.x < 6) atomicMax(&S.mx_ord[threadIdx.x - 3], v);
+        else if (v) atomicAdd(&S.nonfinite, v);
     }
 }
 
-// one block per part
-__global__ void __launch_bounds__(256) k_quantise(const SPart *__restrict__ parts, const SState *__restrict__ st,
-                                                  int32_t *__restrict__ q) {
-    const SPart P = parts[blockIdx.x];
-    const SState &S = st[blockIdx.x];
+// per part: cube extent E = max side (double), scale S = (2^21 - 1) / E
+__global__ void k_scale(const SPart *__restrict__ parts, SState *__restrict__ st, int nparts) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nparts) return;
+    SState &S = st[p];
+    double E = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const float lo = ord2f(S.mn_ord[a]);
+        const float hi = ord2f(S.mx_ord[a]);
+        const double e = __dsub_rn((double)hi, (double)lo);
+        if (e > E) E = e;
+        S.mn[a] = __fadd_rn(lo, 0.0f);  // report -0.0 as +0.0
+    }
+    S.invalid = (S.nonfinite != 0u || parts[p].nverts == 0 || !(E > 0.0)) ? 1u : 0u;
+    S.scale = S.invalid ? 0.0 : __ddiv_rn(2097151.0, E);
+}
+
+__global__ void __launch_bounds__(256) k_quantise(const SPart *__restrict__ parts, const uint64_t *__restrict__ cofs,
+                                                  int nparts, const SState *__restrict__ st, int32_t *__restrict__ q) {
+    const int p = find_part(cofs, nparts, blockIdx.x);
+    const SPart P = parts[p];
+    const SState &S = st[p];
     if (S.invalid) return;
     const double sc = S.scale;
-    for (uint64_t i = threadIdx.x; i < 3ull * P.nverts; i += blockDim.x) {
+    const uint64_t v0 = (blockIdx.x - cofs[p]) * (uint64_t)VCHUNK;
+    const uint64_t v1 = min((uint64_t)P.nverts, v0 + VCHUNK);
+    for (uint64_t i = 3 * v0 + threadIdx.x; i < 3 * v1; i += blockDim.x) {
         const int a = (int)(i % 3);
         const double t = __dmul_rn(__dsub_rn((double)P.xyz[i], (double)S.mn[a]), sc);
         int64_t v = (int64_t)floor(t);
@@ -764,8 +791,8 @@ bs_status sample_visible_parts(const bs_mesh *meshes, const int *res, int nparts
         make_frame(d, views.v[i]);
     }
     std::vector<SPart> hp((size_t)nparts);
-    std::vector<uint64_t> tofs((size_t)nparts), pofs((size_t)nparts);
-    uint64_t V = 0, T = 0, NP = 0;
+    std::vector<uint64_t> tofs((size_t)nparts), pofs((size_t)nparts), cofs((size_t)nparts);
+    uint64_t V = 0, T = 0, NP = 0, NC = 0;
     for (int p = 0; p < nparts; ++p) {
         const bs_mesh &m = meshes[p];
         if (res[p] < 1 || res[p] > BS_MAX_RES) { set_error("bs_sample_visible: part %d: res=%d outside [1,%d]", p, res[p], BS_MAX_RES); return BS_EINVAL; }
@@ -780,6 +807,8 @@ bs_status sample_visible_parts(const bs_mesh *meshes, const int *res, int nparts
         P.vofs = V; P.tofs = T; P.pofs = NP;
         tofs[(size_t)p] = T;
         pofs[(size_t)p] = NP;
+        cofs[(size_t)p] = NC;
+        NC += (m.nverts + VCHUNK - 1) / VCHUNK;
         V += m.nverts;
         T += m.ntris;
         NP += (uint64_t)ndirs * res[p] * res[p];
@@ -799,6 +828,7 @@ bs_status sample_visible_parts(const bs_mesh *meshes, const int *res, int nparts
         probe.take((size_t)nparts * sizeof(SState));
         probe.take((size_t)nparts * 8);
         probe.take((size_t)nparts * 8);
+        probe.take((size_t)nparts * 8);
         probe.take(3 * V * sizeof(int32_t));
         probe.take((size_t)ndirs * T * sizeof(TriSetup));
         probe.take(NP * sizeof(unsigned long long));
@@ -813,6 +843,7 @@ bs_status sample_visible_parts(const bs_mesh *meshes, const int *res, int nparts
     SState *d_st = (SState *)A.take((size_t)nparts * sizeof(SState));
     uint64_t *d_tofs = (uint64_t *)A.take((size_t)nparts * 8);
     uint64_t *d_pofs = (uint64_t *)A.take((size_t)nparts * 8);
+    uint64_t *d_cofs = (uint64_t *)A.take((size_t)nparts * 8);
     int32_t *q = (int32_t *)A.take(3 * V * sizeof(int32_t));
     TriSetup *setup = (TriSetup *)A.take((size_t)ndirs * T * sizeof(TriSetup));
     unsigned long long *depth = (unsigned long long *)A.take(NP * sizeof(unsigned long long));
@@ -826,14 +857,17 @@ bs_status sample_visible_parts(const bs_mesh *meshes, const int *res, int nparts
         if (cudaMemcpyAsync(d_parts, hp.data(), (size_t)nparts * sizeof(SPart), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
             cudaMemcpyAsync(d_tofs, tofs.data(), (size_t)nparts * 8, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
             cudaMemcpyAsync(d_pofs, pofs.data(), (size_t)nparts * 8, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+            cudaMemcpyAsync(d_cofs, cofs.data(), (size_t)nparts * 8, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
             cudaMemsetAsync(depth, 0xff, NP * sizeof(unsigned long long), stream) != cudaSuccess ||
             cudaMemsetAsync(tot, 0, 16, stream) != cudaSuccess) {
             set_error("bs_sample_visible: upload failed: %s", cudaGetErrorString(cudaGetLastError()));
             rc = BS_ECUDA;
             break;
         }
-        k_bbox<<<nparts, 256, 0, stream>>>(d_parts, d_st);
-        k_quantise<<<nparts, 256, 0, stream>>>(d_parts, d_st, q);
+        k_bbox_init<<<(nparts + 255) / 256, 256, 0, stream>>>(d_st, nparts);
+        k_bbox<<<(unsigned)NC, 256, 0, stream>>>(d_parts, d_cofs, nparts, d_st);
+        k_scale<<<(nparts + 255) / 256, 256, 0, stream>>>(d_parts, d_st, nparts);
+        k_quantise<<<(unsigned)NC, 256, 0, stream>>>(d_parts, d_cofs, nparts, d_st, q);
         if (T > 0) {
             dim3 gs((unsigned)std::min<uint64_t>((T + 255) / 256, (uint64_t)sms * 32), ndirs);
             k_setup<<<gs, 256, 0, stream>>>(d_parts, d_tofs, nparts, T, q, d_st, views, setup);

@@ -61,68 +61,73 @@ def run(seed: int = 0, lines: int = 20, per_line: int = 2500, group: int = 50, n
     res = SceneResult()
     tp = _tris_per_part(nboxes, ncyl)
     vp = _verts_per_part(nboxes, ncyl)
+    lres = {**LEVEL_RES, **(level_res or {})}
     torch.cuda.synchronize()
     t0 = time.perf_counter()
 
-    lres = {**LEVEL_RES, **(level_res or {})}
-
-    def finish(idx_list, meshes, level):
-        r = lres[level]
-        sv = bs.sample_visible_batched(meshes, [r] * len(meshes), dirs)
-        ntri = [int(m[1].shape[0]) for m in meshes]
-        mc = [node_bound(t, s["n"]) for t, s in zip(ntri, sv)]
-        live = [j for j in range(len(sv)) if mc[j] > 0]
-        orders = [None] * len(sv)
-        got = bs.order_batched([sv[j]["key"] for j in live], seeds=[seed] * len(live),
-                               part_ids=[idx_list[j] for j in live], max_counts=[mc[j] for j in live],
-                               scales=[sv[j]["scale"] for j in live])
-        for j, o in zip(live, got):
-            orders[j] = o
+    def wave(level, idx, counts):
+        """Generates the nodes idx (node j holds counts[j] parts) into one packed mesh, then
+        samples and orders them with one batched call each."""
+        counts = np.asarray(counts, np.int64)
+        pstart = np.concatenate([[0], np.cumsum(counts)])
+        tot = int(pstart[-1])
+        dev = torch.device("cuda")
+        xyz = torch.empty((tot * vp, 3), dtype=torch.float32, device=dev)
+        tri = torch.empty((tot * tp, 3), dtype=torch.int32, device=dev)
+        rgb = torch.empty((tot * tp, 3), dtype=torch.uint8, device=dev)
+        if np.all(counts == 1):
+            bs.scene_generate(seed, [nodes[i].parts(per_line)[0] for i in idx], nboxes, ncyl, local_indices=True,
+                              out=(xyz, tri, rgb))
+        else:
+            for j, i in enumerate(idx):  # node-local vertex indices: one call per node
+                a, b = int(pstart[j]), int(pstart[j + 1])
+                bs.scene_generate(seed, nodes[i].parts(per_line), nboxes, ncyl,
+                                  out=(xyz[a * vp:b * vp], tri[a * tp:b * tp], rgb[a * tp:b * tp]))
+        ntris = counts * tp
+        sv = bs.sample_visible_packed(xyz, tri, rgb, pstart[:-1] * vp, counts * vp, pstart[:-1] * tp, ntris,
+                                      lres[level], dirs)
+        del xyz, tri, rgb
+        n = sv["n"]
+        mc = np.minimum(np.minimum(NODE_BOUND, ntris // 2), n)
+        live = np.nonzero(mc > 0)[0]
+        idx = np.asarray(idx, np.int64)
+        perm, rad2, _, mofs = bs.order_packed(sv["key"], sv["ofs"][live], n[live], max_counts=mc[live], seeds=seed,
+                                              part_ids=idx[live], scales=sv["scale"][live])
         lv = res.per_level.setdefault(level, {"nodes": 0, "sampled": 0, "ordered": 0, "triangles": 0})
-        for i, s, o, m, t in zip(idx_list, sv, orders, mc, ntri):
-            res.surfels_sampled += s["n"]
-            res.surfels_ordered += m
-            res.triangles += t
-            lv["nodes"] += 1
-            lv["sampled"] += s["n"]
-            lv["ordered"] += m
-            lv["triangles"] += t
+        lv["nodes"] += len(idx)
+        lv["sampled"] += int(n.sum())
+        lv["ordered"] += int(mc.sum())
+        lv["triangles"] += int(ntris.sum())
+        res.nodes += len(idx)
+        res.surfels_sampled += int(n.sum())
+        res.surfels_ordered += int(mc.sum())
+        res.triangles += int(ntris.sum())
+        slot = {int(j): k for k, j in enumerate(live)}
+        for j, i in enumerate(idx.tolist()):
             if i in keep:
-                perm, rad2 = (o[0].cpu().numpy().view(np.uint32), o[1].cpu().numpy()) if o else (None, None)
-                res.kept[i] = (s["key"].cpu().numpy().view(np.uint64), perm, rad2)
-        res.nodes += len(idx_list)
+                a = int(sv["ofs"][j])
+                key = sv["key"][a:a + int(n[j])].cpu().numpy().view(np.uint64)
+                if j in slot:
+                    lo, hi = int(mofs[slot[j]]), int(mofs[slot[j] + 1])
+                    res.kept[i] = (key, perm[lo:hi].cpu().numpy().view(np.uint32), rad2[lo:hi].cpu().numpy())
+                else:
+                    res.kept[i] = (key, None, None)
 
     by_level = {0: [], 1: [], 2: []}
     for i, nd in enumerate(nodes):
         by_level[nd.level].append(i)
-    def level_done(level, t):
-        torch.cuda.synchronize()
-        if level in res.per_level:
-            res.per_level[level]["seconds"] = time.perf_counter() - t
-
-    if 0 in levels:
-        tl = time.perf_counter()
-        leaves = by_level[0]
-        for w in range(0, len(leaves), leaf_wave):
-            idx = leaves[w:w + leaf_wave]
-            parts = [nodes[i].parts(per_line)[0] for i in idx]
-            xyz, tri, rgb = bs.scene_generate(seed, parts, nboxes, ncyl, local_indices=True)
-            meshes = [(xyz[q * vp:(q + 1) * vp], tri[q * tp:(q + 1) * tp], rgb[q * tp:(q + 1) * tp])
-                      for q in range(len(idx))]
-            finish(idx, meshes, 0)
-            del xyz, tri, rgb, meshes
-        level_done(0, tl)
-    for level, wave in ((1, group_wave), (2, 1)):
+    # leaves in waves of single parts, groups in waves of nodes, one line at a time
+    for level, wsize in ((0, leaf_wave), (1, group_wave), (2, 1)):
         if level not in levels:
             continue
         tl = time.perf_counter()
         ids = by_level[level]
-        for w in range(0, len(ids), wave):
-            idx = ids[w:w + wave]
-            meshes = [bs.scene_generate(seed, nodes[i].parts(per_line), nboxes, ncyl) for i in idx]
-            finish(idx, meshes, level)
-            del meshes
-        level_done(level, tl)
+        for w in range(0, len(ids), wsize):
+            idx = ids[w:w + wsize]
+            wave(level, idx, [nodes[i].count for i in idx])
+        torch.cuda.synchronize()
+        if level in res.per_level:
+            res.per_level[level]["seconds"] = time.perf_counter() - tl
     torch.cuda.synchronize()
     res.seconds = time.perf_counter() - t0
     return res

@@ -56,3 +56,27 @@ def test_bad_arguments_rejected_without_gpu():
     assert lib.bs_sample_visible(C.byref(mesh), bad, 1, 64, C.byref(out), None) == bs.BS_EINVAL
     st = C.c_int(0)
     assert lib.bs_server_create(0, 0, C.byref(st)) is None and st.value == bs.BS_EINVAL
+
+
+def test_numpy_struct_layout_matches_ctypes():
+    """The packed bindings fill struct arrays through numpy views; their layout must be the
+    ctypes (and so the C header's) layout."""
+    import numpy as np
+    from paper_1904_08225_gb300 import bs
+    a, arr = bs._struct_array(bs.Mesh, 3)
+    a["xyz"] = [16, 32, 48]
+    a["ntris"] = [1, 2, 3]
+    a["face_rgb"] = 2**40 + 8
+    assert arr[1].xyz == 32 and arr[2].ntris == 3 and arr[0].face_rgb == 2**40 + 8
+    s, sarr = bs._struct_array(bs.Surfels, 2)
+    s["n"] = [5, 6]
+    s["bbox_min"][1] = [1.5, 2.5, 3.5]
+    s["scale"] = 0.25
+    assert sarr[1].n == 6 and list(sarr[1].bbox_min) == [1.5, 2.5, 3.5] and sarr[0].scale == 0.25
+    sarr[0].n = 99  # and back: the C side writes n through the same memory
+    assert s["n"][0] == 99
+    o, oarr = bs._struct_array(bs.OrderOpts, 2)
+    o["seed"] = np.uint64(2**63 + 1)
+    o["start"] = -1
+    o["sample_step"] = 500
+    assert oarr[1].seed == 2**63 + 1 and oarr[1].start == -1 and oarr[0].sample_step == 500

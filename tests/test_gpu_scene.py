@@ -124,3 +124,33 @@ def test_full_scene_seeded_subset(bs):
         key, perm, rad2 = out.kept[i]
         assert len(perm) == scene.node_bound(nodes[i].count * 19_200, len(key))
         _invariants(key, perm, rad2, [1, 2, 17, len(perm) // 2, len(perm) - 1])
+
+
+def test_packed_bindings_match_list_bindings(bs):
+    """sample_visible_packed / order_packed (pointer arrays built with numpy) give the same
+    surfels and orderings as the per-part list bindings."""
+    import torch
+    parts = [(p, 0, p) for p in range(5)]
+    nb, nc = 10, 3
+    vp, tp = nb * W.BOX_VERTS + nc * W.CYL_VERTS, nb * W.BOX_TRIS + nc * W.CYL_TRIS
+    xyz, tri, rgb = bs.scene_generate(3, parts, nb, nc, local_indices=True)
+    P = len(parts)
+    res = [64, 96, 128, 80, 64]
+    sv = bs.sample_visible_packed(xyz, tri, rgb, np.arange(P) * vp, [vp] * P, np.arange(P) * tp, [tp] * P, res,
+                                  W.AXIS_DIRS)
+    meshes = [(xyz[q * vp:(q + 1) * vp], tri[q * tp:(q + 1) * tp], rgb[q * tp:(q + 1) * tp]) for q in range(P)]
+    ref = bs.sample_visible_batched(meshes, res, W.AXIS_DIRS)
+    for q in range(P):
+        a, n = int(sv["ofs"][q]), int(sv["n"][q])
+        assert n == ref[q]["n"] and sv["scale"][q] == ref[q]["scale"]
+        for f in ("key", "nrm", "rgb", "src"):
+            assert torch.equal(sv[f][a:a + n], ref[q][f]), (q, f)
+    mc = [0, 100, 5, 10**9, 1]
+    perm, rad2, radius, mofs = bs.order_packed(sv["key"], sv["ofs"], sv["n"], max_counts=mc, seeds=11,
+                                               part_ids=[7, 8, 9, 10, 11], scales=sv["scale"])
+    got = bs.order_batched([r["key"] for r in ref], seeds=[11] * P, part_ids=[7, 8, 9, 10, 11], max_counts=mc,
+                           scales=[r["scale"] for r in ref])
+    for q in range(P):
+        lo, hi = int(mofs[q]), int(mofs[q + 1])
+        assert torch.equal(perm[lo:hi], got[q][0]) and torch.equal(rad2[lo:hi], got[q][1])
+        assert torch.equal(radius[lo:hi], got[q][2])
