@@ -222,7 +222,8 @@ def config_dict(args, specs):
     return {"workload": f"batched ordering: {len(specs)} tori, lognormal tris 2k-50k, lognormal surfels "
                         f"(median 20k, 1k-500k), 6 axis views at 16^2-1024^2, exact greedy order",
             "parts": len(specs), "seed": args.seed, "dirs": 6,
-            "l2": "inputs larger than L2 (meshes + keys ~ GBs, no flush needed)"}
+            "l2": "inputs larger than L2 (meshes + keys ~ GBs, no flush needed)"} | \
+        ({"tuning": dict(kv.split("=") for kv in args.tune)} if args.tune else {})
 
 
 # ---------------------------------------------------------------------------
@@ -243,6 +244,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip plain / served / cpu baseline legs")
     ap.add_argument("--scene-lines", type=int, default=20, help="production lines of the scene leg (0 skips it)")
     ap.add_argument("--scene-per-line", type=int, default=2500)
+    ap.add_argument("--tune", action="append", default=[], metavar="KNOB=VALUE",
+                    help="bs_set_tuning launch-shape knob for the run (repeatable)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     specs = rank_specs(args.parts, args.seed, rank)
@@ -257,6 +260,9 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     lib = bs.load()
+    for kv in args.tune:
+        name, val = kv.split("=")
+        bs.set_tuning(name, int(val))
     stream = torch.cuda.current_stream()
     dev = torch.device("cuda", local)
 

@@ -264,6 +264,12 @@ bs_status bs_scene_generate(uint64_t seed, const uint64_t *part_ids, const int32
 /* Launch-shape knobs for the autotuner (results never depend on them):
  *  "order_threads"      threads per ordering CTA (64, 128, 256, 512, 1024; 0 = auto)
  *  "order_ctas_per_sm"  cap on resident ordering CTAs per SM (0 = occupancy limit)
+ *  "order_quarters"     batched rounds launch in 1024-thread CTAs that order the largest
+ *                       parts on the whole CTA, then split into four 256-thread quarters
+ *                       taking one part each: 0 = when a cost model predicts a gain,
+ *                       1 = never, 2 = always (parts over 524,288 points stay whole)
+ *  "order_full_parts"   k > 0: the k largest parts run on whole CTAs before the quarters
+ *                       (0 = the cost model decides)
  *  "order_algo"         2 = exact multi-pick rounds (default), 1 = one pick per step
  *  "kernel_timing"      1 = record CUDA events around internal kernels (bs_last_launch_ms)
  * Process-wide; BS_EINVAL for an unknown name or value. */

@@ -94,6 +94,14 @@ bs_status bs_set_tuning(const char *name, int value) {
         if (value != 0 && value != 1) { set_error("bs_set_tuning: kernel_timing=%d not 0 or 1", value); return BS_EINVAL; }
         order_set_kernel_timing(value == 1);
         return BS_OK;
+    } else if (!strcmp(name, "order_quarters")) {
+        if (value != 0 && value != 1 && value != 2) { set_error("bs_set_tuning: order_quarters=%d not 0, 1 or 2", value); return BS_EINVAL; }
+        order_set_quarters(value);
+        return BS_OK;
+    } else if (!strcmp(name, "order_full_parts")) {
+        if (value < 0) { set_error("bs_set_tuning: order_full_parts=%d negative", value); return BS_EINVAL; }
+        order_set_full_parts(value);
+        return BS_OK;
     } else if (!strcmp(name, "order_ctas_per_sm")) {
         if (value < 0 || value > 32) { set_error("bs_set_tuning: order_ctas_per_sm=%d outside [0,32]", value); return BS_EINVAL; }
         ctas = value;

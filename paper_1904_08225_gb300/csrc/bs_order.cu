@@ -26,6 +26,7 @@
 //                 touched group updating its touched buckets.     (the update sweep)
 //   k_radius      radius[k] = sqrt(rad2[k]) / scale in IEEE double, as float.
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <vector>
 
@@ -217,14 +218,51 @@ constexpr int TIE_GROUPS = 8;  // groups a tie window may span
 constexpr int SMAX = 256;      // variant 1: largest random subset per round
 constexpr int SPL = SMAX / 32;
 constexpr int NB_SMEM = 2048;  // parts with at most this many buckets keep bucket records in shared memory
-constexpr size_t ROUNDS_SMEM_STATIC = 18 * 1024;  // bound on the kernel's static shared memory
 constexpr size_t SMEM_LIMIT = 227 * 1024;
+// Quarter mode: a 1024-thread CTA runs four parts at once, 256 threads each, so four
+// independent latency chains share the SM (one part's single simulating warp overlaps
+// the others' sweeps).  A quarter takes parts of at most Q_SG super-groups.
+constexpr int QT = 256;
+constexpr int LB = 4;          // buckets whose loads are issued together in the gather and apply sweeps
+constexpr int Q_SG = 16;       // 524,288 points
+constexpr int Q_NB = 1024;     // bucket records in shared memory up to 32,768 points
 
-// shared-memory bucket capacity for a launch whose largest part has ngmax groups
-static int rounds_nbsm(int ngmax) {
-    return (size_t)NB_SMEM * 24 + (size_t)ngmax * 28 + ROUNDS_SMEM_STATIC <= SMEM_LIMIT ? NB_SMEM : 0;
+// Per-part shared state of the rounds kernel (one per part slot).
+template <int SG>
+struct RoundsSm {
+    uint64_t sgkey[SG], sglo[SG], sghi[SG], sgmask[SG];
+    uint32_t sglist[SG], heavy[SG];
+    uint64_t ck[CAP];
+    int64_t cd[CAP];
+    uint32_t ci[CAP];
+    uint64_t pk[MAXP];
+    int64_t pd[MAXP];
+    uint32_t pi[MAXP];
+    uint32_t sc[SMAX];   // variant 1: the round's sample (index), sorted by index
+    int64_t sd[SMAX];    //            its distance to the chosen set
+    uint64_t sk[SMAX];   //            its position
+    uint32_t ppos[MAXP], tail[MAXP];
+    uint32_t part, ccnt, gcnt, sgcnt, npick, icut, nheavy;
+    int shift;
+    int64_t tieD;
+};
+
+// Bytes of one part slot: the state, then bucket (bkey, blo, bhi: nbcap each) and group
+// (gkey, glo, ghi: ngcap each; glist: ngcap u32) records.
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+template <int SG>
+__host__ __device__ constexpr size_t slot_bytes(int nbcap, int ngcap) {
+    return align16(sizeof(RoundsSm<SG>)) + (size_t)nbcap * 24 + align16((size_t)ngcap * 28);
 }
-static size_t rounds_smem(int ngmax) { return (size_t)rounds_nbsm(ngmax) * 24 + (size_t)ngmax * 28; }
+
+// full-mode bucket capacity for a launch whose largest part has ngmax groups
+static int rounds_nbsm(int ngmax) {
+    return slot_bytes<MAX_SG>(NB_SMEM, ngmax) <= SMEM_LIMIT ? NB_SMEM : 0;
+}
+
+__device__ __forceinline__ void part_sync(int bar, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthreads) : "memory");
+}
 
 __device__ __forceinline__ uint64_t pick_mask(uint32_t np, const uint32_t *pi, const uint64_t *pk, uint64_t allow,
                                               uint32_t own_shift, uint32_t own, uint64_t lo, uint64_t hi, int64_t maxD) {
@@ -238,537 +276,545 @@ __device__ __forceinline__ uint64_t pick_mask(uint32_t np, const uint32_t *pi, c
     return (uint64_t)__ballot_sync(0xffffffffu, ra) | ((uint64_t)__ballot_sync(0xffffffffu, rb) << 32);
 }
 
-template <int T>
-__global__ void __launch_bounds__(T) k_order_rounds(const PartDesc *__restrict__ parts, int nparts,
-                                                    uint32_t *__restrict__ next_part, int ngmax, int nbsm) {
-    static_assert(T >= CAP && T >= SMAX, "the candidate and sample sorts need one thread per entry");
-    constexpr int NW = T / 32;
-    extern __shared__ uint64_t sm[];
-    uint64_t *s_bkey = sm;
-    uint64_t *s_blo = sm + nbsm;
-    uint64_t *s_bhi = sm + 2 * nbsm;
-    uint64_t *s_gkey = sm + 3 * nbsm;
-    uint64_t *s_glo = s_gkey + ngmax;
-    uint64_t *s_ghi = s_gkey + 2 * ngmax;
-    uint32_t *s_glist = (uint32_t *)(s_gkey + 3 * ngmax);
-    __shared__ uint64_t s_sgkey[MAX_SG], s_sglo[MAX_SG], s_sghi[MAX_SG], s_sgmask[MAX_SG];
-    __shared__ uint32_t s_sglist[MAX_SG], s_heavy[MAX_SG];
-    __shared__ uint32_t s_nheavy;
-    __shared__ uint64_t s_ck[CAP];
-    __shared__ int64_t s_cd[CAP];
-    __shared__ uint32_t s_ci[CAP];
-    __shared__ uint64_t s_pk[MAXP];
-    __shared__ int64_t s_pd[MAXP];
-    __shared__ uint32_t s_pi[MAXP];
-    __shared__ uint32_t s_sc[SMAX];   // variant 1: the round's sample (index), sorted by index
-    __shared__ int64_t s_sd[SMAX];    //            its distance to the chosen set
-    __shared__ uint64_t s_sk[SMAX];   //            its position
-    __shared__ uint32_t s_ppos[MAXP], s_tail[MAXP];
-    __shared__ uint32_t s_part, s_ccnt, s_gcnt, s_sgcnt, s_npick, s_icut;
-    __shared__ int s_shift;
-    __shared__ int64_t s_tieD;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
-    for (;;) {
-        if (threadIdx.x == 0) s_part = atomicAdd(next_part, 1u);
-        __syncthreads();
-        const uint32_t p = s_part;
-        if (p >= (uint32_t)nparts) break;
-        const PartDesc P = parts[p];
-        const uint32_t ng = P.ng, ns = (ng + 31) / 32;
-        const uint32_t n = P.n, nb = P.nb, m = P.m;
-        const uint64_t *__restrict__ key = P.key;
-        int64_t *__restrict__ Dg = P.D;
-        // bucket records: shared memory when they fit (generic pointers either way)
-        const bool bsm = nb <= (uint32_t)nbsm;
-        uint64_t *bkey = bsm ? s_bkey : P.bkey;
-        const uint64_t *blo_p = bsm ? s_blo : P.blo;
-        const uint64_t *bhi_p = bsm ? s_bhi : P.bhi;
-        for (uint32_t g = threadIdx.x; g < ng; g += T) {
-            s_gkey[g] = P.gkey[g];
-            s_glo[g] = P.glo[g];
-            s_ghi[g] = P.ghi[g];
+// One part ordered by TP threads (thread tid of them, warp-aligned) that synchronise on
+// named barrier `bar`; S and the record arrays are this part slot's shared memory.
+template <int TP, int SG>
+__device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm, unsigned char *slot, int nbsm,
+                                            int ngcap, int tid, int bar) {
+    static_assert(TP >= CAP && TP >= SMAX, "the candidate and sample sorts need one thread per entry");
+    constexpr int NW = TP / 32;
+    const int lane = tid & 31, warp = tid >> 5;
+    uint64_t *s_bkey = (uint64_t *)(slot + align16(sizeof(RoundsSm<SG>)));
+    uint64_t *s_blo = s_bkey + nbsm;
+    uint64_t *s_bhi = s_bkey + 2 * nbsm;
+    uint64_t *s_gkey = s_bkey + 3 * nbsm;
+    uint64_t *s_glo = s_gkey + ngcap;
+    uint64_t *s_ghi = s_gkey + 2 * ngcap;
+    uint32_t *s_glist = (uint32_t *)(s_gkey + 3 * ngcap);
+    const uint32_t ng = P.ng, ns = (ng + 31) / 32;
+    const uint32_t n = P.n, nb = P.nb, m = P.m;
+    const uint64_t *__restrict__ key = P.key;
+    int64_t *__restrict__ Dg = P.D;
+    // bucket records: shared memory when they fit (generic pointers either way)
+    const bool bsm = nb <= (uint32_t)nbsm;
+    uint64_t *bkey = bsm ? s_bkey : P.bkey;
+    const uint64_t *blo_p = bsm ? s_blo : P.blo;
+    const uint64_t *bhi_p = bsm ? s_bhi : P.bhi;
+    for (uint32_t g = tid; g < ng; g += TP) {
+        s_gkey[g] = P.gkey[g];
+        s_glo[g] = P.glo[g];
+        s_ghi[g] = P.ghi[g];
+    }
+    if (bsm) {
+        for (uint32_t b = tid; b < nb; b += TP) {
+            s_bkey[b] = P.bkey[b];
+            s_blo[b] = P.blo[b];
+            s_bhi[b] = P.bhi[b];
         }
-        if (bsm) {
-            for (uint32_t b = threadIdx.x; b < nb; b += T) {
-                s_bkey[b] = P.bkey[b];
-                s_blo[b] = P.blo[b];
-                s_bhi[b] = P.bhi[b];
+    }
+    if (tid == 0) {
+        P.perm[0] = P.start;
+        P.rad2[0] = INT64_MAX;
+        Sm.shift = 3;
+        Sm.tieD = -2;
+        if (P.variant == 1) {  // remove the start from the remaining set (swap with the last)
+            const uint32_t y = P.R[n - 1];
+            P.R[P.start] = y;
+            P.pos[y] = P.start;
+        }
+    }
+    part_sync(bar, TP);
+    uint32_t round_t = 0;
+    for (uint32_t sg = warp; sg < ns; sg += NW) {
+        const uint32_t g = sg * 32 + lane;
+        const bool vg = g < ng;
+        const uint64_t gk = vg ? s_gkey[g] : 0ull;
+        const uint64_t cand = vg ? (((gk >> 10) << 15) | (uint64_t)(32767 - (lane * 1024 + (1023 - (int)(gk & 1023))))) : 0ull;
+        const uint64_t sk = warp_max_u64(cand);
+        const uint64_t lo = vg ? s_glo[g] : ~0ull, hi = vg ? s_ghi[g] : 0ull;
+        const uint32_t lx = __reduce_min_sync(FULL, vg ? pos_x(lo) : 0xffffffffu);
+        const uint32_t ly = __reduce_min_sync(FULL, vg ? pos_y(lo) : 0xffffffffu);
+        const uint32_t lz = __reduce_min_sync(FULL, vg ? pos_z(lo) : 0xffffffffu);
+        const uint32_t hx = __reduce_max_sync(FULL, vg ? pos_x(hi) : 0u);
+        const uint32_t hy = __reduce_max_sync(FULL, vg ? pos_y(hi) : 0u);
+        const uint32_t hz = __reduce_max_sync(FULL, vg ? pos_z(hi) : 0u);
+        if (lane == 0) {
+            Sm.sgkey[sg] = sk;
+            Sm.sglo[sg] = pack_pos(lx, ly, lz);
+            Sm.sghi[sg] = pack_pos(hx, hy, hz);
+        }
+    }
+    part_sync(bar, TP);
+    uint32_t k = 1;
+    while (k < m) {
+      if (P.variant == 1) {
+        // (S1) the round's random subset of the remaining set R[0, n - k)
+        const uint32_t L = n - k, S = P.sample_size;
+        uint32_t c = 0, slot = 0;
+        int64_t cd = 0;
+        uint64_t ck = 0;
+        if (tid < S) {
+            const uint32_t ctr[4] = {P.part_id, round_t, (uint32_t)tid, 1u};
+            const uint32_t kk[2] = {(uint32_t)P.seed, (uint32_t)(P.seed >> 32)};
+            uint32_t w[4];
+            philox4x32_10(ctr, kk, w);
+            c = P.R[(uint32_t)(((uint64_t)w[0] * L) >> 32)];
+            Sm.sc[tid] = c;
+            cd = Dg[c];
+            ck = key[c];
+        }
+        part_sync(bar, TP);
+        // (S2) sorted by index (equal entries adjacent): slot = #smaller + #equal before
+        if (tid < S) {
+            for (uint32_t u = 0; u < S; ++u) {
+                const uint32_t o = Sm.sc[u];
+                slot += (o < c || (o == c && u < tid)) ? 1u : 0u;
             }
         }
-        if (threadIdx.x == 0) {
-            P.perm[0] = P.start;
-            P.rad2[0] = INT64_MAX;
-            s_shift = 3;
-            s_tieD = -2;
-            if (P.variant == 1) {  // remove the start from the remaining set (swap with the last)
-                const uint32_t y = P.R[n - 1];
-                P.R[P.start] = y;
-                P.pos[y] = P.start;
-            }
+        part_sync(bar, TP);
+        if (tid < S) {
+            Sm.sc[slot] = c;
+            Sm.sd[slot] = cd;
+            Sm.sk[slot] = ck;
         }
-        __syncthreads();
-        uint32_t round_t = 0;
-        for (uint32_t sg = warp; sg < ns; sg += NW) {
-            const uint32_t g = sg * 32 + lane;
-            const bool vg = g < ng;
-            const uint64_t gk = vg ? s_gkey[g] : 0ull;
-            const uint64_t cand = vg ? (((gk >> 10) << 15) | (uint64_t)(32767 - (lane * 1024 + (1023 - (int)(gk & 1023))))) : 0ull;
-            const uint64_t sk = warp_max_u64(cand);
-            const uint64_t lo = vg ? s_glo[g] : ~0ull, hi = vg ? s_ghi[g] : 0ull;
-            const uint32_t lx = __reduce_min_sync(FULL, vg ? pos_x(lo) : 0xffffffffu);
-            const uint32_t ly = __reduce_min_sync(FULL, vg ? pos_y(lo) : 0xffffffffu);
-            const uint32_t lz = __reduce_min_sync(FULL, vg ? pos_z(lo) : 0xffffffffu);
-            const uint32_t hx = __reduce_max_sync(FULL, vg ? pos_x(hi) : 0u);
-            const uint32_t hy = __reduce_max_sync(FULL, vg ? pos_y(hi) : 0u);
-            const uint32_t hz = __reduce_max_sync(FULL, vg ? pos_z(hi) : 0u);
-            if (lane == 0) {
-                s_sgkey[sg] = sk;
-                s_sglo[sg] = pack_pos(lx, ly, lz);
-                s_sghi[sg] = pack_pos(hx, hy, hz);
+        part_sync(bar, TP);
+        // (S3) the m_t = 1 + t / step distinct samples farthest from the chosen set
+        //      (distances as of the round start), ties to the lowest index
+        if (warp == 0) {
+            uint32_t cs[SPL];
+            int64_t ds[SPL];
+            bool live[SPL];
+#pragma unroll
+            for (int u = 0; u < SPL; ++u) {
+                const uint32_t sl = lane + 32 * u;
+                live[u] = sl < S;
+                cs[u] = live[u] ? Sm.sc[sl] : 0u;
+                ds[u] = live[u] ? Sm.sd[sl] : 0;
             }
-        }
-        __syncthreads();
-        uint32_t k = 1;
-        while (k < m) {
-          if (P.variant == 1) {
-            // (S1) the round's random subset of the remaining set R[0, n - k)
-            const uint32_t L = n - k, S = P.sample_size;
-            uint32_t c = 0, slot = 0;
-            int64_t cd = 0;
-            uint64_t ck = 0;
-            if (threadIdx.x < S) {
-                const uint32_t ctr[4] = {P.part_id, round_t, threadIdx.x, 1u};
-                const uint32_t kk[2] = {(uint32_t)P.seed, (uint32_t)(P.seed >> 32)};
-                uint32_t w[4];
-                philox4x32_10(ctr, kk, w);
-                c = P.R[(uint32_t)(((uint64_t)w[0] * L) >> 32)];
-                s_sc[threadIdx.x] = c;
-                cd = Dg[c];
-                ck = key[c];
-            }
-            __syncthreads();
-            // (S2) sorted by index (equal entries adjacent): slot = #smaller + #equal before
-            if (threadIdx.x < S) {
-                for (uint32_t u = 0; u < S; ++u) {
-                    const uint32_t o = s_sc[u];
-                    slot += (o < c || (o == c && u < threadIdx.x)) ? 1u : 0u;
+            const uint32_t mt = 1u + (P.sample_step ? round_t / P.sample_step : 0u);
+            const uint32_t budget = min(min(mt, (uint32_t)MAXP), m - k);
+            uint32_t np = 0;
+            while (np < budget) {
+                uint64_t kmax = 0;
+#pragma unroll
+                for (int u = 0; u < SPL; ++u)
+                    if (live[u]) kmax = max(kmax, ((uint64_t)(ds[u] + 1) << 8) | (uint64_t)(255 - (lane + 32 * u)));
+                const uint64_t best = warp_max_u64(kmax);
+                if (best == 0) break;
+                const uint32_t sl = 255u - (uint32_t)(best & 255u);
+                const uint32_t cb = Sm.sc[sl];
+                if (lane == 0) {
+                    Sm.pi[np] = cb;
+                    Sm.pk[np] = Sm.sk[sl];
+                    Sm.pd[np] = (int64_t)(best >> 8) - 1;
                 }
+                ++np;
+#pragma unroll
+                for (int u = 0; u < SPL; ++u)
+                    if (cs[u] == cb) live[u] = false;
             }
-            __syncthreads();
-            if (threadIdx.x < S) {
-                s_sc[slot] = c;
-                s_sd[slot] = cd;
-                s_sk[slot] = ck;
+            if (lane == 0) Sm.npick = np;
+        }
+        part_sync(bar, TP);
+        const uint32_t npk = Sm.npick;
+        // (S4) rad2 of a pick: its distance to every earlier pick; gather what the removal needs
+        int64_t r2 = 0;
+        if (tid < npk) {
+            r2 = Sm.pd[tid];
+            const uint64_t q = Sm.pk[tid];
+            for (uint32_t u = 0; u < tid; ++u) r2 = min(r2, dist2(q, Sm.pk[u]));
+            Sm.ppos[tid] = P.pos[Sm.pi[tid]];
+            Sm.tail[tid] = P.R[L - npk + tid];
+        }
+        part_sync(bar, TP);
+        if (tid < npk) Sm.pd[tid] = r2;
+        // (S5) remove the picks in pick order, each swapped with the current last entry;
+        //      the last entries all lie in the tail window [L - npk, L) held in Sm.tail
+        if (tid == 0) {
+            const uint32_t base = L - npk;
+            for (uint32_t q = 0; q < npk; ++q) {
+                const uint32_t pp = Sm.ppos[q];
+                const uint32_t y = Sm.tail[L - q - 1 - base];
+                if (pp >= base) {
+                    Sm.tail[pp - base] = y;
+                } else {
+                    P.R[pp] = y;
+                    P.pos[y] = pp;
+                }
+                for (uint32_t r = q + 1; r < npk; ++r)
+                    if (Sm.pi[r] == y) Sm.ppos[r] = pp;
             }
-            __syncthreads();
-            // (S3) the m_t = 1 + t / step distinct samples farthest from the chosen set
-            //      (distances as of the round start), ties to the lowest index
+        }
+        ++round_t;
+        part_sync(bar, TP);
+      } else {
+        // (1) current maximum (every warp computes it; no barrier needed)
+        uint64_t top = 0;
+        for (uint32_t sg = lane; sg < ns; sg += 32) top = max(top, ((Sm.sgkey[sg] >> 15) << 8) | (uint64_t)(255 - sg));
+        top = warp_max_u64(top);
+        const int64_t D1 = (int64_t)(top >> 8) - 1;
+        const uint32_t sgj = 255u - (uint32_t)(top & 255u);
+        const uint32_t j = sgj * 32768u + (32767u - (uint32_t)(Sm.sgkey[sgj] & 32767u));
+        // (2) threshold: tau = D1 (1 - 2^-shift); when more than CAP points tie at D1, a tie
+        //     window instead: tau = D1 and an index cut (the lowest-index tied points fit)
+        const int shift = Sm.shift;
+        const bool tie = D1 == Sm.tieD;
+        const int64_t tau = tie ? D1 : D1 - (D1 >> shift);
+        part_sync(bar, TP);
+        if (tid == 0) { Sm.ccnt = 0; Sm.gcnt = 0; Sm.sgcnt = 0; Sm.icut = 0xffffffffu; }
+        part_sync(bar, TP);
+        // (3) gather the candidates
+        if (tie) {
+            // D1 points in index order from j on, over up to TIE_GROUPS groups holding D1
+            // points, while they fit; icut = first index left out (no D1 point lies below j)
             if (warp == 0) {
-                uint32_t cs[SPL];
-                int64_t ds[SPL];
-                bool live[SPL];
-#pragma unroll
-                for (int u = 0; u < SPL; ++u) {
-                    const uint32_t sl = lane + 32 * u;
-                    live[u] = sl < S;
-                    cs[u] = live[u] ? s_sc[sl] : 0u;
-                    ds[u] = live[u] ? s_sd[sl] : 0;
-                }
-                const uint32_t mt = 1u + (P.sample_step ? round_t / P.sample_step : 0u);
-                const uint32_t budget = min(min(mt, (uint32_t)MAXP), m - k);
-                uint32_t np = 0;
-                while (np < budget) {
-                    uint64_t kmax = 0;
-#pragma unroll
-                    for (int u = 0; u < SPL; ++u)
-                        if (live[u]) kmax = max(kmax, ((uint64_t)(ds[u] + 1) << 8) | (uint64_t)(255 - (lane + 32 * u)));
-                    const uint64_t best = warp_max_u64(kmax);
-                    if (best == 0) break;
-                    const uint32_t sl = 255u - (uint32_t)(best & 255u);
-                    const uint32_t cb = s_sc[sl];
-                    if (lane == 0) {
-                        s_pi[np] = cb;
-                        s_pk[np] = s_sk[sl];
-                        s_pd[np] = (int64_t)(best >> 8) - 1;
-                    }
-                    ++np;
-#pragma unroll
-                    for (int u = 0; u < SPL; ++u)
-                        if (cs[u] == cb) live[u] = false;
-                }
-                if (lane == 0) s_npick = np;
-            }
-            __syncthreads();
-            const uint32_t npk = s_npick;
-            // (S4) rad2 of a pick: its distance to every earlier pick; gather what the removal needs
-            int64_t r2 = 0;
-            if (threadIdx.x < npk) {
-                r2 = s_pd[threadIdx.x];
-                const uint64_t q = s_pk[threadIdx.x];
-                for (uint32_t u = 0; u < threadIdx.x; ++u) r2 = min(r2, dist2(q, s_pk[u]));
-                s_ppos[threadIdx.x] = P.pos[s_pi[threadIdx.x]];
-                s_tail[threadIdx.x] = P.R[L - npk + threadIdx.x];
-            }
-            __syncthreads();
-            if (threadIdx.x < npk) s_pd[threadIdx.x] = r2;
-            // (S5) remove the picks in pick order, each swapped with the current last entry;
-            //      the last entries all lie in the tail window [L - npk, L) held in s_tail
-            if (threadIdx.x == 0) {
-                const uint32_t base = L - npk;
-                for (uint32_t q = 0; q < npk; ++q) {
-                    const uint32_t pp = s_ppos[q];
-                    const uint32_t y = s_tail[L - q - 1 - base];
-                    if (pp >= base) {
-                        s_tail[pp - base] = y;
-                    } else {
-                        P.R[pp] = y;
-                        P.pos[y] = pp;
-                    }
-                    for (uint32_t r = q + 1; r < npk; ++r)
-                        if (s_pi[r] == y) s_ppos[r] = pp;
-                }
-            }
-            ++round_t;
-            __syncthreads();
-          } else {
-            // (1) current maximum (every warp computes it; no barrier needed)
-            uint64_t top = 0;
-            for (uint32_t sg = lane; sg < ns; sg += 32) top = max(top, ((s_sgkey[sg] >> 15) << 8) | (uint64_t)(255 - sg));
-            top = warp_max_u64(top);
-            const int64_t D1 = (int64_t)(top >> 8) - 1;
-            const uint32_t sgj = 255u - (uint32_t)(top & 255u);
-            const uint32_t j = sgj * 32768u + (32767u - (uint32_t)(s_sgkey[sgj] & 32767u));
-            // (2) threshold: tau = D1 (1 - 2^-shift); when more than CAP points tie at D1, a tie
-            //     window instead: tau = D1 and an index cut (the lowest-index tied points fit)
-            const int shift = s_shift;
-            const bool tie = D1 == s_tieD;
-            const int64_t tau = tie ? D1 : D1 - (D1 >> shift);
-            __syncthreads();
-            if (threadIdx.x == 0) { s_ccnt = 0; s_gcnt = 0; s_sgcnt = 0; s_icut = 0xffffffffu; }
-            __syncthreads();
-            // (3) gather the candidates
-            if (tie) {
-                // D1 points in index order from j on, over up to TIE_GROUPS groups holding D1
-                // points, while they fit; icut = first index left out (no D1 point lies below j)
-                if (warp == 0) {
-                    uint32_t cnt = 0, icut = n, used = 0;
-                    bool full = false;
-                    for (uint32_t g0 = j >> 10; g0 < ng && !full && used < TIE_GROUPS; ++g0) {
-                        if ((int64_t)(s_gkey[g0] >> 10) - 1 < tau) continue;
-                        ++used;
-                        const uint32_t b = g0 * 32 + lane;
-                        const uint64_t bk = (b < nb && b >= (j >> 5)) ? bkey[b] : 0ull;
-                        uint32_t mask = __ballot_sync(FULL, (int64_t)(bk >> 5) - 1 >= tau);
-                        while (mask) {
-                            const int bb = __ffs(mask) - 1;
-                            mask &= mask - 1;
-                            const uint32_t i = (g0 * 32 + bb) * 32 + lane;
-                            const int64_t d = i < n ? Dg[i] : -1;
-                            const uint64_t ki = i < n ? key[i] : 0ull;
-                            const bool c = d >= tau;
-                            const uint32_t cm = __ballot_sync(FULL, c);
-                            if (cnt + __popc(cm) > (uint32_t)CAP) {
-                                icut = (g0 * 32 + bb) * 32;
-                                full = true;
-                                break;
-                            }
-                            if (c) {
-                                const uint32_t slot = cnt + __popc(cm & ((1u << lane) - 1u));
-                                s_ci[slot] = i;
-                                s_cd[slot] = d;
-                                s_ck[slot] = ki;
-                            }
-                            cnt += __popc(cm);
-                        }
-                        if (!full && used == TIE_GROUPS) icut = min(n, (g0 + 1) * 1024u);
-                    }
-                    if (lane == 0) { s_ccnt = cnt; s_icut = icut; }
-                }
-            } else {
-                for (uint32_t sg = threadIdx.x; sg < ns; sg += T)
-                    if ((int64_t)(s_sgkey[sg] >> 15) - 1 >= tau) s_sglist[atomicAdd(&s_sgcnt, 1u)] = sg;
-                __syncthreads();
-                const uint32_t nsgl = s_sgcnt;
-                for (uint32_t li = warp; li < nsgl; li += NW) {
-                    const uint32_t g = s_sglist[li] * 32 + lane;
-                    if (g < ng && (int64_t)(s_gkey[g] >> 10) - 1 >= tau) s_glist[atomicAdd(&s_gcnt, 1u)] = g;
-                }
-                __syncthreads();
-                const uint32_t ngl = s_gcnt;
-                for (uint32_t li = warp; li < ngl; li += NW) {
-                    const uint32_t g = s_glist[li];
-                    const uint32_t b = g * 32 + lane;
-                    const uint64_t bk = b < nb ? bkey[b] : 0ull;
+                uint32_t cnt = 0, icut = n, used = 0;
+                bool full = false;
+                for (uint32_t g0 = j >> 10; g0 < ng && !full && used < TIE_GROUPS; ++g0) {
+                    if ((int64_t)(s_gkey[g0] >> 10) - 1 < tau) continue;
+                    ++used;
+                    const uint32_t b = g0 * 32 + lane;
+                    const uint64_t bk = (b < nb && b >= (j >> 5)) ? bkey[b] : 0ull;
                     uint32_t mask = __ballot_sync(FULL, (int64_t)(bk >> 5) - 1 >= tau);
                     while (mask) {
-                        // up to eight buckets per pass so their loads overlap
-                        uint32_t bbs[8];
-                        int nb8 = 0;
-                        while (mask && nb8 < 8) {
-                            bbs[nb8++] = (uint32_t)(__ffs(mask) - 1);
-                            mask &= mask - 1;
+                        const int bb = __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        const uint32_t i = (g0 * 32 + bb) * 32 + lane;
+                        const int64_t d = i < n ? Dg[i] : -1;
+                        const uint64_t ki = i < n ? key[i] : 0ull;
+                        const bool c = d >= tau;
+                        const uint32_t cm = __ballot_sync(FULL, c);
+                        if (cnt + __popc(cm) > (uint32_t)CAP) {
+                            icut = (g0 * 32 + bb) * 32;
+                            full = true;
+                            break;
                         }
-                        int64_t d[8];
-                        uint64_t ki[8];
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            const uint32_t i = (g * 32 + (u < nb8 ? bbs[u] : 0)) * 32 + lane;
-                            const bool ok = u < nb8 && i < n;
-                            d[u] = ok ? Dg[i] : -1;
-                            ki[u] = ok ? key[i] : 0ull;
+                        if (c) {
+                            const uint32_t slot = cnt + __popc(cm & ((1u << lane) - 1u));
+                            Sm.ci[slot] = i;
+                            Sm.cd[slot] = d;
+                            Sm.ck[slot] = ki;
                         }
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            if (u < nb8 && d[u] >= tau && d[u] >= 0) {
-                                const uint32_t slot = atomicAdd(&s_ccnt, 1u);
-                                if (slot < CAP) {
-                                    s_ci[slot] = (g * 32 + bbs[u]) * 32 + lane;
-                                    s_cd[slot] = d[u];
-                                    s_ck[slot] = ki[u];
-                                }
-                            }
-                        }
+                        cnt += __popc(cm);
                     }
+                    if (!full && used == TIE_GROUPS) icut = min(n, (g0 + 1) * 1024u);
                 }
+                if (lane == 0) { Sm.ccnt = cnt; Sm.icut = icut; }
             }
-            __syncthreads();
-            const uint32_t ccnt = s_ccnt;
-            const uint32_t icut = s_icut;
-            if (ccnt > CAP) {
-                // too many candidates: move tau toward D1 by about log2(ccnt / CAP) halvings;
-                // at tau == D1 switch to the tie window until D1 drops
-                if (threadIdx.x == 0) {
-                    if (tau == D1) {
-                        s_tieD = D1;
-                    } else {
-                        int inc = 1;
-                        for (uint32_t c = ccnt / CAP; c > 1; c >>= 1) ++inc;
-                        s_shift = min(shift + inc, 62);
-                    }
-                }
-                __syncthreads();
-                continue;
-            }
-            // (4) candidates in index order: slot order is the lowest-index tie-break
-            if (!tie) {
-                uint32_t ci = 0, rank = 0;
-                int64_t cd = 0;
-                uint64_t ck = 0;
-                if (threadIdx.x < ccnt) {
-                    ci = s_ci[threadIdx.x];
-                    cd = s_cd[threadIdx.x];
-                    ck = s_ck[threadIdx.x];
-                    for (uint32_t u = 0; u < ccnt; ++u) rank += s_ci[u] < ci ? 1u : 0u;
-                }
-                __syncthreads();
-                if (threadIdx.x < ccnt) {
-                    s_ci[rank] = ci;
-                    s_cd[rank] = cd;
-                    s_ck[rank] = ck;
-                }
-                __syncthreads();
-            }
-            // (5) the greedy restricted to C, one warp, while the best stays above (tau, icut);
-            //     slot lane + 32u lives in lane's register u
-            if (warp == 0) {
-                int64_t Dc[CPL];
-                uint64_t qc[CPL];
-                bool live[CPL];
-#pragma unroll
-                for (int u = 0; u < CPL; ++u) {
-                    const uint32_t sl = lane + 32 * u;
-                    live[u] = sl < ccnt;
-                    Dc[u] = live[u] ? s_cd[sl] : 0;
-                    qc[u] = live[u] ? s_ck[sl] : 0ull;
-                }
-                const uint32_t budget = min((uint32_t)MAXP, m - k);
-                uint32_t np = 0;
-                while (np < budget) {
-                    uint64_t kmax = 0;
-#pragma unroll
-                    for (int u = 0; u < CPL; ++u)
-                        if (live[u]) kmax = max(kmax, ((uint64_t)(Dc[u] + 1) << 8) | (uint64_t)(255 - (lane + 32 * u)));
-                    const uint64_t best = warp_max_u64(kmax);
-                    if (best == 0) break;
-                    const uint32_t slot = 255u - (uint32_t)(best & 255u);
-                    const int64_t Dbest = (int64_t)(best >> 8) - 1;
-                    const uint32_t idx = s_ci[slot];
-                    if (!(Dbest > tau || (Dbest == tau && idx < icut))) break;
-                    const uint64_t qbest = s_ck[slot];
-                    if (lane == 0) {
-                        s_pk[np] = qbest;
-                        s_pi[np] = idx;
-                        s_pd[np] = Dbest;
-                    }
-                    ++np;
-#pragma unroll
-                    for (int u = 0; u < CPL; ++u) {
-                        if (lane + 32 * u == slot) {
-                            live[u] = false;
-                        } else if (live[u]) {
-                            Dc[u] = min(Dc[u], dist2(qc[u], qbest));
-                            live[u] = Dc[u] >= tau;  // below tau it cannot be picked in this round
-                        }
-                    }
-                }
-                if (lane == 0) s_npick = np;
-            }
-            if (threadIdx.x == 0 && !tie && ccnt < CAP / 4 && shift > 1) s_shift = shift - 1;
-            __syncthreads();
-          }
-            const uint32_t np = s_npick;
-            // (6) apply the round's picks to the whole part
-            for (uint32_t t = threadIdx.x; t < np; t += T) {
-                Dg[s_pi[t]] = -1;
-                P.perm[k + t] = s_pi[t];
-                P.rad2[k + t] = s_pd[t];
-            }
-            if (threadIdx.x == 0) { s_sgcnt = 0; s_gcnt = 0; }
-            __syncthreads();
-            const uint64_t all = np >= 64 ? ~0ull : ((1ull << np) - 1ull);
-            for (uint32_t sg = warp; sg < ns; sg += NW) {
-                const uint64_t mk = pick_mask(np, s_pi, s_pk, all, 15, sg, s_sglo[sg], s_sghi[sg],
-                                              (int64_t)(s_sgkey[sg] >> 15) - 1);
-                if (mk && lane == 0) {
-                    s_sgmask[sg] = mk;
-                    s_sglist[atomicAdd(&s_sgcnt, 1u)] = sg;
-                }
-            }
-            __syncthreads();
-            const uint32_t nsgl = s_sgcnt;
-            if (threadIdx.x == 0) s_nheavy = 0;
-            __syncthreads();
+        } else {
+            for (uint32_t sg = tid; sg < ns; sg += TP)
+                if ((int64_t)(Sm.sgkey[sg] >> 15) - 1 >= tau) Sm.sglist[atomicAdd(&Sm.sgcnt, 1u)] = sg;
+            part_sync(bar, TP);
+            const uint32_t nsgl = Sm.sgcnt;
             for (uint32_t li = warp; li < nsgl; li += NW) {
-                const uint32_t sg = s_sglist[li];
-                const uint64_t sgm = s_sgmask[sg];
-                if (__popcll((long long)sgm) <= 4) {
-                    // few picks: one lane per group walks them
-                    const uint32_t g = sg * 32 + lane;
-                    if (g < ng) {
-                        const int64_t gD = (int64_t)(s_gkey[g] >> 10) - 1;
-                        const uint64_t lo = s_glo[g], hi = s_ghi[g];
-                        uint64_t mm = sgm;
-                        bool rel = false;
-                        while (mm && !rel) {
-                            const int t = __ffsll((long long)mm) - 1;
-                            mm &= mm - 1;
-                            rel = (s_pi[t] >> 10) == g || box_dist2(lo, hi, s_pk[t]) < gD;
-                        }
-                        if (rel) s_glist[atomicAdd(&s_gcnt, 1u)] = g;
-                    }
-                } else if (lane == 0) {
-                    s_heavy[atomicAdd(&s_nheavy, 1u)] = sg;
-                }
+                const uint32_t g = Sm.sglist[li] * 32 + lane;
+                if (g < ng && (int64_t)(s_gkey[g] >> 10) - 1 >= tau) s_glist[atomicAdd(&Sm.gcnt, 1u)] = g;
             }
-            __syncthreads();
-            {
-                // many picks: one warp per (super-group, group), the lanes test the picks
-                const uint32_t nh = s_nheavy;
-                for (uint32_t it = warp; it < nh * 32; it += NW) {
-                    const uint32_t sg = s_heavy[it >> 5];
-                    const uint32_t g = sg * 32 + (it & 31);
-                    if (g >= ng) continue;
-                    const uint64_t gm = pick_mask(np, s_pi, s_pk, s_sgmask[sg], 10, g, s_glo[g], s_ghi[g],
-                                                  (int64_t)(s_gkey[g] >> 10) - 1);
-                    if (gm && lane == 0) s_glist[atomicAdd(&s_gcnt, 1u)] = g;
-                }
-            }
-            __syncthreads();
-            const uint32_t ngl = s_gcnt;
+            part_sync(bar, TP);
+            const uint32_t ngl = Sm.gcnt;
             for (uint32_t li = warp; li < ngl; li += NW) {
                 const uint32_t g = s_glist[li];
-                const uint64_t gm = pick_mask(np, s_pi, s_pk, s_sgmask[g >> 5], 10, g, s_glo[g], s_ghi[g],
-                                              (int64_t)(s_gkey[g] >> 10) - 1);
                 const uint32_t b = g * 32 + lane;
-                const bool vb = b < nb;
-                uint64_t bk = vb ? bkey[b] : 0ull;
-                const uint64_t blo = vb ? blo_p[b] : 0ull, bhi = vb ? bhi_p[b] : 0ull;
-                const int64_t bD = (int64_t)(bk >> 5) - 1;
-                // picks that may lower a D in this lane's bucket
-                uint64_t bm = 0;
-                if (vb) {
-                    uint64_t mm = gm;
-                    while (mm) {
-                        const int t = __ffsll((long long)mm) - 1;
-                        mm &= mm - 1;
-                        if ((s_pi[t] >> 5) == b || box_dist2(blo, bhi, s_pk[t]) < bD) bm |= 1ull << t;
-                    }
-                }
-                uint32_t amask = __ballot_sync(FULL, bm != 0);
-                const bool aff = bm != 0;
-                while (amask) {
-                    // up to eight affected buckets per pass so their loads overlap
-                    uint32_t bbs[8];
+                const uint64_t bk = b < nb ? bkey[b] : 0ull;
+                uint32_t mask = __ballot_sync(FULL, (int64_t)(bk >> 5) - 1 >= tau);
+                while (mask) {
+                    // up to LB buckets per pass so their loads overlap
+                    uint32_t bbs[LB];
                     int nb8 = 0;
-                    while (amask && nb8 < 8) {
-                        bbs[nb8++] = (uint32_t)(__ffs(amask) - 1);
-                        amask &= amask - 1;
+                    while (mask && nb8 < LB) {
+                        bbs[nb8++] = (uint32_t)(__ffs(mask) - 1);
+                        mask &= mask - 1;
                     }
-                    int64_t d[8];
-                    uint64_t ki[8];
+                    int64_t d[LB];
+                    uint64_t ki[LB];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
+                    for (int u = 0; u < LB; ++u) {
                         const uint32_t i = (g * 32 + (u < nb8 ? bbs[u] : 0)) * 32 + lane;
                         const bool ok = u < nb8 && i < n;
                         d[u] = ok ? Dg[i] : -1;
                         ki[u] = ok ? key[i] : 0ull;
                     }
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        if (u >= nb8) break;
-                        const uint32_t i = (g * 32 + bbs[u]) * 32 + lane;
-                        const uint64_t mu = __shfl_sync(FULL, bm, (int)bbs[u]);
-                        int64_t dd = d[u];
-                        if (dd > 0) {
-                            int64_t nd = dd;
-                            uint64_t mm = mu;
-                            while (mm) {
-                                const int t = __ffsll((long long)mm) - 1;
-                                mm &= mm - 1;
-                                nd = min(nd, dist2(ki[u], s_pk[t]));
-                            }
-                            if (nd < dd) {
-                                dd = nd;
-                                Dg[i] = nd;
+                    for (int u = 0; u < LB; ++u) {
+                        if (u < nb8 && d[u] >= tau && d[u] >= 0) {
+                            const uint32_t slot = atomicAdd(&Sm.ccnt, 1u);
+                            if (slot < CAP) {
+                                Sm.ci[slot] = (g * 32 + bbs[u]) * 32 + lane;
+                                Sm.cd[slot] = d[u];
+                                Sm.ck[slot] = ki[u];
                             }
                         }
-                        const uint64_t nk = i < n ? (((uint64_t)(dd + 1) << 5) | (uint64_t)(31 - lane)) : 0ull;
-                        const uint64_t nbk = warp_max_u64(nk);
-                        if (lane == (int)bbs[u]) bk = nbk;
                     }
                 }
-                if (aff) bkey[b] = bk;
-                const uint64_t cand = vb ? (((bk >> 5) << 10) | (uint64_t)(1023 - (lane * 32 + (31 - (int)(bk & 31))))) : 0ull;
-                const uint64_t ngk = warp_max_u64(cand);
-                if (lane == 0) s_gkey[g] = ngk;
             }
-            __syncthreads();
-            for (uint32_t li = warp; li < nsgl; li += NW) {
-                const uint32_t sg = s_sglist[li];
+        }
+        part_sync(bar, TP);
+        const uint32_t ccnt = Sm.ccnt;
+        const uint32_t icut = Sm.icut;
+        if (ccnt > CAP) {
+            // too many candidates: move tau toward D1 by about log2(ccnt / CAP) halvings;
+            // at tau == D1 switch to the tie window until D1 drops
+            if (tid == 0) {
+                if (tau == D1) {
+                    Sm.tieD = D1;
+                } else {
+                    int inc = 1;
+                    for (uint32_t c = ccnt / CAP; c > 1; c >>= 1) ++inc;
+                    Sm.shift = min(shift + inc, 62);
+                }
+            }
+            part_sync(bar, TP);
+            continue;
+        }
+        // (4) candidates in index order: slot order is the lowest-index tie-break
+        if (!tie) {
+            uint32_t ci = 0, rank = 0;
+            int64_t cd = 0;
+            uint64_t ck = 0;
+            if (tid < ccnt) {
+                ci = Sm.ci[tid];
+                cd = Sm.cd[tid];
+                ck = Sm.ck[tid];
+                for (uint32_t u = 0; u < ccnt; ++u) rank += Sm.ci[u] < ci ? 1u : 0u;
+            }
+            part_sync(bar, TP);
+            if (tid < ccnt) {
+                Sm.ci[rank] = ci;
+                Sm.cd[rank] = cd;
+                Sm.ck[rank] = ck;
+            }
+            part_sync(bar, TP);
+        }
+        // (5) the greedy restricted to C, one warp, while the best stays above (tau, icut);
+        //     slot lane + 32u lives in lane's register u
+        if (warp == 0) {
+            int64_t Dc[CPL];
+            uint64_t qc[CPL];
+            bool live[CPL];
+#pragma unroll
+            for (int u = 0; u < CPL; ++u) {
+                const uint32_t sl = lane + 32 * u;
+                live[u] = sl < ccnt;
+                Dc[u] = live[u] ? Sm.cd[sl] : 0;
+                qc[u] = live[u] ? Sm.ck[sl] : 0ull;
+            }
+            const uint32_t budget = min((uint32_t)MAXP, m - k);
+            uint32_t np = 0;
+            while (np < budget) {
+                uint64_t kmax = 0;
+#pragma unroll
+                for (int u = 0; u < CPL; ++u)
+                    if (live[u]) kmax = max(kmax, ((uint64_t)(Dc[u] + 1) << 8) | (uint64_t)(255 - (lane + 32 * u)));
+                const uint64_t best = warp_max_u64(kmax);
+                if (best == 0) break;
+                const uint32_t slot = 255u - (uint32_t)(best & 255u);
+                const int64_t Dbest = (int64_t)(best >> 8) - 1;
+                const uint32_t idx = Sm.ci[slot];
+                if (!(Dbest > tau || (Dbest == tau && idx < icut))) break;
+                const uint64_t qbest = Sm.ck[slot];
+                if (lane == 0) {
+                    Sm.pk[np] = qbest;
+                    Sm.pi[np] = idx;
+                    Sm.pd[np] = Dbest;
+                }
+                ++np;
+#pragma unroll
+                for (int u = 0; u < CPL; ++u) {
+                    if (lane + 32 * u == slot) {
+                        live[u] = false;
+                    } else if (live[u]) {
+                        Dc[u] = min(Dc[u], dist2(qc[u], qbest));
+                        live[u] = Dc[u] >= tau;  // below tau it cannot be picked in this round
+                    }
+                }
+            }
+            if (lane == 0) Sm.npick = np;
+        }
+        if (tid == 0 && !tie && ccnt < CAP / 4 && shift > 1) Sm.shift = shift - 1;
+        part_sync(bar, TP);
+      }
+        const uint32_t np = Sm.npick;
+        // (6) apply the round's picks to the whole part
+        for (uint32_t t = tid; t < np; t += TP) {
+            Dg[Sm.pi[t]] = -1;
+            P.perm[k + t] = Sm.pi[t];
+            P.rad2[k + t] = Sm.pd[t];
+        }
+        if (tid == 0) { Sm.sgcnt = 0; Sm.gcnt = 0; }
+        part_sync(bar, TP);
+        const uint64_t all = np >= 64 ? ~0ull : ((1ull << np) - 1ull);
+        for (uint32_t sg = warp; sg < ns; sg += NW) {
+            const uint64_t mk = pick_mask(np, Sm.pi, Sm.pk, all, 15, sg, Sm.sglo[sg], Sm.sghi[sg],
+                                          (int64_t)(Sm.sgkey[sg] >> 15) - 1);
+            if (mk && lane == 0) {
+                Sm.sgmask[sg] = mk;
+                Sm.sglist[atomicAdd(&Sm.sgcnt, 1u)] = sg;
+            }
+        }
+        part_sync(bar, TP);
+        const uint32_t nsgl = Sm.sgcnt;
+        if (tid == 0) Sm.nheavy = 0;
+        part_sync(bar, TP);
+        for (uint32_t li = warp; li < nsgl; li += NW) {
+            const uint32_t sg = Sm.sglist[li];
+            const uint64_t sgm = Sm.sgmask[sg];
+            if (__popcll((long long)sgm) <= 4) {
+                // few picks: one lane per group walks them
                 const uint32_t g = sg * 32 + lane;
-                const uint64_t gk = g < ng ? s_gkey[g] : 0ull;
-                const uint64_t cand = g < ng ? (((gk >> 10) << 15) | (uint64_t)(32767 - (lane * 1024 + (1023 - (int)(gk & 1023))))) : 0ull;
-                const uint64_t sk = warp_max_u64(cand);
-                if (lane == 0) s_sgkey[sg] = sk;
+                if (g < ng) {
+                    const int64_t gD = (int64_t)(s_gkey[g] >> 10) - 1;
+                    const uint64_t lo = s_glo[g], hi = s_ghi[g];
+                    uint64_t mm = sgm;
+                    bool rel = false;
+                    while (mm && !rel) {
+                        const int t = __ffsll((long long)mm) - 1;
+                        mm &= mm - 1;
+                        rel = (Sm.pi[t] >> 10) == g || box_dist2(lo, hi, Sm.pk[t]) < gD;
+                    }
+                    if (rel) s_glist[atomicAdd(&Sm.gcnt, 1u)] = g;
+                }
+            } else if (lane == 0) {
+                Sm.heavy[atomicAdd(&Sm.nheavy, 1u)] = sg;
             }
-            k += np;
-            __syncthreads();
         }
-        // the part's radii, then its completion flag (host-mapped memory, after a
-        // system-scope fence so the host sees every output of the part first)
-        if (P.radius)
-            for (uint32_t q = threadIdx.x; q < m; q += T) {
-                const int64_t r2 = P.rad2[q];
-                P.radius[q] = r2 == INT64_MAX ? __int_as_float(0x7f800000)
-                                              : (float)__ddiv_rn(__dsqrt_rn((double)r2), P.scale);
+        part_sync(bar, TP);
+        {
+            // many picks: one warp per (super-group, group), the lanes test the picks
+            const uint32_t nh = Sm.nheavy;
+            for (uint32_t it = warp; it < nh * 32; it += NW) {
+                const uint32_t sg = Sm.heavy[it >> 5];
+                const uint32_t g = sg * 32 + (it & 31);
+                if (g >= ng) continue;
+                const uint64_t gm = pick_mask(np, Sm.pi, Sm.pk, Sm.sgmask[sg], 10, g, s_glo[g], s_ghi[g],
+                                              (int64_t)(s_gkey[g] >> 10) - 1);
+                if (gm && lane == 0) s_glist[atomicAdd(&Sm.gcnt, 1u)] = g;
             }
-        __syncthreads();
-        if (threadIdx.x == 0 && P.done) {
-            __threadfence_system();
-            *(volatile uint32_t *)P.done = 1u;
         }
+        part_sync(bar, TP);
+        const uint32_t ngl = Sm.gcnt;
+        for (uint32_t li = warp; li < ngl; li += NW) {
+            const uint32_t g = s_glist[li];
+            const uint64_t gm = pick_mask(np, Sm.pi, Sm.pk, Sm.sgmask[g >> 5], 10, g, s_glo[g], s_ghi[g],
+                                          (int64_t)(s_gkey[g] >> 10) - 1);
+            const uint32_t b = g * 32 + lane;
+            const bool vb = b < nb;
+            uint64_t bk = vb ? bkey[b] : 0ull;
+            const uint64_t blo = vb ? blo_p[b] : 0ull, bhi = vb ? bhi_p[b] : 0ull;
+            const int64_t bD = (int64_t)(bk >> 5) - 1;
+            // picks that may lower a D in this lane's bucket
+            uint64_t bm = 0;
+            if (vb) {
+                uint64_t mm = gm;
+                while (mm) {
+                    const int t = __ffsll((long long)mm) - 1;
+                    mm &= mm - 1;
+                    if ((Sm.pi[t] >> 5) == b || box_dist2(blo, bhi, Sm.pk[t]) < bD) bm |= 1ull << t;
+                }
+            }
+            uint32_t amask = __ballot_sync(FULL, bm != 0);
+            const bool aff = bm != 0;
+            while (amask) {
+                // up to LB affected buckets per pass so their loads overlap
+                uint32_t bbs[LB];
+                int nb8 = 0;
+                while (amask && nb8 < LB) {
+                    bbs[nb8++] = (uint32_t)(__ffs(amask) - 1);
+                    amask &= amask - 1;
+                }
+                int64_t d[LB];
+                uint64_t ki[LB];
+#pragma unroll
+                for (int u = 0; u < LB; ++u) {
+                    const uint32_t i = (g * 32 + (u < nb8 ? bbs[u] : 0)) * 32 + lane;
+                    const bool ok = u < nb8 && i < n;
+                    d[u] = ok ? Dg[i] : -1;
+                    ki[u] = ok ? key[i] : 0ull;
+                }
+#pragma unroll
+                for (int u = 0; u < LB; ++u) {
+                    if (u >= nb8) break;
+                    const uint32_t i = (g * 32 + bbs[u]) * 32 + lane;
+                    const uint64_t mu = __shfl_sync(FULL, bm, (int)bbs[u]);
+                    int64_t dd = d[u];
+                    if (dd > 0) {
+                        int64_t nd = dd;
+                        uint64_t mm = mu;
+                        while (mm) {
+                            const int t = __ffsll((long long)mm) - 1;
+                            mm &= mm - 1;
+                            nd = min(nd, dist2(ki[u], Sm.pk[t]));
+                        }
+                        if (nd < dd) {
+                            dd = nd;
+                            Dg[i] = nd;
+                        }
+                    }
+                    const uint64_t nk = i < n ? (((uint64_t)(dd + 1) << 5) | (uint64_t)(31 - lane)) : 0ull;
+                    const uint64_t nbk = warp_max_u64(nk);
+                    if (lane == (int)bbs[u]) bk = nbk;
+                }
+            }
+            if (aff) bkey[b] = bk;
+            const uint64_t cand = vb ? (((bk >> 5) << 10) | (uint64_t)(1023 - (lane * 32 + (31 - (int)(bk & 31))))) : 0ull;
+            const uint64_t ngk = warp_max_u64(cand);
+            if (lane == 0) s_gkey[g] = ngk;
+        }
+        part_sync(bar, TP);
+        for (uint32_t li = warp; li < nsgl; li += NW) {
+            const uint32_t sg = Sm.sglist[li];
+            const uint32_t g = sg * 32 + lane;
+            const uint64_t gk = g < ng ? s_gkey[g] : 0ull;
+            const uint64_t cand = g < ng ? (((gk >> 10) << 15) | (uint64_t)(32767 - (lane * 1024 + (1023 - (int)(gk & 1023))))) : 0ull;
+            const uint64_t sk = warp_max_u64(cand);
+            if (lane == 0) Sm.sgkey[sg] = sk;
+        }
+        k += np;
+        part_sync(bar, TP);
+    }
+    // the part's radii, then its completion flag (host-mapped memory, after a
+    // system-scope fence so the host sees every output of the part first)
+    if (P.radius)
+        for (uint32_t q = tid; q < m; q += TP) {
+            const int64_t r2 = P.rad2[q];
+            P.radius[q] = r2 == INT64_MAX ? __int_as_float(0x7f800000)
+                                          : (float)__ddiv_rn(__dsqrt_rn((double)r2), P.scale);
+        }
+    part_sync(bar, TP);
+    if (tid == 0 && P.done) {
+        __threadfence_system();
+        *(volatile uint32_t *)P.done = 1u;
+    }
+    part_sync(bar, TP);
+}
+
+// Persistent rounds kernel.  Parts [0, nfull) run one at a time on the whole CTA; with
+// QUARTERS (CT = 1024) the CTA then splits into four 256-thread quarters that take the
+// remaining parts [nfull, nparts) one each, on named barriers 1-4.  next[0] and next[1]
+// are the two phases' work counters.
+template <int CT, bool QUARTERS>
+__global__ void __launch_bounds__(CT) k_order_rounds(const PartDesc *__restrict__ parts, int nparts, int nfull,
+                                                     uint32_t *__restrict__ next, int ngmax, int nbsm, int ngq, int nbq) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ uint32_t s_part[4];
+    for (;;) {
+        if (threadIdx.x == 0) s_part[0] = atomicAdd(&next[0], 1u);
         __syncthreads();
+        const uint32_t p = s_part[0];
+        __syncthreads();
+        if (p >= (uint32_t)nfull) break;
+        rounds_part<CT, MAX_SG>(parts[p], *(RoundsSm<MAX_SG> *)smraw, smraw, nbsm, ngmax, threadIdx.x, 0);
+    }
+    if constexpr (QUARTERS) {
+        const int q = threadIdx.x / QT, tid = threadIdx.x % QT;
+        unsigned char *slot = smraw + (size_t)q * slot_bytes<Q_SG>(nbq, ngq);
+        for (;;) {
+            if (tid == 0) s_part[q] = (uint32_t)nfull + atomicAdd(&next[1], 1u);
+            part_sync(1 + q, QT);
+            const uint32_t p = s_part[q];
+            part_sync(1 + q, QT);
+            if (p >= (uint32_t)nparts) break;
+            rounds_part<QT, Q_SG>(parts[p], *(RoundsSm<Q_SG> *)slot, slot, nbq, ngq, tid, 1 + q);
+        }
     }
 }
 
@@ -796,6 +842,8 @@ struct LoopCfg {
 static int g_loop_threads_override = 0;   // set by bs_set_tuning("order_threads", v)
 static int g_order_algo = 2;              // 1 = one pick per step, 2 = exact multi-pick rounds
 static int g_ctas_per_sm_override = 0;    // set by bs_set_tuning("order_ctas_per_sm", v)
+static int g_quarters = 0;                // set by bs_set_tuning("order_quarters", v): 0 auto, 1 off, 2 on
+static int g_full_parts = 0;              // set by bs_set_tuning("order_full_parts", k); 0 = cost model
 
 void order_set_tuning(int threads, int ctas_per_sm) {
     g_loop_threads_override = threads;
@@ -803,6 +851,10 @@ void order_set_tuning(int threads, int ctas_per_sm) {
 }
 
 void order_set_algo(int algo) { g_order_algo = algo; }
+
+void order_set_quarters(int v) { g_quarters = v; }
+
+void order_set_full_parts(int k) { g_full_parts = k; }
 
 // Optional per-kernel timing: events recorded on the launch stream around one kernel.
 static bool g_kernel_timing = false;
@@ -835,40 +887,56 @@ bs_status order_last_launch_ms(int which, double *ms) {
     return BS_OK;
 }
 
+static size_t rounds_smem_full(int ngmax) { return slot_bytes<MAX_SG>(rounds_nbsm(ngmax), ngmax); }
+
+// quarter-mode bucket capacity: what is left of a quarter of the shared memory
+static int quarter_nbq(int ngq) {
+    const long left = (long)(SMEM_LIMIT / 4) - (long)align16(sizeof(RoundsSm<Q_SG>)) - (long)align16((size_t)ngq * 28);
+    return (int)std::max(0L, std::min((long)Q_NB, left / 24));
+}
+
+template <int CT, bool QU>
+static cudaError_t launch_rounds(const PartDesc *d_parts, int nparts, int nfull, uint32_t *d_next, int ngmax, int ngq,
+                                 int grid, cudaStream_t stream) {
+    const int nbq = QU ? quarter_nbq(ngq) : 0;
+    size_t smem = rounds_smem_full(ngmax);
+    if (QU) smem = std::max(smem, 4 * slot_bytes<Q_SG>(nbq, ngq));
+    cudaError_t e = cudaFuncSetAttribute(k_order_rounds<CT, QU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_order_rounds<CT, QU><<<grid, CT, smem, stream>>>(d_parts, nparts, nfull, d_next, ngmax, rounds_nbsm(ngmax), ngq,
+                                                        nbq);
+    return cudaGetLastError();
+}
+
 template <int T>
 static cudaError_t launch_loop(const PartDesc *d_parts, int nparts, uint32_t *d_next, int ngmax, int grid,
                                cudaStream_t stream, int algo) {
-    cudaError_t e;
     if (algo == 1) {
         const size_t smem = (size_t)ngmax * 36;
-        e = cudaFuncSetAttribute(k_order_loop<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_order_loop<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k_order_loop<T><<<grid, T, smem, stream>>>(d_parts, nparts, d_next, ngmax);
+        return cudaGetLastError();
     } else if constexpr (T >= CAP && T >= SMAX) {
-        const size_t smem = rounds_smem(ngmax);
-        e = cudaFuncSetAttribute(k_order_rounds<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_order_rounds<T><<<grid, T, smem, stream>>>(d_parts, nparts, d_next, ngmax, rounds_nbsm(ngmax));
+        return launch_rounds<T, false>(d_parts, nparts, nparts, d_next, ngmax, 0, grid, stream);
     } else {
         return cudaErrorInvalidConfiguration;  // the rounds kernel needs at least CAP threads
     }
-    return cudaGetLastError();
 }
 
 template <int T>
 static int occupancy(int ngmax, int algo) {
     int blocks = 0;
-    cudaError_t e;
+    cudaError_t e = cudaSuccess;
     if (algo == 1) {
         const size_t smem = (size_t)ngmax * 36;
         cudaFuncSetAttribute(k_order_loop<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_order_loop<T>, T, smem);
     } else if constexpr (T >= CAP && T >= SMAX) {
-        const size_t smem = rounds_smem(ngmax);
-        cudaFuncSetAttribute(k_order_rounds<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_order_rounds<T>, T, smem);
+        const size_t smem = rounds_smem_full(ngmax);
+        cudaFuncSetAttribute(k_order_rounds<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_order_rounds<T, false>, T, smem);
     } else {
-        e = cudaSuccess;
         blocks = 1;
     }
     if (e != cudaSuccess) {
@@ -887,9 +955,50 @@ static int pick_threads(int ngmax, bool batched, int algo) {
     return 512;
 }
 
-// one persistent loop launch over parts[0..nparts) with T threads per CTA
+// How many of the largest parts (sizes sorted descending) to run on whole 1024-thread
+// CTAs before the CTAs split into quarters for the rest; -1 when plain whole-CTA launches
+// are predicted faster.  Cost model (measured on GB300): a part costs n ln n; a whole CTA
+// orders at speed 1, a quarter at 0.41 with four per SM.  kmin parts are too large for a
+// quarter.
+static int quarter_split(const std::vector<uint32_t> &ns, int sms, int kmin) {
+    const int P = (int)ns.size();
+    if (kmin >= P) return -1;
+    std::vector<double> w(P), tail(P + 1, 0.0);
+    for (int i = 0; i < P; ++i) w[i] = (double)ns[i] * std::log((double)ns[i] + 2.0);
+    for (int i = P - 1; i >= 0; --i) tail[i] = tail[i + 1] + w[i];
+    const double RQ = 0.41;
+    double best = std::max(tail[0] / sms, w[0]);  // whole CTAs only
+    int pick = -1;
+    for (int k = kmin; k <= std::min(P - 1, std::max(kmin, sms)); ++k) {
+        const double tfull = k > 0 ? std::max(w[0], tail[0] - tail[k] > 0 ? (tail[0] - tail[k]) / sms : 0.0) : 0.0;
+        const int free_sms = std::max(1, sms - std::min(k, sms / 2));
+        const double tq = std::max(tail[k] / (4.0 * RQ * free_sms), w[k] / RQ);
+        const double t = std::max(tfull, tq);
+        if (t < best * 0.97) {  // a clear predicted gain only
+            best = t;
+            pick = k;
+        }
+    }
+    return pick;
+}
+
+// one persistent rounds launch over parts[0..nparts) (sorted by size, largest first; ns
+// their sizes, ngs their group counts); d_next holds two zeroed work counters
 static cudaError_t launch_set(const PartDesc *d_parts, int nparts, uint32_t *d_next, int ngmax, int T, int sms,
-                              cudaStream_t stream, int algo) {
+                              cudaStream_t stream, int algo, const std::vector<uint32_t> &ns,
+                              const std::vector<uint32_t> &ngs) {
+    if (algo == 2 && g_quarters != 1 && !(g_loop_threads_override && g_loop_threads_override != 1024)) {
+        int kmin = 0;
+        while (kmin < nparts && ngs[kmin] > (uint32_t)(Q_SG * 32)) ++kmin;
+        int nfull = -1;
+        if (g_full_parts > 0) nfull = std::max(kmin, std::min(g_full_parts, nparts));
+        else if (g_quarters == 2) nfull = kmin;
+        else if (nparts >= 2 * sms) nfull = quarter_split(ns, sms, kmin);
+        if (nfull >= 0 && nfull < nparts) {
+            const int ngq = (int)ngs[nfull];
+            return launch_rounds<1024, true>(d_parts, nparts, nfull, d_next, ngmax, ngq, sms, stream);
+        }
+    }
     int per_sm = 1;
     switch (T) {
         case 64: per_sm = occupancy<64>(ngmax, algo); break;
@@ -968,7 +1077,7 @@ bs_status order_parts(std::vector<PartDesc> &hp, cudaStream_t stream, bool batch
     do {
         if (cudaMemcpyAsync(d_parts, sorted.data(), (size_t)nparts * sizeof(PartDesc), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
             cudaMemcpyAsync(d_gofs, gofs.data(), (size_t)nparts * 4, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
-            cudaMemsetAsync(d_next, 0, 4, stream) != cudaSuccess) {
+            cudaMemsetAsync(d_next, 0, 8, stream) != cudaSuccess) {
             set_error("bs_order: descriptor upload failed: %s", cudaGetErrorString(cudaGetLastError()));
             rc = BS_ECUDA;
             break;
@@ -986,7 +1095,10 @@ bs_status order_parts(std::vector<PartDesc> &hp, cudaStream_t stream, bool batch
         for (const auto &q : sorted) sampled |= q.variant == 1 || q.done != nullptr;
         const int algo = sampled ? 2 : g_order_algo;
         timing_mark(1, 0, stream);
-        e = launch_set(d_parts, nparts, d_next, (int)ngmax, pick_threads((int)ngmax, batched, algo), sms, stream, algo);
+        std::vector<uint32_t> ns(nparts), ngs(nparts);
+        for (int r = 0; r < nparts; ++r) { ns[r] = sorted[r].n; ngs[r] = sorted[r].ng; }
+        e = launch_set(d_parts, nparts, d_next, (int)ngmax, pick_threads((int)ngmax, batched, algo), sms, stream, algo,
+                       ns, ngs);
         timing_mark(1, 1, stream);
         if (e != cudaSuccess) {
             set_error("bs_order: loop launch failed: %s", cudaGetErrorString(e));

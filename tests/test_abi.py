@@ -32,6 +32,10 @@ def test_error_message_and_tuning_validation():
     assert "order_threads" in bs.last_error()
     assert lib.bs_set_tuning(b"nope", 1) == bs.BS_EINVAL
     assert lib.bs_set_tuning(b"order_threads", 0) == bs.BS_OK
+    assert lib.bs_set_tuning(b"order_quarters", 3) == bs.BS_EINVAL
+    assert lib.bs_set_tuning(b"order_quarters", 0) == bs.BS_OK
+    assert lib.bs_set_tuning(b"order_full_parts", -1) == bs.BS_EINVAL
+    assert lib.bs_set_tuning(b"order_full_parts", 0) == bs.BS_OK
 
 
 def test_bad_arguments_rejected_without_gpu():

@@ -186,6 +186,42 @@ def test_order_batched_matches_single_and_oracle(bs):
         assert torch.equal(p1, perm) and torch.equal(r1, rad2)
 
 
+@pytest.mark.parametrize("threads,quarters,full_parts", [(0, 2, 0), (0, 2, 5), (0, 2, 200), (0, 0, 0), (0, 1, 0),
+                                                        (1024, 2, 3), (512, 0, 0)])
+def test_order_quarter_mode(bs, threads, quarters, full_parts):
+    """The batched rounds launch in 1024-thread CTAs (the largest parts on whole CTAs, the
+    rest four at a time on 256-thread quarters), forced or chosen by the cost model, gives
+    every part the result of the plain launch and of the oracle."""
+    g = np.random.default_rng(9)
+    keys, starts = [], []
+    for i in range(700):
+        n = int(g.integers(50, 4000)) if i % 97 else int(g.integers(20000, 70000))
+        pts = np.unique(g.integers(0, 1 << int(g.integers(6, 21)), size=(n, 3)), axis=0)
+        order = np.argsort(oracle.pack(pts), kind="stable")
+        keys.append(_dev(oracle.pack(pts[order]).view(np.int64)))
+        starts.append(int(g.integers(0, len(pts))))
+    try:
+        bs.set_tuning("order_quarters", 1)
+        base = bs.order_batched(keys, starts=starts)
+        bs.set_tuning("order_threads", threads)
+        bs.set_tuning("order_quarters", quarters)
+        bs.set_tuning("order_full_parts", full_parts)
+        got = bs.order_batched(keys, starts=starts)
+        again = bs.order_batched(keys, starts=starts)
+    finally:
+        bs.set_tuning("order_threads", 0)
+        bs.set_tuning("order_quarters", 0)
+        bs.set_tuning("order_full_parts", 0)
+    for i in range(len(keys)):
+        assert torch.equal(base[i][0], got[i][0]) and torch.equal(base[i][1], got[i][1]), i
+        assert torch.equal(base[i][2], got[i][2]), i
+    for i in range(0, len(keys), 7):
+        assert torch.equal(again[i][0], got[i][0]), i
+    for i in (0, 1, 97, 350, 699):
+        rp, rr = oracle.greedy(_np(keys[i]).view(np.uint64), starts[i])
+        assert np.array_equal(_np(got[i][0], np.uint32), rp) and np.array_equal(_np(got[i][1]), rr), i
+
+
 @pytest.mark.parametrize("threads", [64, 128, 256, 512, 1024])
 def test_order_launch_shape_independent(bs, threads):
     g = np.random.default_rng(4)
