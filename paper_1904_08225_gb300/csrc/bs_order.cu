@@ -588,43 +588,92 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
         // (5) the greedy restricted to C, one warp, while the best stays above (tau, icut);
         //     slot lane + 32u lives in lane's register u
         if (warp == 0) {
-            int64_t Dc[CPL];
-            uint64_t qc[CPL];
-            bool live[CPL];
-#pragma unroll
-            for (int u = 0; u < CPL; ++u) {
-                const uint32_t sl = lane + 32 * u;
-                live[u] = sl < ccnt;
-                Dc[u] = live[u] ? Sm.cd[sl] : 0;
-                qc[u] = live[u] ? Sm.ck[sl] : 0ull;
-            }
             const uint32_t budget = min((uint32_t)MAXP, m - k);
             uint32_t np = 0;
-            while (np < budget) {
-                uint64_t kmax = 0;
-#pragma unroll
-                for (int u = 0; u < CPL; ++u)
-                    if (live[u]) kmax = max(kmax, ((uint64_t)(Dc[u] + 1) << 8) | (uint64_t)(255 - (lane + 32 * u)));
-                const uint64_t best = warp_max_u64(kmax);
-                if (best == 0) break;
-                const uint32_t slot = 255u - (uint32_t)(best & 255u);
-                const int64_t Dbest = (int64_t)(best >> 8) - 1;
-                const uint32_t idx = Sm.ci[slot];
-                if (!(Dbest > tau || (Dbest == tau && idx < icut))) break;
-                const uint64_t qbest = Sm.ck[slot];
-                if (lane == 0) {
-                    Sm.pk[np] = qbest;
-                    Sm.pi[np] = idx;
-                    Sm.pd[np] = Dbest;
-                }
-                ++np;
+            if (D1 - tau < (int64_t)(1 << 25) - 1) {
+                // every candidate's D lies in [tau, D1] and stays there while it can be
+                // picked, so rp = D - tau + 1 < 2^25 (0 = out of the round) and a 32-bit
+                // key rp << 7 | (127 - slot) orders (D, lowest slot) in one reduction
+                uint32_t rp[CPL];
+                int32_t cx[CPL], cy[CPL], cz[CPL];
 #pragma unroll
                 for (int u = 0; u < CPL; ++u) {
-                    if (lane + 32 * u == slot) {
-                        live[u] = false;
-                    } else if (live[u]) {
-                        Dc[u] = min(Dc[u], dist2(qc[u], qbest));
-                        live[u] = Dc[u] >= tau;  // below tau it cannot be picked in this round
+                    const uint32_t sl = lane + 32 * u;
+                    const bool lv = sl < ccnt;
+                    const uint64_t q = lv ? Sm.ck[sl] : 0ull;
+                    rp[u] = lv ? (uint32_t)(Sm.cd[sl] - tau) + 1u : 0u;
+                    cx[u] = (int32_t)pos_x(q);
+                    cy[u] = (int32_t)pos_y(q);
+                    cz[u] = (int32_t)pos_z(q);
+                }
+                while (np < budget) {
+                    uint32_t kmax = 0;
+#pragma unroll
+                    for (int u = 0; u < CPL; ++u)
+                        kmax = max(kmax, rp[u] ? (rp[u] << 7) | (uint32_t)(127 - (lane + 32 * u)) : 0u);
+                    const uint32_t best = __reduce_max_sync(FULL, kmax);
+                    if (best == 0) break;
+                    const uint32_t slot = 127u - (best & 127u);
+                    const int64_t off = (int64_t)(best >> 7) - 1;
+                    const uint32_t idx = Sm.ci[slot];
+                    if (!(off > 0 || idx < icut)) break;
+                    const uint64_t qbest = Sm.ck[slot];
+                    if (lane == 0) {
+                        Sm.pk[np] = qbest;
+                        Sm.pi[np] = idx;
+                        Sm.pd[np] = tau + off;
+                    }
+                    ++np;
+                    const int32_t bx = (int32_t)pos_x(qbest), by = (int32_t)pos_y(qbest), bz = (int32_t)pos_z(qbest);
+#pragma unroll
+                    for (int u = 0; u < CPL; ++u) {
+                        if (lane + 32 * u == slot) {
+                            rp[u] = 0u;
+                        } else if (rp[u]) {
+                            const int32_t dx = cx[u] - bx, dy = cy[u] - by, dz = cz[u] - bz;
+                            const int64_t t = (int64_t)dx * dx + (int64_t)dy * dy + (int64_t)dz * dz - tau;
+                            // below tau it cannot be picked in this round
+                            if (t < (int64_t)rp[u] - 1) rp[u] = t < 0 ? 0u : (uint32_t)t + 1u;
+                        }
+                    }
+                }
+            } else {
+                int64_t Dc[CPL];
+                uint64_t qc[CPL];
+                bool live[CPL];
+#pragma unroll
+                for (int u = 0; u < CPL; ++u) {
+                    const uint32_t sl = lane + 32 * u;
+                    live[u] = sl < ccnt;
+                    Dc[u] = live[u] ? Sm.cd[sl] : 0;
+                    qc[u] = live[u] ? Sm.ck[sl] : 0ull;
+                }
+                while (np < budget) {
+                    uint64_t kmax = 0;
+#pragma unroll
+                    for (int u = 0; u < CPL; ++u)
+                        if (live[u]) kmax = max(kmax, ((uint64_t)(Dc[u] + 1) << 8) | (uint64_t)(255 - (lane + 32 * u)));
+                    const uint64_t best = warp_max_u64(kmax);
+                    if (best == 0) break;
+                    const uint32_t slot = 255u - (uint32_t)(best & 255u);
+                    const int64_t Dbest = (int64_t)(best >> 8) - 1;
+                    const uint32_t idx = Sm.ci[slot];
+                    if (!(Dbest > tau || (Dbest == tau && idx < icut))) break;
+                    const uint64_t qbest = Sm.ck[slot];
+                    if (lane == 0) {
+                        Sm.pk[np] = qbest;
+                        Sm.pi[np] = idx;
+                        Sm.pd[np] = Dbest;
+                    }
+                    ++np;
+#pragma unroll
+                    for (int u = 0; u < CPL; ++u) {
+                        if (lane + 32 * u == slot) {
+                            live[u] = false;
+                        } else if (live[u]) {
+                            Dc[u] = min(Dc[u], dist2(qc[u], qbest));
+                            live[u] = Dc[u] >= tau;  // below tau it cannot be picked in this round
+                        }
                     }
                 }
             }

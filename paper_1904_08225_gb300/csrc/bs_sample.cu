@@ -225,9 +225,24 @@ __global__ void __launch_bounds__(256) k_quantise(const SPart *__restrict__ part
 struct TriSetup {
     int32_t x[3], y[3];
     uint32_t w[3];
-    uint32_t ord;  // bits 0-1: input vertex of slot 0, 2-3 slot 1, 4-5 slot 2; 0xffffffff = skip
+    uint32_t ord;   // bits 0-1: input vertex of slot 0, 2-3 slot 1, 4-5 slot 2; bits 8-23: part;
+                    // 0xffffffff = skip
     int64_t area2;
+    uint64_t rcp;   // floor((2^64 - 1) / area2): exact division by area2, see div_area
 };
+
+__device__ __forceinline__ int setup_part(const TriSetup &s) { return (int)((s.ord >> 8) & 0xffffu); }
+
+// floor(num / d) for d >= 1 from m = floor((2^64 - 1) / d) (division by an invariant
+// integer, Granlund and Montgomery, PLDI 1994): the high word of num * m is at most two
+// below the quotient, so two conditional corrections make it exact.
+__device__ __forceinline__ uint64_t div_area(uint64_t num, uint64_t d, uint64_t m) {
+    uint64_t q = __umul64hi(num, m);
+    uint64_t r = num - q * d;
+    if (r >= d) { ++q; r -= d; }
+    if (r >= d) { ++q; }
+    return q;
+}
 
 __device__ __forceinline__ void project(const View &V, int res, const int32_t *q, int32_t &X, int32_t &Y,
                                         uint32_t &W) {
@@ -255,6 +270,7 @@ __global__ void k_setup(const SPart *__restrict__ parts, const uint64_t *__restr
         if (st[p].invalid || v0 >= P.nverts || v1 >= P.nverts || v2 >= P.nverts) {
             s.ord = 0xffffffffu;
             s.area2 = 0;
+            s.rcp = 0;
             out[(uint64_t)dir * T + tg] = s;
             if (!st[p].invalid && dir == 0) atomicAdd(&st[p].badtri, 1u);
             continue;
@@ -271,8 +287,9 @@ __global__ void k_setup(const SPart *__restrict__ parts, const uint64_t *__restr
         s.x[0] = X[0]; s.y[0] = Y[0]; s.w[0] = W[0];
         s.x[1] = X[o1]; s.y[1] = Y[o1]; s.w[1] = W[o1];
         s.x[2] = X[o2]; s.y[2] = Y[o2]; s.w[2] = W[o2];
-        s.ord = a2 == 0 ? 0xffffffffu : (uint32_t)(0 | (o1 << 2) | (o2 << 4));
+        s.ord = a2 == 0 ? 0xffffffffu : (uint32_t)(0 | (o1 << 2) | (o2 << 4) | ((uint32_t)p << 8));
         s.area2 = a2;
+        s.rcp = a2 == 0 ? 0ull : ~0ull / (uint64_t)a2;
         out[(uint64_t)dir * T + tg] = s;
     }
 }
@@ -301,35 +318,70 @@ __device__ __forceinline__ void pixel_span(int32_t lo, int32_t hi, int res, int3
     if (p1 > res - 1) p1 = res - 1;
 }
 
-// One warp per (direction, triangle); lanes stride over the pixels of its screen bbox.
-__global__ void __launch_bounds__(256) k_raster(const SPart *__restrict__ parts, const uint64_t *__restrict__ tofs,
-                                                int nparts, uint64_t T, const TriSetup *__restrict__ setup,
+// Depth pass of one (direction, triangle) over pixels [px0, px1] x [py0, py1], by `lanes`
+// threads starting at pixel offset `first`.
+__device__ __forceinline__ void raster_pixels(const TriSetup &s, int32_t px0, int32_t px1, int32_t py0, int32_t py1,
+                                              uint32_t first, uint32_t lanes, int res, uint32_t t,
+                                              unsigned long long *__restrict__ dbuf) {
+    const uint32_t wdt = (uint32_t)(px1 - px0 + 1);
+    const uint32_t npx = wdt * (uint32_t)(py1 - py0 + 1);
+    for (uint32_t pp = first; pp < npx; pp += lanes) {
+        const int32_t py = py0 + (int32_t)(pp / wdt), px = px0 + (int32_t)(pp % wdt);
+        int64_t lam[3];
+        if (!cover(s, px, py, lam)) continue;
+        const uint64_t num = (uint64_t)lam[0] * s.w[0] + (uint64_t)lam[1] * s.w[1] + (uint64_t)lam[2] * s.w[2];
+        const uint64_t z = div_area(num, (uint64_t)s.area2, s.rcp);
+        atomicMin(dbuf + (uint64_t)py * res + px, (unsigned long long)((z << 32) | t));
+    }
+}
+
+// A thread per (direction, triangle): triangles whose screen bbox holds at most
+// RASTER_SMALL pixels are rasterised by their own thread; larger ones by the whole warp,
+// one after another.
+constexpr uint32_t RASTER_SMALL = 16;
+
+__global__ void __launch_bounds__(256) k_raster(const SPart *__restrict__ parts, uint64_t T,
+                                                const TriSetup *__restrict__ setup,
                                                 unsigned long long *__restrict__ depth) {
     const int dir = blockIdx.y;
     const int lane = threadIdx.x & 31;
-    const uint64_t warps_per_grid = (uint64_t)gridDim.x * (blockDim.x >> 5);
-    for (uint64_t tg = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); tg < T; tg += warps_per_grid) {
-        const TriSetup s = setup[(uint64_t)dir * T + tg];
-        if (s.ord == 0xffffffffu) continue;
-        const int p = find_part(tofs, nparts, tg);
-        const int res = parts[p].res;
-        const uint32_t t = (uint32_t)(tg - parts[p].tofs);
-        unsigned long long *dbuf = depth + parts[p].pofs + (uint64_t)dir * res * res;
-        const int32_t xmin = min(s.x[0], min(s.x[1], s.x[2])), xmax = max(s.x[0], max(s.x[1], s.x[2]));
-        const int32_t ymin = min(s.y[0], min(s.y[1], s.y[2])), ymax = max(s.y[0], max(s.y[1], s.y[2]));
-        int32_t px0, px1, py0, py1;
-        pixel_span(xmin, xmax, res, px0, px1);
-        pixel_span(ymin, ymax, res, py0, py1);
-        if (px1 < px0 || py1 < py0) continue;
-        const uint32_t wdt = (uint32_t)(px1 - px0 + 1);
-        const uint32_t npx = wdt * (uint32_t)(py1 - py0 + 1);
-        for (uint32_t pp = lane; pp < npx; pp += 32) {
-            const int32_t py = py0 + (int32_t)(pp / wdt), px = px0 + (int32_t)(pp % wdt);
-            int64_t lam[3];
-            if (!cover(s, px, py, lam)) continue;
-            const uint64_t num = (uint64_t)lam[0] * s.w[0] + (uint64_t)lam[1] * s.w[1] + (uint64_t)lam[2] * s.w[2];
-            const uint64_t z = num / (uint64_t)s.area2;
-            atomicMin(dbuf + (uint64_t)py * res + px, (unsigned long long)((z << 32) | t));
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < T; base += stride) {
+        const uint64_t tg = base + lane;
+        TriSetup s;
+        bool valid = false;
+        int32_t px0 = 0, px1 = -1, py0 = 0, py1 = -1;
+        int res = 0;
+        uint32_t t = 0;
+        unsigned long long *dbuf = nullptr;
+        if (tg < T) {
+            s = setup[(uint64_t)dir * T + tg];
+            if (s.ord != 0xffffffffu) {
+                const SPart &P = parts[setup_part(s)];
+                res = P.res;
+                t = (uint32_t)(tg - P.tofs);
+                dbuf = depth + P.pofs + (uint64_t)dir * res * res;
+                const int32_t xmin = min(s.x[0], min(s.x[1], s.x[2])), xmax = max(s.x[0], max(s.x[1], s.x[2]));
+                const int32_t ymin = min(s.y[0], min(s.y[1], s.y[2])), ymax = max(s.y[0], max(s.y[1], s.y[2]));
+                pixel_span(xmin, xmax, res, px0, px1);
+                pixel_span(ymin, ymax, res, py0, py1);
+                valid = px1 >= px0 && py1 >= py0;
+            }
+        }
+        const uint32_t npx = valid ? (uint32_t)(px1 - px0 + 1) * (uint32_t)(py1 - py0 + 1) : 0u;
+        if (valid && npx <= RASTER_SMALL) raster_pixels(s, px0, px1, py0, py1, 0u, 1u, res, t, dbuf);
+        uint32_t big = __ballot_sync(0xffffffffu, npx > RASTER_SMALL);
+        while (big) {
+            const int j = __ffs(big) - 1;
+            big &= big - 1;
+            // the whole warp on lane j's triangle (its record reloaded: one broadcast load)
+            const TriSetup sj = setup[(uint64_t)dir * T + base + j];
+            const int32_t bx0 = __shfl_sync(0xffffffffu, px0, j), bx1 = __shfl_sync(0xffffffffu, px1, j);
+            const int32_t by0 = __shfl_sync(0xffffffffu, py0, j), by1 = __shfl_sync(0xffffffffu, py1, j);
+            const int rj = __shfl_sync(0xffffffffu, res, j);
+            const uint32_t tj = __shfl_sync(0xffffffffu, t, j);
+            unsigned long long *dj = (unsigned long long *)__shfl_sync(0xffffffffu, (unsigned long long)dbuf, j);
+            raster_pixels(sj, bx0, bx1, by0, by1, (uint32_t)lane, 32u, rj, tj, dj);
         }
     }
 }
@@ -496,7 +548,7 @@ __device__ void resolve_pixel(const View &V, const TriSetup &s, const int32_t *_
         const uint64_t num = (uint64_t)lam[0] * (uint64_t)q[3ull * slot[0] + a] +
                              (uint64_t)lam[1] * (uint64_t)q[3ull * slot[1] + a] +
                              (uint64_t)lam[2] * (uint64_t)q[3ull * slot[2] + a];
-        pos[a] = num / (uint64_t)s.area2;
+        pos[a] = div_area(num, (uint64_t)s.area2, s.rcp);
     }
     key = pack_pos(pos[0], pos[1], pos[2]);
     int64_t e1[3], e2[3];
@@ -544,6 +596,9 @@ __global__ void __launch_bounds__(256) k_resolve(const unsigned long long *__res
     __syncthreads();
     uint32_t out = blockofs[blockIdx.x];
     for (int w = 0; w < warp; ++w) out += wc[w];
+    // the part of the lane's pixels, searched again only when they leave its range
+    int p = -1;
+    uint64_t p_lo = 1, p_hi = 0;
     for (int r = 0; r < TILE_ROUNDS; ++r) {
         const uint64_t i = base + (uint64_t)r * 32 + lane;
         const unsigned long long dv = i < npix ? depth[i] : ~0ull;
@@ -551,7 +606,11 @@ __global__ void __launch_bounds__(256) k_resolve(const unsigned long long *__res
         const uint32_t m = __ballot_sync(0xffffffffu, hit);
         if (hit) {
             const uint32_t o = out + __popc(m & ((1u << lane) - 1u));
-            const int p = find_part(pofs, nparts, i);
+            if (i < p_lo || i >= p_hi) {
+                p = find_part(pofs, nparts, i);
+                p_lo = pofs[p];
+                p_hi = p + 1 < nparts ? pofs[p + 1] : npix;
+            }
             const SPart &P = parts[p];
             const uint64_t res2 = (uint64_t)P.res * P.res;
             const uint64_t local = i - P.pofs;
@@ -871,8 +930,8 @@ bs_status sample_visible_parts(const bs_mesh *meshes, const int *res, int nparts
         if (T > 0) {
             dim3 gs((unsigned)std::min<uint64_t>((T + 255) / 256, (uint64_t)sms * 32), ndirs);
             k_setup<<<gs, 256, 0, stream>>>(d_parts, d_tofs, nparts, T, q, d_st, views, setup);
-            dim3 gr((unsigned)std::min<uint64_t>((T + 7) / 8, (uint64_t)sms * 64), ndirs);
-            k_raster<<<gr, 256, 0, stream>>>(d_parts, d_tofs, nparts, T, setup, depth);
+            dim3 gr((unsigned)std::min<uint64_t>((T + 255) / 256, (uint64_t)sms * 16), ndirs);
+            k_raster<<<gr, 256, 0, stream>>>(d_parts, T, setup, depth);
         }
         k_cover_count<<<ptiles, 256, 0, stream>>>(depth, NP, bc);
         scan_excl(bc, ptiles, tot, stmp, stream);

@@ -6,7 +6,8 @@ scene seed (bs_scene_generate) when its wave runs, so the scene's triangles are 
 all resident.  A node is sampled from the six axis directions at a resolution set by
 its level and ordered exactly, keeping the first min(200k, triangles / 2) surfels -- the
 per-object bound of the paper's evaluation (Sec. 5).  Waves of nodes go through
-bs_sample_visible_batched and bs_order_batched.
+bs_sample_visible_batched and bs_order_batched on two alternating streams, so one wave's
+ordering overlaps the next wave's generation and sampling.
 """
 from __future__ import annotations
 
@@ -116,7 +117,12 @@ def run(seed: int = 0, lines: int = 20, per_line: int = 2500, group: int = 50, n
     by_level = {0: [], 1: [], 2: []}
     for i, nd in enumerate(nodes):
         by_level[nd.level].append(i)
-    # leaves in waves of single parts, groups in waves of nodes, one line at a time
+    # leaves in waves of single parts, groups in waves of nodes, one line at a time.  Waves
+    # alternate between two streams: a wave's sampling call returns once its surfels exist
+    # and its ordering then runs on the GPU while the next wave is generated and sampled.
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for st in streams:
+        st.wait_stream(torch.cuda.current_stream())
     for level, wsize in ((0, leaf_wave), (1, group_wave), (2, 1)):
         if level not in levels:
             continue
@@ -124,7 +130,8 @@ def run(seed: int = 0, lines: int = 20, per_line: int = 2500, group: int = 50, n
         ids = by_level[level]
         for w in range(0, len(ids), wsize):
             idx = ids[w:w + wsize]
-            wave(level, idx, [nodes[i].count for i in idx])
+            with torch.cuda.stream(streams[(w // wsize) % 2]):
+                wave(level, idx, [nodes[i].count for i in idx])
         torch.cuda.synchronize()
         if level in res.per_level:
             res.per_level[level]["seconds"] = time.perf_counter() - tl
