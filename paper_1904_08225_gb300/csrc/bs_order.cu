@@ -586,25 +586,32 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
             part_sync(bar, TP);
         }
         // (5) the greedy restricted to C, one warp, while the best stays above (tau, icut);
-        //     slot lane + 32u lives in lane's register u
+        //     slot lane + 32u lives in lane's register u.  The updates are branch-free (a
+        //     branch per register keeps the four updates from overlapping); pick t is
+        //     recorded in lane t & 31 and written out after the loop.
         if (warp == 0) {
             const uint32_t budget = min((uint32_t)MAXP, m - k);
+            const bool tiecut = icut != 0xffffffffu;
             uint32_t np = 0;
+            int32_t cx[CPL], cy[CPL], cz[CPL];
+#pragma unroll
+            for (int u = 0; u < CPL; ++u) {
+                const uint32_t sl = lane + 32 * u;
+                const uint64_t q = sl < ccnt ? Sm.ck[sl] : 0ull;
+                cx[u] = (int32_t)pos_x(q);
+                cy[u] = (int32_t)pos_y(q);
+                cz[u] = (int32_t)pos_z(q);
+            }
             if (D1 - tau < (int64_t)(1 << 25) - 1) {
                 // every candidate's D lies in [tau, D1] and stays there while it can be
                 // picked, so rp = D - tau + 1 < 2^25 (0 = out of the round) and a 32-bit
                 // key rp << 7 | (127 - slot) orders (D, lowest slot) in one reduction
                 uint32_t rp[CPL];
-                int32_t cx[CPL], cy[CPL], cz[CPL];
+                uint32_t rec[2] = {0u, 0u};  // slot << 25 | (D - tau)
 #pragma unroll
                 for (int u = 0; u < CPL; ++u) {
                     const uint32_t sl = lane + 32 * u;
-                    const bool lv = sl < ccnt;
-                    const uint64_t q = lv ? Sm.ck[sl] : 0ull;
-                    rp[u] = lv ? (uint32_t)(Sm.cd[sl] - tau) + 1u : 0u;
-                    cx[u] = (int32_t)pos_x(q);
-                    cy[u] = (int32_t)pos_y(q);
-                    cz[u] = (int32_t)pos_z(q);
+                    rp[u] = sl < ccnt ? (uint32_t)(Sm.cd[sl] - tau) + 1u : 0u;
                 }
                 while (np < budget) {
                     uint32_t kmax = 0;
@@ -614,66 +621,101 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
                     const uint32_t best = __reduce_max_sync(FULL, kmax);
                     if (best == 0) break;
                     const uint32_t slot = 127u - (best & 127u);
-                    const int64_t off = (int64_t)(best >> 7) - 1;
-                    const uint32_t idx = Sm.ci[slot];
-                    if (!(off > 0 || idx < icut)) break;
-                    const uint64_t qbest = Sm.ck[slot];
-                    if (lane == 0) {
-                        Sm.pk[np] = qbest;
-                        Sm.pi[np] = idx;
-                        Sm.pd[np] = tau + off;
-                    }
+                    const uint32_t off = (best >> 7) - 1u;
+                    if (off == 0 && tiecut && Sm.ci[slot] >= icut) break;  // a tied point past the cut
+                    const uint32_t r = (slot << 25) | off;
+                    rec[0] = (lane == (int)(np & 31) && np < 32) ? r : rec[0];
+                    rec[1] = (lane == (int)(np & 31) && np >= 32) ? r : rec[1];
                     ++np;
-                    const int32_t bx = (int32_t)pos_x(qbest), by = (int32_t)pos_y(qbest), bz = (int32_t)pos_z(qbest);
+                    const int su = (int)(slot >> 5), so = (int)(slot & 31);
+                    int32_t sx = cx[0], sy = cy[0], sz = cz[0];
+#pragma unroll
+                    for (int u = 1; u < CPL; ++u) {
+                        sx = su == u ? cx[u] : sx;
+                        sy = su == u ? cy[u] : sy;
+                        sz = su == u ? cz[u] : sz;
+                    }
+                    const int32_t bx = __shfl_sync(FULL, sx, so), by = __shfl_sync(FULL, sy, so),
+                                  bz = __shfl_sync(FULL, sz, so);
+                    int64_t t[CPL];
 #pragma unroll
                     for (int u = 0; u < CPL; ++u) {
-                        if (lane + 32 * u == slot) {
-                            rp[u] = 0u;
-                        } else if (rp[u]) {
-                            const int32_t dx = cx[u] - bx, dy = cy[u] - by, dz = cz[u] - bz;
-                            const int64_t t = (int64_t)dx * dx + (int64_t)dy * dy + (int64_t)dz * dz - tau;
-                            // below tau it cannot be picked in this round
-                            if (t < (int64_t)rp[u] - 1) rp[u] = t < 0 ? 0u : (uint32_t)t + 1u;
-                        }
+                        const int32_t dx = cx[u] - bx, dy = cy[u] - by, dz = cz[u] - bz;
+                        t[u] = (int64_t)dx * dx + (int64_t)dy * dy + (int64_t)dz * dz - tau;
+                    }
+#pragma unroll
+                    for (int u = 0; u < CPL; ++u) {
+                        // the new D = min(D, d); below tau it cannot be picked in this round
+                        const bool lower = t[u] < (int64_t)rp[u] - 1;
+                        const uint32_t nv = t[u] < 0 ? 0u : (uint32_t)t[u] + 1u;
+                        rp[u] = (lane + 32 * u == (int)slot) ? 0u : ((rp[u] != 0u && lower) ? nv : rp[u]);
+                    }
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t t = lane + 32 * h;
+                    if (t < np) {
+                        const uint32_t slot = rec[h] >> 25;
+                        Sm.pi[t] = Sm.ci[slot];
+                        Sm.pk[t] = Sm.ck[slot];
+                        Sm.pd[t] = tau + (int64_t)(rec[h] & ((1u << 25) - 1u));
                     }
                 }
             } else {
-                int64_t Dc[CPL];
-                uint64_t qc[CPL];
-                bool live[CPL];
+                int64_t Dc[CPL];  // -1 = out of the round
+                int64_t recD[2] = {0, 0};
+                uint32_t recS[2] = {0u, 0u};
 #pragma unroll
                 for (int u = 0; u < CPL; ++u) {
                     const uint32_t sl = lane + 32 * u;
-                    live[u] = sl < ccnt;
-                    Dc[u] = live[u] ? Sm.cd[sl] : 0;
-                    qc[u] = live[u] ? Sm.ck[sl] : 0ull;
+                    Dc[u] = sl < ccnt ? Sm.cd[sl] : -1;
                 }
                 while (np < budget) {
                     uint64_t kmax = 0;
 #pragma unroll
                     for (int u = 0; u < CPL; ++u)
-                        if (live[u]) kmax = max(kmax, ((uint64_t)(Dc[u] + 1) << 8) | (uint64_t)(255 - (lane + 32 * u)));
+                        kmax = max(kmax, Dc[u] >= 0 ? ((uint64_t)(Dc[u] + 1) << 8) | (uint64_t)(255 - (lane + 32 * u))
+                                                    : (uint64_t)0);
                     const uint64_t best = warp_max_u64(kmax);
                     if (best == 0) break;
                     const uint32_t slot = 255u - (uint32_t)(best & 255u);
                     const int64_t Dbest = (int64_t)(best >> 8) - 1;
-                    const uint32_t idx = Sm.ci[slot];
-                    if (!(Dbest > tau || (Dbest == tau && idx < icut))) break;
-                    const uint64_t qbest = Sm.ck[slot];
-                    if (lane == 0) {
-                        Sm.pk[np] = qbest;
-                        Sm.pi[np] = idx;
-                        Sm.pd[np] = Dbest;
-                    }
+                    if (Dbest == tau && tiecut && Sm.ci[slot] >= icut) break;  // a tied point past the cut
+                    const bool mine = lane == (int)(np & 31);
+                    recD[0] = (mine && np < 32) ? Dbest : recD[0];
+                    recS[0] = (mine && np < 32) ? slot : recS[0];
+                    recD[1] = (mine && np >= 32) ? Dbest : recD[1];
+                    recS[1] = (mine && np >= 32) ? slot : recS[1];
                     ++np;
+                    const int su = (int)(slot >> 5), so = (int)(slot & 31);
+                    int32_t sx = cx[0], sy = cy[0], sz = cz[0];
+#pragma unroll
+                    for (int u = 1; u < CPL; ++u) {
+                        sx = su == u ? cx[u] : sx;
+                        sy = su == u ? cy[u] : sy;
+                        sz = su == u ? cz[u] : sz;
+                    }
+                    const int32_t bx = __shfl_sync(FULL, sx, so), by = __shfl_sync(FULL, sy, so),
+                                  bz = __shfl_sync(FULL, sz, so);
+                    int64_t t[CPL];
 #pragma unroll
                     for (int u = 0; u < CPL; ++u) {
-                        if (lane + 32 * u == slot) {
-                            live[u] = false;
-                        } else if (live[u]) {
-                            Dc[u] = min(Dc[u], dist2(qc[u], qbest));
-                            live[u] = Dc[u] >= tau;  // below tau it cannot be picked in this round
-                        }
+                        const int32_t dx = cx[u] - bx, dy = cy[u] - by, dz = cz[u] - bz;
+                        t[u] = (int64_t)dx * dx + (int64_t)dy * dy + (int64_t)dz * dz;
+                    }
+#pragma unroll
+                    for (int u = 0; u < CPL; ++u) {
+                        const int64_t nd = min(Dc[u], t[u]);
+                        Dc[u] = (lane + 32 * u == (int)slot || Dc[u] < 0 || nd < tau) ? -1 : nd;
+                    }
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t t = lane + 32 * h;
+                    if (t < np) {
+                        Sm.pi[t] = Sm.ci[recS[h]];
+                        Sm.pk[t] = Sm.ck[recS[h]];
+                        Sm.pd[t] = recD[h];
                     }
                 }
             }
