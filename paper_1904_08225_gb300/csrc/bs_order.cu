@@ -238,6 +238,7 @@ struct RoundsSm {
     uint64_t pk[MAXP];
     int64_t pd[MAXP];
     uint32_t pi[MAXP];
+    int32_t px[MAXP], py[MAXP], pz[MAXP];  // the picks' coordinates, unpacked
     uint32_t sc[SMAX];   // variant 1: the round's sample (index), sorted by index
     int64_t sd[SMAX];    //            its distance to the chosen set
     uint64_t sk[SMAX];   //            its position
@@ -264,15 +265,35 @@ __device__ __forceinline__ void part_sync(int bar, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthreads) : "memory");
 }
 
-__device__ __forceinline__ uint64_t pick_mask(uint32_t np, const uint32_t *pi, const uint64_t *pk, uint64_t allow,
-                                              uint32_t own_shift, uint32_t own, uint64_t lo, uint64_t hi, int64_t maxD) {
-    // bit t set if pick t may lower a D inside the box [lo, hi] (whose largest D is maxD)
-    // or lies inside the index range `own` at granularity own_shift
+// A box with its corners unpacked.
+struct Box {
+    int32_t lx, ly, lz, hx, hy, hz;
+};
+__device__ __forceinline__ Box unpack_box(uint64_t lo, uint64_t hi) {
+    return Box{(int32_t)pos_x(lo), (int32_t)pos_y(lo), (int32_t)pos_z(lo),
+               (int32_t)pos_x(hi), (int32_t)pos_y(hi), (int32_t)pos_z(hi)};
+}
+// squared distance from (x, y, z) to the box, 0 inside (the same value as box_dist2)
+__device__ __forceinline__ int64_t box_dist2_xyz(const Box &b, int32_t x, int32_t y, int32_t z) {
+    const int32_t dx = max(max(b.lx - x, x - b.hx), 0);
+    const int32_t dy = max(max(b.ly - y, y - b.hy), 0);
+    const int32_t dz = max(max(b.lz - z, z - b.hz), 0);
+    return (int64_t)dx * dx + (int64_t)dy * dy + (int64_t)dz * dz;
+}
+
+// bit t set if pick t may lower a D inside the box (whose largest D is maxD) or lies
+// inside the index range `own` at granularity own_shift; px/py/pz the picks' coordinates
+__device__ __forceinline__ uint64_t pick_mask(uint32_t np, const uint32_t *pi, const int32_t *px, const int32_t *py,
+                                              const int32_t *pz, uint64_t allow, uint32_t own_shift, uint32_t own,
+                                              uint64_t lo, uint64_t hi, int64_t maxD) {
     const int lane = threadIdx.x & 31;
+    const Box b = unpack_box(lo, hi);
     bool ra = false, rb = false;
     const uint32_t ta = lane, tb = lane + 32;
-    if (ta < np && ((allow >> ta) & 1ull)) ra = (pi[ta] >> own_shift) == own || box_dist2(lo, hi, pk[ta]) < maxD;
-    if (tb < np && ((allow >> tb) & 1ull)) rb = (pi[tb] >> own_shift) == own || box_dist2(lo, hi, pk[tb]) < maxD;
+    if (ta < np && ((allow >> ta) & 1ull))
+        ra = (pi[ta] >> own_shift) == own || box_dist2_xyz(b, px[ta], py[ta], pz[ta]) < maxD;
+    if (tb < np && ((allow >> tb) & 1ull))
+        rb = (pi[tb] >> own_shift) == own || box_dist2_xyz(b, px[tb], py[tb], pz[tb]) < maxD;
     return (uint64_t)__ballot_sync(0xffffffffu, ra) | ((uint64_t)__ballot_sync(0xffffffffu, rb) << 32);
 }
 
@@ -730,12 +751,16 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
             Dg[Sm.pi[t]] = -1;
             P.perm[k + t] = Sm.pi[t];
             P.rad2[k + t] = Sm.pd[t];
+            const uint64_t q = Sm.pk[t];
+            Sm.px[t] = (int32_t)pos_x(q);
+            Sm.py[t] = (int32_t)pos_y(q);
+            Sm.pz[t] = (int32_t)pos_z(q);
         }
         if (tid == 0) { Sm.sgcnt = 0; Sm.gcnt = 0; }
         part_sync(bar, TP);
         const uint64_t all = np >= 64 ? ~0ull : ((1ull << np) - 1ull);
         for (uint32_t sg = warp; sg < ns; sg += NW) {
-            const uint64_t mk = pick_mask(np, Sm.pi, Sm.pk, all, 15, sg, Sm.sglo[sg], Sm.sghi[sg],
+            const uint64_t mk = pick_mask(np, Sm.pi, Sm.px, Sm.py, Sm.pz, all, 15, sg, Sm.sglo[sg], Sm.sghi[sg],
                                           (int64_t)(Sm.sgkey[sg] >> 15) - 1);
             if (mk && lane == 0) {
                 Sm.sgmask[sg] = mk;
@@ -754,13 +779,13 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
                 const uint32_t g = sg * 32 + lane;
                 if (g < ng) {
                     const int64_t gD = (int64_t)(s_gkey[g] >> 10) - 1;
-                    const uint64_t lo = s_glo[g], hi = s_ghi[g];
+                    const Box gb = unpack_box(s_glo[g], s_ghi[g]);
                     uint64_t mm = sgm;
                     bool rel = false;
-                    while (mm && !rel) {
+                    while (mm) {  // the same (at most four) picks on every lane: no divergence
                         const int t = __ffsll((long long)mm) - 1;
                         mm &= mm - 1;
-                        rel = (Sm.pi[t] >> 10) == g || box_dist2(lo, hi, Sm.pk[t]) < gD;
+                        rel |= (Sm.pi[t] >> 10) == g || box_dist2_xyz(gb, Sm.px[t], Sm.py[t], Sm.pz[t]) < gD;
                     }
                     if (rel) s_glist[atomicAdd(&Sm.gcnt, 1u)] = g;
                 }
@@ -776,7 +801,7 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
                 const uint32_t sg = Sm.heavy[it >> 5];
                 const uint32_t g = sg * 32 + (it & 31);
                 if (g >= ng) continue;
-                const uint64_t gm = pick_mask(np, Sm.pi, Sm.pk, Sm.sgmask[sg], 10, g, s_glo[g], s_ghi[g],
+                const uint64_t gm = pick_mask(np, Sm.pi, Sm.px, Sm.py, Sm.pz, Sm.sgmask[sg], 10, g, s_glo[g], s_ghi[g],
                                               (int64_t)(s_gkey[g] >> 10) - 1);
                 if (gm && lane == 0) s_glist[atomicAdd(&Sm.gcnt, 1u)] = g;
             }
@@ -785,21 +810,22 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
         const uint32_t ngl = Sm.gcnt;
         for (uint32_t li = warp; li < ngl; li += NW) {
             const uint32_t g = s_glist[li];
-            const uint64_t gm = pick_mask(np, Sm.pi, Sm.pk, Sm.sgmask[g >> 5], 10, g, s_glo[g], s_ghi[g],
+            const uint64_t gm = pick_mask(np, Sm.pi, Sm.px, Sm.py, Sm.pz, Sm.sgmask[g >> 5], 10, g, s_glo[g], s_ghi[g],
                                           (int64_t)(s_gkey[g] >> 10) - 1);
             const uint32_t b = g * 32 + lane;
             const bool vb = b < nb;
             uint64_t bk = vb ? bkey[b] : 0ull;
-            const uint64_t blo = vb ? blo_p[b] : 0ull, bhi = vb ? bhi_p[b] : 0ull;
-            const int64_t bD = (int64_t)(bk >> 5) - 1;
-            // picks that may lower a D in this lane's bucket
+            const Box bb = unpack_box(vb ? blo_p[b] : 0ull, vb ? bhi_p[b] : 0ull);
+            const int64_t bD = (int64_t)(bk >> 5) - 1;  // -1 past the end: no pick qualifies
+            // picks that may lower a D in this lane's bucket (gm is the same on every lane)
             uint64_t bm = 0;
-            if (vb) {
+            {
                 uint64_t mm = gm;
                 while (mm) {
                     const int t = __ffsll((long long)mm) - 1;
                     mm &= mm - 1;
-                    if ((Sm.pi[t] >> 5) == b || box_dist2(blo, bhi, Sm.pk[t]) < bD) bm |= 1ull << t;
+                    const bool r = (Sm.pi[t] >> 5) == b || box_dist2_xyz(bb, Sm.px[t], Sm.py[t], Sm.pz[t]) < bD;
+                    bm |= r ? 1ull << t : 0ull;
                 }
             }
             uint32_t amask = __ballot_sync(FULL, bm != 0);
@@ -827,15 +853,18 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
                     const uint32_t i = (g * 32 + bbs[u]) * 32 + lane;
                     const uint64_t mu = __shfl_sync(FULL, bm, (int)bbs[u]);
                     int64_t dd = d[u];
-                    if (dd > 0) {
+                    {
+                        // every lane walks the bucket's picks (mu is the same on every lane)
+                        const int32_t x = (int32_t)pos_x(ki[u]), y = (int32_t)pos_y(ki[u]), z = (int32_t)pos_z(ki[u]);
                         int64_t nd = dd;
                         uint64_t mm = mu;
                         while (mm) {
                             const int t = __ffsll((long long)mm) - 1;
                             mm &= mm - 1;
-                            nd = min(nd, dist2(ki[u], Sm.pk[t]));
+                            const int32_t dx = x - Sm.px[t], dy = y - Sm.py[t], dz = z - Sm.pz[t];
+                            nd = min(nd, (int64_t)dx * dx + (int64_t)dy * dy + (int64_t)dz * dz);
                         }
-                        if (nd < dd) {
+                        if (dd > 0 && nd < dd) {  // chosen points (-1) and duplicates (0) stay
                             dd = nd;
                             Dg[i] = nd;
                         }
