@@ -210,7 +210,9 @@ __global__ void __launch_bounds__(T) k_order_loop(const PartDesc *__restrict__ p
 // (32 groups, 32768 points) prunes the apply sweep of large parts.
 //   sgkey = (D+1) << 15 | (32767 - i_in_supergroup);   top = (D+1) << 8 | (255 - sg)
 // ---------------------------------------------------------------------------
-constexpr int CAP = 128;     // candidates per round (four per lane of the simulating warp)
+constexpr int CAP_BITS = 7;
+constexpr int CAP = 1 << CAP_BITS;  // candidates per round (CAP / 32 per lane of the simulating warp)
+constexpr int OFF_BITS = 32 - CAP_BITS;  // 32-bit simulation keys: (D - tau + 1) << CAP_BITS | slot
 constexpr int CPL = CAP / 32;
 constexpr int MAXP = 64;     // picks per round (pick sets are 64-bit masks)
 constexpr int MAX_SG = 192;  // super-groups: BS_MAX_POINTS / 32768
@@ -623,12 +625,13 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
                 cy[u] = (int32_t)pos_y(q);
                 cz[u] = (int32_t)pos_z(q);
             }
-            if (D1 - tau < (int64_t)(1 << 25) - 1) {
+            if (D1 - tau < (int64_t)(1u << OFF_BITS) - 1) {
                 // every candidate's D lies in [tau, D1] and stays there while it can be
-                // picked, so rp = D - tau + 1 < 2^25 (0 = out of the round) and a 32-bit
-                // key rp << 7 | (127 - slot) orders (D, lowest slot) in one reduction
+                // picked, so rp = D - tau + 1 < 2^OFF_BITS (0 = out of the round) and a
+                // 32-bit key rp << CAP_BITS | (CAP - 1 - slot) orders (D, lowest slot) in one
+                // reduction
                 uint32_t rp[CPL];
-                uint32_t rec[2] = {0u, 0u};  // slot << 25 | (D - tau)
+                uint32_t rec[2] = {0u, 0u};  // slot << OFF_BITS | (D - tau)
 #pragma unroll
                 for (int u = 0; u < CPL; ++u) {
                     const uint32_t sl = lane + 32 * u;
@@ -638,13 +641,13 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
                     uint32_t kmax = 0;
 #pragma unroll
                     for (int u = 0; u < CPL; ++u)
-                        kmax = max(kmax, rp[u] ? (rp[u] << 7) | (uint32_t)(127 - (lane + 32 * u)) : 0u);
+                        kmax = max(kmax, rp[u] ? (rp[u] << CAP_BITS) | (uint32_t)(CAP - 1 - (lane + 32 * u)) : 0u);
                     const uint32_t best = __reduce_max_sync(FULL, kmax);
                     if (best == 0) break;
-                    const uint32_t slot = 127u - (best & 127u);
-                    const uint32_t off = (best >> 7) - 1u;
+                    const uint32_t slot = (uint32_t)(CAP - 1) - (best & (uint32_t)(CAP - 1));
+                    const uint32_t off = (best >> CAP_BITS) - 1u;
                     if (off == 0 && tiecut && Sm.ci[slot] >= icut) break;  // a tied point past the cut
-                    const uint32_t r = (slot << 25) | off;
+                    const uint32_t r = (slot << OFF_BITS) | off;
                     rec[0] = (lane == (int)(np & 31) && np < 32) ? r : rec[0];
                     rec[1] = (lane == (int)(np & 31) && np >= 32) ? r : rec[1];
                     ++np;
@@ -676,10 +679,10 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
                 for (int h = 0; h < 2; ++h) {
                     const uint32_t t = lane + 32 * h;
                     if (t < np) {
-                        const uint32_t slot = rec[h] >> 25;
+                        const uint32_t slot = rec[h] >> OFF_BITS;
                         Sm.pi[t] = Sm.ci[slot];
                         Sm.pk[t] = Sm.ck[slot];
-                        Sm.pd[t] = tau + (int64_t)(rec[h] & ((1u << 25) - 1u));
+                        Sm.pd[t] = tau + (int64_t)(rec[h] & ((1u << OFF_BITS) - 1u));
                     }
                 }
             } else {
