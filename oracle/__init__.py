@@ -69,6 +69,9 @@ def _load():
             lib.or_prefix_for_radius.argtypes = [P, C.c_uint64, C.c_int64]
             lib.or_prefix_for_radius.restype = C.c_uint64
             lib.or_num_threads.restype = C.c_int
+            lib.or_sample_splats.argtypes = [C.c_uint64, P, P, P, C.c_int, P, P, P, P, P, C.c_double, P, C.c_int,
+                                             C.c_int, P, P, P, P, C.c_uint64]
+            lib.or_sample_splats.restype = C.c_int64
             _lib = lib
     return _lib
 
@@ -155,6 +158,46 @@ def sample_mesh(mesh, dirs, res: int):
     """Quantise then sample a workloads.Mesh: returns (surfels dict, bbox_min, scale)."""
     q, mn, s = quantise(mesh.xyz)
     return sample_visible(q, mesh.tri, mesh.rgb, dirs, res), mn, s
+
+
+def sample_splats(sets, frame_min, frame_scale: float, dirs, res: int):
+    """Parent-node sampling from child surfels drawn as oriented discs (Sec. 3.4, Sec. 4.2).
+
+    sets: list of dicts with key u64 (n,) in the set's own frame, nrm int16 (n,3),
+    rgb uint8 (n,3) or None, bbox_min (3,) float32, scale (float) and r2 (int, squared disc
+    radius in the set's units).  The parent frame is (frame_min float32 (3,), frame_scale).
+    dirs: axis directions.  Returns dict(key, nrm, rgb, src) like sample_visible().
+    """
+    lib = _load()
+    keys = [np.ascontiguousarray(st["key"], dtype=np.uint64) for st in sets]
+    n = [len(k) for k in keys]
+    ofs = np.concatenate([[0], np.cumsum(n)]).astype(np.uint64)
+    skey = np.ascontiguousarray(np.concatenate(keys) if keys else np.zeros(0, np.uint64), dtype=np.uint64)
+    snrm = np.ascontiguousarray(np.concatenate([np.asarray(st["nrm"], np.int16).reshape(-1, 3) for st in sets])
+                                if sets else np.zeros((0, 3), np.int16), dtype=np.int16)
+    have_rgb = any(st.get("rgb") is not None for st in sets)
+    srgb = None
+    if have_rgb:
+        srgb = np.ascontiguousarray(np.concatenate([
+            np.asarray(st["rgb"], np.uint8).reshape(-1, 3) if st.get("rgb") is not None
+            else np.zeros((len(k), 3), np.uint8) for st, k in zip(sets, keys)]), dtype=np.uint8)
+    bmin = np.ascontiguousarray(np.array([st["bbox_min"] for st in sets], np.float32).reshape(-1))
+    scale = np.ascontiguousarray([float(st["scale"]) for st in sets], dtype=np.float64)
+    r2 = np.ascontiguousarray([int(st["r2"]) for st in sets], dtype=np.int64)
+    fmin = np.ascontiguousarray(frame_min, dtype=np.float32)
+    dd = np.ascontiguousarray(dirs, dtype=np.int8).reshape(-1, 3)
+    args = (len(skey), _p(skey), _p(snrm), None if srgb is None else _p(srgb), len(sets), _p(ofs), _p(bmin),
+            _p(scale), _p(r2), _p(fmin), float(frame_scale), _p(dd), dd.shape[0], res)
+    cnt = lib.or_sample_splats(*args, None, None, None, None, 0)
+    if cnt < 0:
+        raise ValueError(f"or_sample_splats failed ({cnt})")
+    key = np.zeros(cnt, np.uint64)
+    nrm = np.zeros((cnt, 3), np.int16)
+    col = np.zeros((cnt, 3), np.uint8)
+    src = np.zeros(cnt, np.uint32)
+    c2 = lib.or_sample_splats(*args, _p(key), _p(nrm), _p(col), _p(src), cnt)
+    assert c2 == cnt
+    return dict(key=key, nrm=nrm, rgb=col, src=src)
 
 
 def start_index(n: int, seed: int = 0, part_id: int = 0, start: int = -1) -> int:

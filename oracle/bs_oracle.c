@@ -406,6 +406,204 @@ int64_t or_sample_visible(const int32_t *q, uint64_t nverts, const uint32_t *tri
 }
 
 /* ------------------------------------------------------------------------ */
+/* Hierarchical generation from child surfels (Sec. 3.4: a parent node's      */
+/* initial set may be rendered from its children's surfel approximations     */
+/* instead of their triangles), with each surfel drawn as the oriented disc  */
+/* of Sec. 4.2 (position, normal, radius).  Readings:                        */
+/*  - a set of splats carries its own frame (bbox_min float32, scale double) */
+/*    and one squared disc radius r2 in its own quantised units;            */
+/*  - a splat centre moves to the parent frame by IEEE double operations in   */
+/*    this order: t = q / s_child; t = bmin_child + t; t = t - fmin;          */
+/*    t = t * s_parent; c = clamp(floor(t), 0, 2^21 - 1);                     */
+/*  - the radius likewise: r = sqrt(r2) / s_child * s_parent (double);        */
+/*    R2 = ceil(r * r), at most 3 (2^21 - 1)^2;                              */
+/*  - views are the six axis directions; a pixel centre's ray hits the disc  */
+/*    plane n.(p - c) = 0 (n = the splat's snorm16 normal turned toward the   */
+/*    camera, nw = n.d > 0; discs seen edge-on, nw = 0, are skipped) and the  */
+/*    pixel is covered when the hit point lies within R2 of c -- an exact    */
+/*    integer test in units of 1/(2 res) of a pixel-centre step;             */
+/*  - depth of the hit point = floor of the exact rational depth; the        */
+/*    smallest (depth << 32 | global splat index) wins a pixel;              */
+/*  - the emitted surfel is the hit point (floor per axis), the splat's       */
+/*    turned normal and colour; emission index, duplicate merge and Morton   */
+/*    order as for triangles.                                                 */
+/* ------------------------------------------------------------------------ */
+static int64_t floor_div(int64_t a, int64_t b) /* b > 0 */
+{
+    int64_t q = a / b;
+    if ((a % b) != 0 && a < 0) q--;
+    return q;
+}
+
+typedef struct {
+    int64_t c[3];  /* centre in the parent frame */
+    int64_t R2;    /* squared radius in parent units */
+} or_splat;
+
+static void splat_to_parent(uint64_t key, const float bmin[3], double s_child, int64_t r2, const float fmin[3],
+                            double s_parent, or_splat *o)
+{
+    int64_t q[3];
+    unpack_key(key, q);
+    for (int a = 0; a < 3; a++) {
+        double t = (double)q[a] / s_child;
+        t = (double)bmin[a] + t;
+        t = t - (double)fmin[a];
+        t = t * s_parent;
+        double f = floor(t);
+        int64_t v = f < 0.0 ? 0 : (f > (double)OR_Q ? OR_Q : (int64_t)f);
+        o->c[a] = v;
+    }
+    const double rmax2 = 3.0 * (double)OR_Q * (double)OR_Q;
+    double r = sqrt((double)r2) / s_child;
+    r = r * s_parent;
+    double rr = r * r;
+    o->R2 = rr >= rmax2 ? (int64_t)rmax2 : (int64_t)ceil(rr);
+}
+
+/* Pixels of one axis direction covered by one splat, with their depth keys. */
+static void splat_dir(const or_view *vw, const or_splat *sp, const int16_t n16[3], uint32_t g, uint64_t *depth)
+{
+    int64_t n[3] = {n16[0], n16[1], n16[2]};
+    int64_t nu = 0, nv = 0, nw = 0, cu = 0, cv = 0, cd = 0;
+    for (int a = 0; a < 3; a++) {
+        nu += vw->u[a] * n[a]; nv += vw->v[a] * n[a]; nw += vw->d[a] * n[a];
+        cu += vw->u[a] * sp->c[a]; cv += vw->v[a] * sp->c[a]; cd += vw->d[a] * sp->c[a];
+    }
+    if (nw == 0) return;
+    if (nw < 0) { nu = -nu; nv = -nv; nw = -nw; }
+    const int64_t res = vw->res, two_res = 2 * res;
+    const int64_t cu2 = (cu - vw->ulo) * two_res, cv2 = (cv - vw->vlo) * two_res;
+    const int64_t dc = -cd + vw->wbias;
+    /* a covered pixel has DU^2 <= R2 (2 res)^2 (and the same for DV), so only  */
+    /* the pixels with |DU|, |DV| <= 2 res Rb, Rb = ceil(sqrt(R2)), are tested  */
+    int64_t Rb = (int64_t)sqrt((double)sp->R2);
+    while (Rb * Rb < sp->R2) Rb++;
+    int64_t px0 = -floor_div(-(cu2 - two_res * Rb - vw->U1), 2 * vw->U1), px1 = floor_div(cu2 + two_res * Rb - vw->U1, 2 * vw->U1);
+    int64_t py0 = -floor_div(-(cv2 - two_res * Rb - vw->V1), 2 * vw->V1), py1 = floor_div(cv2 + two_res * Rb - vw->V1, 2 * vw->V1);
+    if (px0 < 0) px0 = 0;
+    if (py0 < 0) py0 = 0;
+    if (px1 > res - 1) px1 = res - 1;
+    if (py1 > res - 1) py1 = res - 1;
+    for (int64_t py = py0; py <= py1; py++) {
+        const int64_t DV = (2 * py + 1) * vw->V1 - cv2;
+        for (int64_t px = px0; px <= px1; px++) {
+            const int64_t DU = (2 * px + 1) * vw->U1 - cu2;
+            __int128 lhs = ((__int128)DU * DU + (__int128)DV * DV) * ((__int128)nw * nw);
+            const __int128 t = (__int128)nu * DU + (__int128)nv * DV;
+            lhs += t * t;
+            const __int128 rhs = (__int128)sp->R2 * ((__int128)two_res * two_res) * ((__int128)nw * nw);
+            if (lhs > rhs) continue;
+            int64_t z = floor_div(dc * nw * two_res + nu * DU + nv * DV, nw * two_res);
+            if (z < 0) z = 0;
+            if (z > 0xFFFFFFFFll) z = 0xFFFFFFFFll;
+            const uint64_t v = ((uint64_t)z << 32) | g;
+            uint64_t *dp = &depth[(uint64_t)py * res + px];
+            if (v < *dp) *dp = v;
+        }
+    }
+}
+
+/* The surfel of a pixel won by splat sp: the hit point, the turned normal. */
+static void splat_resolve(const or_view *vw, const or_splat *sp, const int16_t n16[3], const uint8_t *rgb3,
+                          int64_t px, int64_t py, or_row *r)
+{
+    int64_t n[3] = {n16[0], n16[1], n16[2]};
+    int64_t nu = 0, nv = 0, nw = 0, cu = 0, cv = 0;
+    for (int a = 0; a < 3; a++) {
+        nu += vw->u[a] * n[a]; nv += vw->v[a] * n[a]; nw += vw->d[a] * n[a];
+        cu += vw->u[a] * sp->c[a]; cv += vw->v[a] * sp->c[a];
+    }
+    const int flip = nw < 0;
+    if (flip) { nu = -nu; nv = -nv; nw = -nw; }
+    const int64_t two_res = 2 * vw->res;
+    const int64_t DU = (2 * px + 1) * vw->U1 - (cu - vw->ulo) * two_res;
+    const int64_t DV = (2 * py + 1) * vw->V1 - (cv - vw->vlo) * two_res;
+    /* hit point = c + u DU/(2res) + v DV/(2res) - d (nu DU + nv DV)/(nw 2res); */
+    /* u, v, d are signed unit axis vectors, so each axis gets one term         */
+    const int64_t W = nu * DU + nv * DV;
+    int64_t pos[3];
+    for (int a = 0; a < 3; a++) {
+        int64_t p = sp->c[a];
+        if (vw->u[a] != 0) p += floor_div(vw->u[a] * DU, two_res);
+        if (vw->v[a] != 0) p += floor_div(vw->v[a] * DV, two_res);
+        if (vw->d[a] != 0) p += floor_div(-vw->d[a] * W, nw * two_res);
+        pos[a] = p < 0 ? 0 : (p > OR_Q ? OR_Q : p);
+    }
+    for (int a = 0; a < 3; a++) {
+        r->nrm[a] = (int16_t)(flip ? -n16[a] : n16[a]);
+        r->rgb[a] = rgb3 ? rgb3[a] : 0;
+    }
+    r->key = pack_key(pos[0], pos[1], pos[2]);
+    r->morton = or_morton3((uint32_t)pos[0], (uint32_t)pos[1], (uint32_t)pos[2]);
+}
+
+/* Splat sampling of one parent node.  Splats are concatenated over nsets   */
+/* sets; set i holds splats [set_ofs[i], set_ofs[i+1]) with frame bmin[3i..],  */
+/* scale[i] and squared radius r2[i].  The parent frame is (fmin, fscale).    */
+/* dirs must be axis directions.  Returns N as or_sample_visible does, -1 on  */
+/* bad arguments, -2 when out of memory.                                     */
+int64_t or_sample_splats(uint64_t nsplat, const uint64_t *skey, const int16_t *snrm, const uint8_t *srgb, int nsets,
+                         const uint64_t *set_ofs, const float *bmin, const double *scale, const int64_t *r2,
+                         const float fmin[3], double fscale, const int8_t *dirs, int ndirs, int res,
+                         uint64_t *key, int16_t *nrm, uint8_t *rgb, uint32_t *src, uint64_t cap)
+{
+    if (res < 1 || res > 4096 || ndirs < 1 || nsets < 0 || nsplat >= 0xFFFFFFFFull) return -1;
+    if (set_ofs[0] != 0 || set_ofs[nsets] != nsplat) return -1;
+    for (int di = 0; di < ndirs; di++) {
+        const int8_t *d = dirs + 3 * di;
+        const int nz = (d[0] != 0) + (d[1] != 0) + (d[2] != 0);
+        if (nz != 1) return -1;
+    }
+    or_splat *sp = (or_splat *)malloc((nsplat ? nsplat : 1) * sizeof(or_splat));
+    const uint64_t npix = (uint64_t)res * res;
+    uint64_t *depth = (uint64_t *)malloc(npix * sizeof(uint64_t));
+    uint64_t rcap = 1024, nrow = 0;
+    or_row *rows = (or_row *)malloc(rcap * sizeof(or_row));
+    if (!sp || !depth || !rows) { free(sp); free(depth); free(rows); return -2; }
+    for (int i = 0; i < nsets; i++)
+        for (uint64_t g = set_ofs[i]; g < set_ofs[i + 1]; g++)
+            splat_to_parent(skey[g], bmin + 3 * i, scale[i], r2[i], fmin, fscale, &sp[g]);
+    for (int di = 0; di < ndirs; di++) {
+        or_view vw;
+        make_view(dirs + 3 * di, res, &vw);
+        for (uint64_t i = 0; i < npix; i++) depth[i] = ~(uint64_t)0;
+        for (uint64_t g = 0; g < nsplat; g++) splat_dir(&vw, &sp[g], snrm + 3 * g, (uint32_t)g, depth);
+        for (int64_t py = 0; py < res; py++)
+            for (int64_t px = 0; px < res; px++) {
+                const uint64_t v = depth[(uint64_t)py * res + px];
+                if (v == ~(uint64_t)0) continue;
+                if (nrow == rcap) {
+                    rcap *= 2;
+                    or_row *nr = (or_row *)realloc(rows, rcap * sizeof(or_row));
+                    if (!nr) { free(sp); free(depth); free(rows); return -2; }
+                    rows = nr;
+                }
+                or_row *r = &rows[nrow++];
+                memset(r, 0, sizeof(*r));
+                const uint32_t g = (uint32_t)(v & 0xFFFFFFFFu);
+                splat_resolve(&vw, &sp[g], snrm + 3 * (uint64_t)g, srgb ? srgb + 3 * (uint64_t)g : NULL, px, py, r);
+                r->e = (uint32_t)((uint64_t)di * npix + (uint64_t)py * res + (uint64_t)px);
+            }
+    }
+    free(sp);
+    free(depth);
+    qsort(rows, nrow, sizeof(or_row), row_cmp);
+    uint64_t n = 0;
+    for (uint64_t i = 0; i < nrow; i++) {
+        if (i > 0 && rows[i].morton == rows[i - 1].morton) continue;
+        if (n < cap) {
+            key[n] = rows[i].key;
+            for (int a = 0; a < 3; a++) { nrm[3 * n + a] = rows[i].nrm[a]; rgb[3 * n + a] = rows[i].rgb[a]; }
+            src[n] = rows[i].e;
+        }
+        n++;
+    }
+    free(rows);
+    return (int64_t)n;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Progressive ordering: the exact greedy permutation (farthest-first        */
 /* traversal) that Sec. 3.2 sets as the goal and Sec. 3.3 uses as the quality */
 /* reference.  perm[0] = s; for k >= 1, perm[k] is the unchosen point whose   */
