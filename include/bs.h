@@ -140,6 +140,50 @@ bs_status bs_sample_visible(const bs_mesh *mesh, const bs_dir *dirs, int ndirs, 
 bs_status bs_sample_visible_batched(const bs_mesh *meshes, const int *res, int nparts, const bs_dir *dirs,
                                     int ndirs, bs_surfels *out, void *cuda_stream);
 
+/* ---- Bottom-up generation from child surfels (Sec. 3.4), each surfel drawn as the
+ * oriented disc of Sec. 4.2. ---- */
+
+/* One child's surfels splatted into a parent node. */
+typedef struct {
+    const uint64_t *key;   /* DEVICE: positions in this set's own 21-bit frame (bs_surfels.key) */
+    const int16_t *nrm;    /* DEVICE: snorm16 normals, 3 per surfel */
+    const uint8_t *rgb;    /* DEVICE: RGB8, 3 per surfel, or NULL (black) */
+    const uint32_t *perm;  /* DEVICE or NULL: splat i is surfel perm[i] (a prefix of an ordering) */
+    uint64_t n;            /* splats used from this set */
+    float bbox_min[3];     /* the set's frame, as bs_sample_visible reported it */
+    double scale;
+    int64_t r2;            /* squared disc radius in the set's quantised units, >= 0 */
+    uint32_t node;         /* the parent node (index into nodes[]) it is drawn into */
+} bs_splat_set;
+
+/* A parent node: its quantisation frame, raster resolution and outputs. */
+typedef struct {
+    float frame_min[3];    /* the node's frame: q = floor((x - frame_min) * scale) */
+    double scale;          /* > 0 */
+    int32_t res;           /* 1..BS_MAX_RES */
+} bs_splat_node;
+
+/* bs_sample_splats -- the initial surfel set of parent nodes rendered from child surfels
+ * instead of triangles (Sec. 3.4 bottom-up), each surfel an oriented disc (Sec. 4.2).
+ * A splat's centre and radius move to its node's frame by IEEE double operations in a
+ * fixed order (t = q / s_set; t = bbox_min + t; t = t - frame_min; t = t * s_node;
+ * floor, clamped to [0, 2^21 - 1]; radius sqrt(r2) / s_set * s_node, R2 = ceil(r^2),
+ * at most 3 (2^21 - 1)^2).  For every direction (axis directions only) a pixel is
+ * covered by a disc when its centre's ray meets the disc's plane within the radius
+ * (exact integer test; discs seen edge-on are skipped); the nearest hit wins (ties to
+ * the lower global splat index, sets concatenated in order) and emits its hit point
+ * (floor), the disc normal turned toward the camera and its colour.  Emission index,
+ * merge of equal positions and Morton order are those of bs_sample_visible; src holds
+ * the emission index.
+ *  sets : HOST array of nsets descriptors (0 <= nsets); nodes : HOST array of nnodes
+ *  dirs : HOST array of ndirs axis directions; out : HOST array of nnodes caller-owned
+ *         device surfel arrays (out[i].bbox_min / scale are set to node i's frame)
+ * BS_EINVAL for a non-axis direction, a set naming a missing node, a bad resolution or
+ * scale, NULL arrays, or more than 2^32 - 1 splats; BS_EOVERFLOW as for
+ * bs_sample_visible_batched.  Synchronises the stream. */
+bs_status bs_sample_splats(const bs_splat_set *sets, int nsets, const bs_splat_node *nodes, int nnodes,
+                           const bs_dir *dirs, int ndirs, bs_surfels *out, void *cuda_stream);
+
 /* bs_order -- progressive ordering of one part (Sec. 3.2 goal; Sec. 4.1 radius).
  * Computes the exact greedy permutation (farthest-first traversal) of the
  * points s->key[0..n): perm[0] is the start index; perm[k] (k >= 1) is the

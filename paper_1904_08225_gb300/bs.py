@@ -24,7 +24,7 @@ INT64_MAX = (1 << 63) - 1
 # symbols include/bs.h declares; the library must export every one
 EXPORTS = ["bs_sample_visible", "bs_sample_visible_batched", "bs_order", "bs_order_noalloc", "bs_order_batched", "bs_server_create", "bs_server_submit",
            "bs_server_poll", "bs_server_times", "bs_server_destroy", "bs_set_tuning", "bs_last_launch_ms",
-           "bs_prefix_median_nn", "bs_prefix_for_radius", "bs_prefix_estimate", "bs_scene_generate",
+           "bs_prefix_median_nn", "bs_prefix_for_radius", "bs_prefix_estimate", "bs_scene_generate", "bs_sample_splats",
            "bs_last_error"]
 
 
@@ -46,6 +46,16 @@ class Dir(C.Structure):
 class Surfels(C.Structure):
     _fields_ = [("key", C.c_void_p), ("nrm", C.c_void_p), ("rgb", C.c_void_p), ("src", C.c_void_p),
                 ("n", C.c_uint64), ("cap", C.c_uint64), ("bbox_min", C.c_float * 3), ("scale", C.c_double)]
+
+
+class SplatSet(C.Structure):
+    _fields_ = [("key", C.c_void_p), ("nrm", C.c_void_p), ("rgb", C.c_void_p), ("perm", C.c_void_p),
+                ("n", C.c_uint64), ("bbox_min", C.c_float * 3), ("scale", C.c_double), ("r2", C.c_int64),
+                ("node", C.c_uint32)]
+
+
+class SplatNode(C.Structure):
+    _fields_ = [("frame_min", C.c_float * 3), ("scale", C.c_double), ("res", C.c_int32)]
 
 
 class OrderOpts(C.Structure):
@@ -74,6 +84,8 @@ def load(build_if_stale: bool = True) -> C.CDLL:
             lib.bs_sample_visible.argtypes = [C.POINTER(Mesh), C.POINTER(Dir), C.c_int, C.c_int, C.POINTER(Surfels), P]
             lib.bs_sample_visible_batched.argtypes = [C.POINTER(Mesh), C.POINTER(C.c_int), C.c_int, C.POINTER(Dir),
                                                       C.c_int, C.POINTER(Surfels), P]
+            lib.bs_sample_splats.argtypes = [C.POINTER(SplatSet), C.c_int, C.POINTER(SplatNode), C.c_int,
+                                             C.POINTER(Dir), C.c_int, C.POINTER(Surfels), P]
             lib.bs_order.argtypes = [C.POINTER(Surfels), C.POINTER(OrderOpts), P, P, P, P]
             lib.bs_order_noalloc.argtypes = [C.POINTER(Surfels), C.POINTER(OrderOpts), P, P, P, P]
             lib.bs_order_batched.argtypes = [C.POINTER(Surfels), C.c_int, C.POINTER(OrderOpts), P, P, P, P]
@@ -266,6 +278,53 @@ def sample_visible_batched(meshes, res, dirs, stream=None, caps=None):
         res_list.append(dict(key=key[o:o + n], nrm=nrm[o:o + n], rgb=col[o:o + n], src=src[o:o + n], n=n,
                              bbox_min=np.array(list(outs[i].bbox_min), np.float32), scale=float(outs[i].scale)))
     return res_list
+
+
+def sample_splats(sets, nodes, dirs, caps=None, stream=None):
+    """bs_sample_splats: parent nodes sampled from child surfels drawn as oriented discs.
+
+    sets: list of dicts with key (CUDA int64 (n,)), nrm (CUDA int16 (n,3)), rgb (CUDA uint8
+    (n,3) or None), perm (CUDA int32 view of u32 or None; splat i = surfel perm[i]), n,
+    bbox_min (3 floats), scale, r2 (squared disc radius in the set's units) and node.
+    nodes: list of (frame_min (3 floats), scale, res).  dirs: axis directions.
+    Returns one dict per node like sample_visible()."""
+    torch = _torch()
+    lib = load()
+    d = np.asarray(dirs, dtype=np.int8).reshape(-1, 3)
+    darr = (Dir * len(d))(*[Dir(int(a), int(b), int(c)) for a, b, c in d])
+    S = len(sets)
+    sarr = (SplatSet * max(S, 1))()
+    for i, st in enumerate(sets):
+        sarr[i] = SplatSet(st["key"].data_ptr(), st["nrm"].data_ptr(),
+                           st["rgb"].data_ptr() if st.get("rgb") is not None else None,
+                           st["perm"].data_ptr() if st.get("perm") is not None else None,
+                           int(st["n"]), (C.c_float * 3)(*[float(x) for x in st["bbox_min"]]), float(st["scale"]),
+                           int(st["r2"]), int(st["node"]))
+    K = len(nodes)
+    narr = (SplatNode * K)(*[SplatNode((C.c_float * 3)(*[float(x) for x in fm]), float(sc), int(r))
+                             for fm, sc, r in nodes])
+    capl = [int(caps[i]) if caps is not None else len(d) * int(nodes[i][2]) ** 2 for i in range(K)]
+    ofs = np.concatenate([[0], np.cumsum(capl)]).astype(np.int64)
+    dev = sets[0]["key"].device if sets else torch.device("cuda")
+    tot = int(ofs[-1])
+    key = torch.empty(tot, dtype=torch.int64, device=dev)
+    nrm = torch.empty((tot, 3), dtype=torch.int16, device=dev)
+    col = torch.empty((tot, 3), dtype=torch.uint8, device=dev)
+    src = torch.empty(tot, dtype=torch.int32, device=dev)
+    onp, oarr = _struct_array(Surfels, K)
+    onp["key"] = key.data_ptr() + 8 * ofs[:-1]
+    onp["nrm"] = nrm.data_ptr() + 6 * ofs[:-1]
+    onp["rgb"] = col.data_ptr() + 3 * ofs[:-1]
+    onp["src"] = src.data_ptr() + 4 * ofs[:-1]
+    onp["cap"] = capl
+    st_ = lib.bs_sample_splats(sarr, S, narr, K, darr, len(d), oarr, _stream(stream))
+    _check(st_, "bs_sample_splats")
+    out = []
+    for i in range(K):
+        o, n = int(ofs[i]), int(onp["n"][i])
+        out.append(dict(key=key[o:o + n], nrm=nrm[o:o + n], rgb=col[o:o + n], src=src[o:o + n], n=n,
+                        bbox_min=onp["bbox_min"][i].copy(), scale=float(onp["scale"][i])))
+    return out
 
 
 def _np_dtype(ct) -> np.dtype:

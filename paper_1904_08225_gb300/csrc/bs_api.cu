@@ -167,6 +167,12 @@ bs_status bs_scene_generate(uint64_t seed, const uint64_t *part_ids, const int32
                           local_indices, xyz, tri, rgb, (cudaStream_t)cuda_stream);
 }
 
+bs_status bs_sample_splats(const bs_splat_set *sets, int nsets, const bs_splat_node *nodes, int nnodes,
+                           const bs_dir *dirs, int ndirs, bs_surfels *out, void *cuda_stream) {
+    clear_error();
+    return sample_splats(sets, nsets, nodes, nnodes, dirs, ndirs, out, (cudaStream_t)cuda_stream);
+}
+
 double bs_prefix_estimate(uint64_t pm, int64_t rm2, int64_t r2) {
     if (r2 <= 0) return (double)INFINITY;
     return (double)pm * (double)rm2 / (double)r2;

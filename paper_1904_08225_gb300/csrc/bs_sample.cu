@@ -17,6 +17,8 @@
 // multiply, written with explicit round-to-nearest intrinsics so nothing is fused)
 // and the unit normal (IEEE double multiply/add/sqrt/divide, same intrinsics).
 #include <algorithm>
+#include <cmath>
+#include <cstring>
 #include <cstdio>
 #include <vector>
 
@@ -833,6 +835,103 @@ static bs_status alloc_async(char **p, size_t bytes, cudaStream_t stream, const 
     return BS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Phase 2, shared by triangle and splat sampling: `resolve` writes one row per covered
+// pixel (packed pixel order, so increasing e within a part); the rows are stable-sorted
+// by Morton code and then part, the first row of each (part, position) is kept and
+// every part's outputs are written.  *B receives the scratch block (freed by the caller).
+// ---------------------------------------------------------------------------
+template <class Resolve>
+static bs_status merge_rows(uint32_t nrows, int nparts, const SPart *d_parts, SState *d_st, uint32_t *tot, int sms,
+                            cudaStream_t stream, char **B, Resolve resolve) {
+    if (nrows == 0) return BS_OK;
+    const uint32_t rtiles = (nrows + TILE - 1) / TILE;
+    Scratch Bs;
+    {
+        Scratch probe;
+        for (int i = 0; i < 3; ++i) probe.take((size_t)nrows * 8);          // morton, key, nrm
+        for (int i = 0; i < 4; ++i) probe.take((size_t)nrows * 4);          // rgb, e, part, idx
+        probe.take((size_t)nrows * 8);                                      // sort key temp
+        probe.take((size_t)nrows * 4);                                      // sort value temp
+        probe.take((size_t)nrows * 8);                                      // part keys
+        probe.take(256ull * rtiles * 4);                                    // digit counts
+        probe.take(scan_tmp_words(256ull * rtiles) * 4);
+        probe.take(((size_t)rtiles + 1) * 4);
+        const bs_status rc = alloc_async(B, probe.off, stream, "merge");
+        if (rc != BS_OK) return rc;
+        Bs.base = *B;
+    }
+    Rows rows;
+    rows.morton = (uint64_t *)Bs.take((size_t)nrows * 8);
+    rows.key = (uint64_t *)Bs.take((size_t)nrows * 8);
+    rows.nrm = (uint64_t *)Bs.take((size_t)nrows * 8);
+    rows.rgb = (uint32_t *)Bs.take((size_t)nrows * 4);
+    rows.e = (uint32_t *)Bs.take((size_t)nrows * 4);
+    rows.part = (uint32_t *)Bs.take((size_t)nrows * 4);
+    rows.idx = (uint32_t *)Bs.take((size_t)nrows * 4);
+    uint64_t *ktmp = (uint64_t *)Bs.take((size_t)nrows * 8);
+    uint32_t *vtmp = (uint32_t *)Bs.take((size_t)nrows * 4);
+    uint64_t *pkey = (uint64_t *)Bs.take((size_t)nrows * 8);
+    uint32_t *cnt = (uint32_t *)Bs.take(256ull * rtiles * 4);
+    uint32_t *cnt_tmp = (uint32_t *)Bs.take(scan_tmp_words(256ull * rtiles) * 4);
+    uint32_t *ubc = (uint32_t *)Bs.take(((size_t)rtiles + 1) * 4);
+    resolve(rows);
+    // stable: by Morton code, then by part (rows of one part stay in Morton order)
+    uint32_t *sorted_idx = rows.idx;
+    // sort a copy of the Morton codes so rows.morton stays indexable by row
+    cudaMemcpyAsync(pkey, rows.morton, (size_t)nrows * 8, cudaMemcpyDeviceToDevice, stream);
+    radix_sort(pkey, sorted_idx, ktmp, vtmp, nrows, 64, cnt, cnt_tmp, stream);
+    if (nparts > 1) {
+        k_part_keys<<<(unsigned)std::min<uint64_t>((nrows + 255) / 256, (uint64_t)sms * 32), 256, 0, stream>>>(
+            sorted_idx, rows.part, nrows, pkey);
+        radix_sort(pkey, sorted_idx, ktmp, vtmp, nrows, 16, cnt, cnt_tmp, stream);
+    }
+    k_unique_count<<<rtiles, 256, 0, stream>>>(sorted_idx, rows, nrows, ubc);
+    scan_excl(ubc, rtiles, tot + 1, cnt_tmp, stream);
+    k_unique_pass<0><<<rtiles, 256, 0, stream>>>(sorted_idx, rows, nrows, ubc, d_parts, d_st);
+    k_unique_pass<1><<<rtiles, 256, 0, stream>>>(sorted_idx, rows, nrows, ubc, d_parts, d_st);
+    return BS_OK;
+}
+
+// Host epilogue, shared: read the part states back, report counts and frames, and the
+// first error (invalid part, bad triangle, capacity).
+static bs_status finish_parts(int nparts, SState *d_st, std::vector<SState> &hs, bs_surfels *out,
+                              cudaStream_t stream, const char *who) {
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(hs.data(), d_st, (size_t)nparts * sizeof(SState), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess) {
+        set_error("%s: merge phase failed: %s", who, cudaGetErrorString(cudaGetLastError()));
+        return BS_ECUDA;
+    }
+    for (int p = 0; p < nparts; ++p) {
+        const SState &S = hs[(size_t)p];
+        out[p].n = S.end_out - S.first_out;
+        for (int a = 0; a < 3; ++a) out[p].bbox_min[a] = S.mn[a];
+        out[p].scale = S.scale;
+    }
+    for (int p = 0; p < nparts; ++p) {
+        const SState &S = hs[(size_t)p];
+        if (S.invalid) {
+            out[p].n = 0;
+            set_error(S.nonfinite ? "%s: part %d: non-finite vertex coordinate" : "%s: part %d: mesh has zero extent",
+                      who, p);
+            return BS_EINVAL;
+        }
+        if (S.badtri) {
+            out[p].n = 0;
+            set_error("%s: part %d: %u triangles reference a vertex index >= nverts", who, p, S.badtri);
+            return BS_EINVAL;
+        }
+    }
+    for (int p = 0; p < nparts; ++p)
+        if (out[p].n > out[p].cap) {
+            set_error("%s: part %d: %llu surfels exceed capacity %llu", who, p, (unsigned long long)out[p].n,
+                      (unsigned long long)out[p].cap);
+            return BS_EOVERFLOW;
+        }
+    return BS_OK;
+}
+
 bs_status sample_visible_parts(const bs_mesh *meshes, const int *res, int nparts, const bs_dir *dirs, int ndirs,
                                bs_surfels *out, cudaStream_t stream) {
     if (nparts < 1 || nparts > 65535) { set_error("bs_sample_visible: nparts=%d outside [1, 65535]", nparts); return BS_EINVAL; }
@@ -943,93 +1042,11 @@ bs_status sample_visible_parts(const bs_mesh *meshes, const int *res, int nparts
             break;
         }
         // ---- phase 2: resolve, sort, merge, write ----
-        if (nrows > 0) {
-            const uint32_t rtiles = (nrows + TILE - 1) / TILE;
-            Scratch Bs;
-            {
-                Scratch probe;
-                for (int i = 0; i < 3; ++i) probe.take((size_t)nrows * 8);          // morton, key, nrm
-                for (int i = 0; i < 4; ++i) probe.take((size_t)nrows * 4);          // rgb, e, part, idx
-                probe.take((size_t)nrows * 8);                                      // sort key temp
-                probe.take((size_t)nrows * 4);                                      // sort value temp
-                probe.take((size_t)nrows * 8);                                      // part keys
-                probe.take(256ull * rtiles * 4);                                    // digit counts
-                probe.take(scan_tmp_words(256ull * rtiles) * 4);
-                probe.take(((size_t)rtiles + 1) * 4);
-                rc = alloc_async(&B, probe.off, stream, "merge");
-                if (rc != BS_OK) break;
-                Bs.base = B;
-            }
-            Rows rows;
-            rows.morton = (uint64_t *)Bs.take((size_t)nrows * 8);
-            rows.key = (uint64_t *)Bs.take((size_t)nrows * 8);
-            rows.nrm = (uint64_t *)Bs.take((size_t)nrows * 8);
-            rows.rgb = (uint32_t *)Bs.take((size_t)nrows * 4);
-            rows.e = (uint32_t *)Bs.take((size_t)nrows * 4);
-            rows.part = (uint32_t *)Bs.take((size_t)nrows * 4);
-            rows.idx = (uint32_t *)Bs.take((size_t)nrows * 4);
-            uint64_t *ktmp = (uint64_t *)Bs.take((size_t)nrows * 8);
-            uint32_t *vtmp = (uint32_t *)Bs.take((size_t)nrows * 4);
-            uint64_t *pkey = (uint64_t *)Bs.take((size_t)nrows * 8);
-            uint32_t *cnt = (uint32_t *)Bs.take(256ull * rtiles * 4);
-            uint32_t *cnt_tmp = (uint32_t *)Bs.take(scan_tmp_words(256ull * rtiles) * 4);
-            uint32_t *ubc = (uint32_t *)Bs.take(((size_t)rtiles + 1) * 4);
+        rc = merge_rows(nrows, nparts, d_parts, d_st, tot, sms, stream, &B, [&](const Rows &rows) {
             k_resolve<<<ptiles, 256, 0, stream>>>(depth, NP, d_parts, d_pofs, nparts, T, q, setup, views, bc, rows);
-            // stable: by Morton code, then by part (rows of one part stay in Morton order)
-            uint32_t *sorted_idx = rows.idx;
-            {
-                // sort a copy of the Morton codes so rows.morton stays indexable by row
-                cudaMemcpyAsync(pkey, rows.morton, (size_t)nrows * 8, cudaMemcpyDeviceToDevice, stream);
-                radix_sort(pkey, sorted_idx, ktmp, vtmp, nrows, 64, cnt, cnt_tmp, stream);
-                if (nparts > 1) {
-                    k_part_keys<<<(unsigned)std::min<uint64_t>((nrows + 255) / 256, (uint64_t)sms * 32), 256, 0, stream>>>(
-                        sorted_idx, rows.part, nrows, pkey);
-                    radix_sort(pkey, sorted_idx, ktmp, vtmp, nrows, 16, cnt, cnt_tmp, stream);
-                }
-            }
-            k_unique_count<<<rtiles, 256, 0, stream>>>(sorted_idx, rows, nrows, ubc);
-            scan_excl(ubc, rtiles, tot + 1, cnt_tmp, stream);
-            k_unique_pass<0><<<rtiles, 256, 0, stream>>>(sorted_idx, rows, nrows, ubc, d_parts, d_st);
-            k_unique_pass<1><<<rtiles, 256, 0, stream>>>(sorted_idx, rows, nrows, ubc, d_parts, d_st);
-        }
-        if (cudaGetLastError() != cudaSuccess ||
-            cudaMemcpyAsync(hs.data(), d_st, (size_t)nparts * sizeof(SState), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
-            cudaStreamSynchronize(stream) != cudaSuccess) {
-            set_error("bs_sample_visible: merge phase failed: %s", cudaGetErrorString(cudaGetLastError()));
-            rc = BS_ECUDA;
-            break;
-        }
-        for (int p = 0; p < nparts && rc == BS_OK; ++p) {
-            const SState &S = hs[(size_t)p];
-            out[p].n = S.end_out - S.first_out;
-            for (int a = 0; a < 3; ++a) out[p].bbox_min[a] = S.mn[a];
-            out[p].scale = S.scale;
-        }
-        for (int p = 0; p < nparts; ++p) {
-            const SState &S = hs[(size_t)p];
-            if (S.invalid) {
-                out[p].n = 0;
-                set_error(S.nonfinite ? "bs_sample_visible: part %d: non-finite vertex coordinate"
-                                      : "bs_sample_visible: part %d: mesh has zero extent", p);
-                rc = BS_EINVAL;
-                break;
-            }
-            if (S.badtri) {
-                out[p].n = 0;
-                set_error("bs_sample_visible: part %d: %u triangles reference a vertex index >= nverts", p, S.badtri);
-                rc = BS_EINVAL;
-                break;
-            }
-        }
-        if (rc == BS_OK) {
-            for (int p = 0; p < nparts; ++p)
-                if (out[p].n > out[p].cap) {
-                    set_error("bs_sample_visible: part %d: %llu surfels exceed capacity %llu", p,
-                              (unsigned long long)out[p].n, (unsigned long long)out[p].cap);
-                    rc = BS_EOVERFLOW;
-                    break;
-                }
-        }
+        });
+        if (rc != BS_OK) break;
+        rc = finish_parts(nparts, d_st, hs, out, stream, "bs_sample_visible");
     } while (0);
     if (B) cudaFreeAsync(B, stream);
     cudaFreeAsync(A.base, stream);
@@ -1040,6 +1057,381 @@ bs_status sample_visible(const bs_mesh *mesh, const bs_dir *dirs, int ndirs, int
                          cudaStream_t stream) {
     if (!mesh || !dirs || !out) { set_error("bs_sample_visible: NULL argument"); return BS_EINVAL; }
     return sample_visible_parts(mesh, &res, 1, dirs, ndirs, out, stream);
+}
+
+
+// ===========================================================================
+// Splat sampling: a parent node's initial surfel set rendered from its children's
+// surfels instead of their triangles (Sec. 3.4, bottom-up), each surfel drawn as the
+// oriented disc of Sec. 4.2.  Axis views only.  Coverage, depth and the emitted hit
+// point are exact integer arithmetic in units of 1/(2 res) of a pixel-centre step:
+// pixel (px, py) has its ray at u = ulo + (2px + 1) U1 / (2 res) (likewise v); with
+// DU = (2px + 1) U1 - 2 res (cu - ulo) and nw = n.d > 0 (normal turned to the camera),
+// the ray meets the plane n.(p - c) = 0 within the disc iff
+//   (DU^2 + DV^2) nw^2 + (nu DU + nv DV)^2 <= R2 (2 res)^2 nw^2,
+// at depth dc + (nu DU + nv DV) / (nw 2 res), dc = -(d.c) + wbias.
+// ===========================================================================
+struct SSet {
+    const uint64_t *key;
+    const int16_t *nrm;
+    const uint8_t *rgb;
+    const uint32_t *perm;
+    float bmin[3];
+    uint32_t node;
+    double scale;
+    int64_t r2;
+};
+
+struct Splat {          // one splat in its node's frame
+    int32_t c[3];
+    int16_t n[3];
+    uint16_t pad;
+    uint32_t rgb;       // 3 bytes packed
+    uint32_t node;
+    int64_t R2;         // squared radius in node units
+    int64_t Rb;         // ceil(sqrt(R2))
+};
+
+__device__ __forceinline__ int64_t floor_div64(int64_t a, int64_t b) {  // b > 0
+    int64_t q = a / b;
+    if ((a % b) != 0 && a < 0) --q;
+    return q;
+}
+
+// splat g of the call: its set, its surfel (through perm), moved to its node's frame
+__global__ void k_splat_setup(const SSet *__restrict__ sets, const uint64_t *__restrict__ sofs, int nsets, uint64_t S,
+                              const SState *__restrict__ st, Splat *__restrict__ out) {
+    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < S; g += (uint64_t)gridDim.x * blockDim.x) {
+        const int si = find_part(sofs, nsets, g);
+        const SSet &T = sets[si];
+        const uint64_t i = g - sofs[si];
+        const uint64_t idx = T.perm ? (uint64_t)T.perm[i] : i;
+        const uint64_t key = T.key[idx];
+        const SState &N = st[T.node];
+        const uint32_t qc[3] = {pos_x(key), pos_y(key), pos_z(key)};
+        Splat sp;
+        for (int a = 0; a < 3; ++a) {
+            double t = __ddiv_rn((double)qc[a], T.scale);
+            t = __dadd_rn((double)T.bmin[a], t);
+            t = __dsub_rn(t, (double)N.mn[a]);
+            t = __dmul_rn(t, N.scale);
+            const double f = floor(t);
+            sp.c[a] = f < 0.0 ? 0 : (f > (double)QMAX ? (int32_t)QMAX : (int32_t)f);
+            sp.n[a] = T.nrm[3 * idx + a];
+        }
+        const double rmax2 = 3.0 * (double)QMAX * (double)QMAX;
+        double r = __ddiv_rn(__dsqrt_rn(__ll2double_rn(T.r2)), T.scale);
+        r = __dmul_rn(r, N.scale);
+        const double rr = __dmul_rn(r, r);
+        sp.R2 = rr >= rmax2 ? (int64_t)rmax2 : (int64_t)ceil(rr);
+        int64_t rb = (int64_t)__dsqrt_rn(__ll2double_rn(sp.R2));
+        for (int it = 0; it < 4 && rb * rb < sp.R2; ++it) ++rb;
+        sp.Rb = rb;
+        sp.rgb = T.rgb ? ((uint32_t)T.rgb[3 * idx] | ((uint32_t)T.rgb[3 * idx + 1] << 8) |
+                          ((uint32_t)T.rgb[3 * idx + 2] << 16))
+                       : 0u;
+        sp.node = T.node;
+        sp.pad = 0;
+        out[g] = sp;
+    }
+}
+
+// A splat in one view: normal components (turned to the camera), scaled centre, pixel box.
+struct SplatView {
+    int64_t nu, nv, nw, cu2, cv2, dc, two_res;
+    int32_t px0, px1, py0, py1;
+    bool flip;
+};
+
+__device__ __forceinline__ bool splat_view(const View &V, const Splat &sp, int res, SplatView &w) {
+    int64_t nu = 0, nv = 0, nw = 0, cu = 0, cv = 0, cd = 0;
+    for (int a = 0; a < 3; ++a) {
+        nu += (int64_t)V.u[a] * sp.n[a];
+        nv += (int64_t)V.v[a] * sp.n[a];
+        nw += (int64_t)V.d[a] * sp.n[a];
+        cu += (int64_t)V.u[a] * sp.c[a];
+        cv += (int64_t)V.v[a] * sp.c[a];
+        cd += (int64_t)V.d[a] * sp.c[a];
+    }
+    w.flip = nw < 0;
+    if (w.flip) { nu = -nu; nv = -nv; nw = -nw; }
+    w.nu = nu; w.nv = nv; w.nw = nw;
+    w.two_res = 2 * (int64_t)res;
+    w.cu2 = (cu - V.ulo) * w.two_res;
+    w.cv2 = (cv - V.vlo) * w.two_res;
+    w.dc = -cd + V.wbias;
+    if (nw == 0) return false;  // seen edge-on
+    // a covered pixel has |DU|, |DV| <= 2 res Rb
+    const int64_t span = w.two_res * sp.Rb;
+    int64_t px0 = -floor_div64(-(w.cu2 - span - V.U1), 2 * V.U1), px1 = floor_div64(w.cu2 + span - V.U1, 2 * V.U1);
+    int64_t py0 = -floor_div64(-(w.cv2 - span - V.V1), 2 * V.V1), py1 = floor_div64(w.cv2 + span - V.V1, 2 * V.V1);
+    px0 = px0 < 0 ? 0 : px0;
+    py0 = py0 < 0 ? 0 : py0;
+    px1 = px1 > res - 1 ? res - 1 : px1;
+    py1 = py1 > res - 1 ? res - 1 : py1;
+    w.px0 = (int32_t)px0; w.px1 = (int32_t)px1; w.py0 = (int32_t)py0; w.py1 = (int32_t)py1;
+    return px0 <= px1 && py0 <= py1;
+}
+
+__device__ __forceinline__ void splat_pixels(const View &V, const SplatView &w, int64_t R2, uint32_t g, int res,
+                                             uint32_t first, uint32_t lanes, unsigned long long *__restrict__ dbuf) {
+    const uint32_t wdt = (uint32_t)(w.px1 - w.px0 + 1);
+    const uint32_t npx = wdt * (uint32_t)(w.py1 - w.py0 + 1);
+    const __int128 nw2 = (__int128)w.nw * w.nw;
+    const __int128 rhs = (__int128)R2 * ((__int128)w.two_res * w.two_res) * nw2;
+    for (uint32_t pp = first; pp < npx; pp += lanes) {
+        const int32_t py = w.py0 + (int32_t)(pp / wdt), px = w.px0 + (int32_t)(pp % wdt);
+        const int64_t DU = (2 * (int64_t)px + 1) * V.U1 - w.cu2;
+        const int64_t DV = (2 * (int64_t)py + 1) * V.V1 - w.cv2;
+        const __int128 t = (__int128)w.nu * DU + (__int128)w.nv * DV;
+        const __int128 lhs = ((__int128)DU * DU + (__int128)DV * DV) * nw2 + t * t;
+        if (lhs > rhs) continue;
+        int64_t z = floor_div64(w.dc * w.nw * w.two_res + w.nu * DU + w.nv * DV, w.nw * w.two_res);
+        z = z < 0 ? 0 : (z > 0xFFFFFFFFll ? 0xFFFFFFFFll : z);
+        atomicMin(dbuf + (uint64_t)py * res + px, (unsigned long long)(((uint64_t)z << 32) | g));
+    }
+}
+
+// a thread per (direction, splat); discs whose pixel box holds more than RASTER_SMALL
+// pixels are drawn by the whole warp
+__global__ void __launch_bounds__(256) k_splat_raster(const SPart *__restrict__ parts, uint64_t S,
+                                                      const Splat *__restrict__ splats, const Views views,
+                                                      unsigned long long *__restrict__ depth) {
+    const int dir = blockIdx.y;
+    const View &V = views.v[dir];
+    const int lane = threadIdx.x & 31;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < S; base += stride) {
+        const uint64_t g = base + lane;
+        SplatView w;
+        bool valid = false;
+        int res = 0;
+        int64_t R2 = 0;
+        unsigned long long *dbuf = nullptr;
+        if (g < S) {
+            const Splat sp = splats[g];
+            const SPart &P = parts[sp.node];
+            res = P.res;
+            R2 = sp.R2;
+            dbuf = depth + P.pofs + (uint64_t)dir * res * res;
+            valid = splat_view(V, sp, res, w);
+        }
+        const uint32_t npx = valid ? (uint32_t)(w.px1 - w.px0 + 1) * (uint32_t)(w.py1 - w.py0 + 1) : 0u;
+        if (valid && npx <= RASTER_SMALL) splat_pixels(V, w, R2, (uint32_t)g, res, 0u, 1u, dbuf);
+        uint32_t big = __ballot_sync(0xffffffffu, npx > RASTER_SMALL);
+        while (big) {
+            const int j = __ffs(big) - 1;
+            big &= big - 1;
+            // the whole warp on lane j's disc (its record reloaded: one broadcast load)
+            const Splat sj = splats[base + j];
+            const SPart &Pj = parts[sj.node];
+            SplatView wj;
+            splat_view(V, sj, Pj.res, wj);
+            splat_pixels(V, wj, sj.R2, (uint32_t)(base + j), Pj.res, (uint32_t)lane, 32u,
+                         depth + Pj.pofs + (uint64_t)dir * Pj.res * Pj.res);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_splat_resolve(const unsigned long long *__restrict__ depth, uint64_t npix,
+                                                       const SPart *__restrict__ parts, const uint64_t *__restrict__ pofs,
+                                                       int nparts, const Splat *__restrict__ splats, const Views views,
+                                                       const uint32_t *__restrict__ blockofs, Rows rows) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t base = (uint64_t)blockIdx.x * TILE + (uint64_t)warp * TILE_ROUNDS * 32;
+    __shared__ uint32_t wc[TILE_WARPS];
+    uint32_t c = 0;
+    for (int r = 0; r < TILE_ROUNDS; ++r) {
+        const uint64_t i = base + (uint64_t)r * 32 + lane;
+        c += (i < npix && depth[i] != ~0ull) ? 1u : 0u;
+    }
+    c = __reduce_add_sync(0xffffffffu, c);
+    if (lane == 0) wc[warp] = c;
+    __syncthreads();
+    uint32_t out = blockofs[blockIdx.x];
+    for (int w = 0; w < warp; ++w) out += wc[w];
+    int p = -1;
+    uint64_t p_lo = 1, p_hi = 0;
+    for (int r = 0; r < TILE_ROUNDS; ++r) {
+        const uint64_t i = base + (uint64_t)r * 32 + lane;
+        const unsigned long long dv = i < npix ? depth[i] : ~0ull;
+        const bool hit = dv != ~0ull;
+        const uint32_t m = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+            const uint32_t o = out + __popc(m & ((1u << lane) - 1u));
+            if (i < p_lo || i >= p_hi) {
+                p = find_part(pofs, nparts, i);
+                p_lo = pofs[p];
+                p_hi = p + 1 < nparts ? pofs[p + 1] : npix;
+            }
+            const SPart &P = parts[p];
+            const uint64_t res2 = (uint64_t)P.res * P.res;
+            const uint64_t local = i - P.pofs;
+            const int dir = (int)(local / res2);
+            const uint64_t pix = local - (uint64_t)dir * res2;
+            const int64_t py = (int64_t)(pix / P.res), px = (int64_t)(pix % P.res);
+            const uint32_t g = (uint32_t)(dv & 0xffffffffull);
+            const Splat sp = splats[g];
+            const View &V = views.v[dir];
+            SplatView w;
+            splat_view(V, sp, P.res, w);
+            const int64_t DU = (2 * px + 1) * V.U1 - w.cu2;
+            const int64_t DV = (2 * py + 1) * V.V1 - w.cv2;
+            const int64_t W = w.nu * DU + w.nv * DV;
+            uint64_t pos[3];
+            for (int a = 0; a < 3; ++a) {
+                int64_t q = sp.c[a];
+                if (V.u[a] != 0) q += floor_div64((int64_t)V.u[a] * DU, w.two_res);
+                if (V.v[a] != 0) q += floor_div64((int64_t)V.v[a] * DV, w.two_res);
+                if (V.d[a] != 0) q += floor_div64(-(int64_t)V.d[a] * W, w.nw * w.two_res);
+                pos[a] = (uint64_t)(q < 0 ? 0 : (q > QMAX ? QMAX : q));
+            }
+            const uint64_t key = pack_pos(pos[0], pos[1], pos[2]);
+            uint64_t np = 0;
+            for (int a = 0; a < 3; ++a) {
+                const int16_t v = w.flip ? (int16_t)-sp.n[a] : sp.n[a];
+                np |= (uint64_t)(uint16_t)v << (16 * a);
+            }
+            rows.morton[o] = morton_of(key);
+            rows.key[o] = key;
+            rows.nrm[o] = np;
+            rows.rgb[o] = sp.rgb;
+            rows.e[o] = (uint32_t)local;
+            rows.part[o] = (uint32_t)p;
+            rows.idx[o] = o;
+        }
+        out += __popc(m);
+    }
+}
+
+bs_status sample_splats(const bs_splat_set *sets, int nsets, const bs_splat_node *nodes, int nnodes, const bs_dir *dirs,
+                        int ndirs, bs_surfels *out, cudaStream_t stream) {
+    const char *who = "bs_sample_splats";
+    if (nnodes < 1 || nnodes > 65535) { set_error("%s: nnodes=%d outside [1, 65535]", who, nnodes); return BS_EINVAL; }
+    if (nsets < 0 || (nsets > 0 && !sets) || !nodes || !dirs || !out) { set_error("%s: NULL or bad argument", who); return BS_EINVAL; }
+    if (ndirs < 1 || ndirs > BS_MAX_DIRS) { set_error("%s: ndirs=%d outside [1,%d]", who, ndirs, BS_MAX_DIRS); return BS_EINVAL; }
+    Views views;
+    views.ndirs = ndirs;
+    for (int i = 0; i < ndirs; ++i) {
+        const bs_dir d = dirs[i];
+        const int nz = (d.x != 0) + (d.y != 0) + (d.z != 0);
+        const bool unit = (d.x >= -1 && d.x <= 1) && (d.y >= -1 && d.y <= 1) && (d.z >= -1 && d.z <= 1);
+        if (nz != 1 || !unit) { set_error("%s: direction %d is not an axis direction", who, i); return BS_EINVAL; }
+        make_frame(d, views.v[i]);
+    }
+    std::vector<SPart> hp((size_t)nnodes);
+    std::vector<SState> hs((size_t)nnodes);
+    std::vector<uint64_t> pofs((size_t)nnodes);
+    uint64_t NP = 0;
+    for (int p = 0; p < nnodes; ++p) {
+        const bs_splat_node &N = nodes[p];
+        if (N.res < 1 || N.res > BS_MAX_RES) { set_error("%s: node %d: res=%d outside [1,%d]", who, p, N.res, BS_MAX_RES); return BS_EINVAL; }
+        if (!(N.scale > 0.0) || !std::isfinite(N.scale) || !std::isfinite(N.frame_min[0]) || !std::isfinite(N.frame_min[1]) ||
+            !std::isfinite(N.frame_min[2])) {
+            set_error("%s: node %d: bad frame", who, p);
+            return BS_EINVAL;
+        }
+        if (out[p].cap > 0 && !out[p].key) { set_error("%s: node %d: NULL key output", who, p); return BS_EINVAL; }
+        SPart &P = hp[(size_t)p];
+        memset(&P, 0, sizeof(P));
+        P.okey = out[p].key; P.onrm = out[p].nrm; P.orgb = out[p].rgb; P.osrc = out[p].src;
+        P.cap = out[p].cap;
+        P.res = N.res;
+        P.pofs = NP;
+        pofs[(size_t)p] = NP;
+        NP += (uint64_t)ndirs * N.res * N.res;
+        SState &T = hs[(size_t)p];
+        memset(&T, 0, sizeof(T));
+        for (int a = 0; a < 3; ++a) T.mn[a] = N.frame_min[a];
+        T.scale = N.scale;
+    }
+    if (NP >= (1ull << 32)) { set_error("%s: %llu pixels in one call (limit 2^32)", who, (unsigned long long)NP); return BS_EINVAL; }
+    std::vector<SSet> hsets((size_t)std::max(nsets, 1));
+    std::vector<uint64_t> sofs((size_t)std::max(nsets, 1));
+    uint64_t S = 0;
+    for (int i = 0; i < nsets; ++i) {
+        const bs_splat_set &T = sets[i];
+        if (T.node >= (uint32_t)nnodes) { set_error("%s: set %d: node %u >= nnodes", who, i, T.node); return BS_EINVAL; }
+        if (T.n > 0 && (!T.key || !T.nrm)) { set_error("%s: set %d: NULL key or normal array", who, i); return BS_EINVAL; }
+        if (T.r2 < 0 || !(T.scale > 0.0) || !std::isfinite(T.scale)) { set_error("%s: set %d: bad radius or scale", who, i); return BS_EINVAL; }
+        SSet &D = hsets[(size_t)i];
+        D.key = T.key; D.nrm = T.nrm; D.rgb = T.rgb; D.perm = T.perm;
+        for (int a = 0; a < 3; ++a) D.bmin[a] = T.bbox_min[a];
+        D.node = T.node; D.scale = T.scale; D.r2 = T.r2;
+        sofs[(size_t)i] = S;
+        S += T.n;
+        if (S >= 0xFFFFFFFFull) { set_error("%s: more than 2^32 - 1 splats", who); return BS_EINVAL; }
+    }
+    const uint32_t ptiles = (uint32_t)((NP + TILE - 1) / TILE);
+    int sms = 152, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    Scratch A;
+    size_t a_bytes = 0;
+    {
+        Scratch probe;
+        probe.take((size_t)nnodes * sizeof(SPart));
+        probe.take((size_t)nnodes * sizeof(SState));
+        probe.take((size_t)nnodes * 8);
+        probe.take(hsets.size() * sizeof(SSet));
+        probe.take(sofs.size() * 8);
+        probe.take((size_t)std::max<uint64_t>(S, 1) * sizeof(Splat));
+        probe.take(NP * sizeof(unsigned long long));
+        probe.take(((size_t)ptiles + 1) * 4);
+        probe.take(scan_tmp_words(ptiles) * 4);
+        probe.take(16);
+        a_bytes = probe.off;
+    }
+    bs_status rc = alloc_async(&A.base, a_bytes, stream, "splat");
+    if (rc != BS_OK) return rc;
+    SPart *d_parts = (SPart *)A.take((size_t)nnodes * sizeof(SPart));
+    SState *d_st = (SState *)A.take((size_t)nnodes * sizeof(SState));
+    uint64_t *d_pofs = (uint64_t *)A.take((size_t)nnodes * 8);
+    SSet *d_sets = (SSet *)A.take(hsets.size() * sizeof(SSet));
+    uint64_t *d_sofs = (uint64_t *)A.take(sofs.size() * 8);
+    Splat *d_splats = (Splat *)A.take((size_t)std::max<uint64_t>(S, 1) * sizeof(Splat));
+    unsigned long long *depth = (unsigned long long *)A.take(NP * sizeof(unsigned long long));
+    uint32_t *bc = (uint32_t *)A.take(((size_t)ptiles + 1) * 4);
+    uint32_t *stmp = (uint32_t *)A.take(scan_tmp_words(ptiles) * 4);
+    uint32_t *tot = (uint32_t *)A.take(16);
+    char *B = nullptr;
+    uint32_t nrows = 0;
+    do {
+        if (cudaMemcpyAsync(d_parts, hp.data(), (size_t)nnodes * sizeof(SPart), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+            cudaMemcpyAsync(d_st, hs.data(), (size_t)nnodes * sizeof(SState), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+            cudaMemcpyAsync(d_pofs, pofs.data(), (size_t)nnodes * 8, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+            cudaMemcpyAsync(d_sets, hsets.data(), hsets.size() * sizeof(SSet), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+            cudaMemcpyAsync(d_sofs, sofs.data(), sofs.size() * 8, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+            cudaMemsetAsync(depth, 0xff, NP * sizeof(unsigned long long), stream) != cudaSuccess ||
+            cudaMemsetAsync(tot, 0, 16, stream) != cudaSuccess) {
+            set_error("%s: upload failed: %s", who, cudaGetErrorString(cudaGetLastError()));
+            rc = BS_ECUDA;
+            break;
+        }
+        if (S > 0) {
+            k_splat_setup<<<(unsigned)std::min<uint64_t>((S + 255) / 256, (uint64_t)sms * 32), 256, 0, stream>>>(
+                d_sets, d_sofs, nsets, S, d_st, d_splats);
+            dim3 gr((unsigned)std::min<uint64_t>((S + 255) / 256, (uint64_t)sms * 16), ndirs);
+            k_splat_raster<<<gr, 256, 0, stream>>>(d_parts, S, d_splats, views, depth);
+        }
+        k_cover_count<<<ptiles, 256, 0, stream>>>(depth, NP, bc);
+        scan_excl(bc, ptiles, tot, stmp, stream);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(&nrows, tot, 4, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+            cudaStreamSynchronize(stream) != cudaSuccess) {
+            set_error("%s: raster phase failed: %s", who, cudaGetErrorString(cudaGetLastError()));
+            rc = BS_ECUDA;
+            break;
+        }
+        rc = merge_rows(nrows, nnodes, d_parts, d_st, tot, sms, stream, &B, [&](const Rows &rows) {
+            k_splat_resolve<<<ptiles, 256, 0, stream>>>(depth, NP, d_parts, d_pofs, nnodes, d_splats, views, bc, rows);
+        });
+        if (rc != BS_OK) break;
+        rc = finish_parts(nnodes, d_st, hs, out, stream, who);
+    } while (0);
+    if (B) cudaFreeAsync(B, stream);
+    cudaFreeAsync(A.base, stream);
+    return rc;
 }
 
 }  // namespace bs
