@@ -217,6 +217,14 @@ bs_status bs_prefix_median_nn(const bs_surfels *s, const uint32_t *perm, uint64_
  * host.  Synchronises the stream. */
 bs_status bs_prefix_for_radius(const int64_t *rad2, uint64_t m, int64_t r2, uint64_t *p, void *cuda_stream);
 
+/* bs_prefix_for_radius for nparts orderings in one launch (the children of the parent
+ * nodes of Sec. 3.4's bottom-up generation).  rad2: HOST array of device pointers; m, r2:
+ * HOST arrays; p: HOST output.  r2_at (HOST, may be NULL) receives rad2[min(p, m - 1)]:
+ * the squared distance within which the prefix of length p reaches every point (exact for
+ * p < m, an upper bound when no ordered entry qualifies).  Synchronises the stream. */
+bs_status bs_prefix_for_radius_batched(const int64_t *const *rad2, const uint64_t *m, const int64_t *r2, int nparts,
+                                       uint64_t *p, int64_t *r2_at, void *cuda_stream);
+
 /* The paper's estimate of that prefix length, p(r) = pm * (r_m / r)^2, from the
  * squared radii rm2 = r_m^2 and r2 = r^2 (same units); +inf for r2 <= 0. */
 double bs_prefix_estimate(uint64_t pm, int64_t rm2, int64_t r2);

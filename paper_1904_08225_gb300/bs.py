@@ -25,6 +25,7 @@ INT64_MAX = (1 << 63) - 1
 EXPORTS = ["bs_sample_visible", "bs_sample_visible_batched", "bs_order", "bs_order_noalloc", "bs_order_batched", "bs_server_create", "bs_server_submit",
            "bs_server_poll", "bs_server_times", "bs_server_destroy", "bs_set_tuning", "bs_last_launch_ms",
            "bs_prefix_median_nn", "bs_prefix_for_radius", "bs_prefix_estimate", "bs_scene_generate", "bs_sample_splats",
+           "bs_prefix_for_radius_batched",
            "bs_last_error"]
 
 
@@ -84,6 +85,7 @@ def load(build_if_stale: bool = True) -> C.CDLL:
             lib.bs_sample_visible.argtypes = [C.POINTER(Mesh), C.POINTER(Dir), C.c_int, C.c_int, C.POINTER(Surfels), P]
             lib.bs_sample_visible_batched.argtypes = [C.POINTER(Mesh), C.POINTER(C.c_int), C.c_int, C.POINTER(Dir),
                                                       C.c_int, C.POINTER(Surfels), P]
+            lib.bs_prefix_for_radius_batched.argtypes = [P, P, P, C.c_int, P, P, P]
             lib.bs_sample_splats.argtypes = [C.POINTER(SplatSet), C.c_int, C.POINTER(SplatNode), C.c_int,
                                              C.POINTER(Dir), C.c_int, C.POINTER(Surfels), P]
             lib.bs_order.argtypes = [C.POINTER(Surfels), C.POINTER(OrderOpts), P, P, P, P]
@@ -200,6 +202,26 @@ def prefix_for_radius(rad2, r2: int, stream=None) -> int:
     _check(lib.bs_prefix_for_radius(C.c_void_p(rad2.data_ptr()), rad2.shape[0], int(r2), C.byref(out),
                                     _stream(stream)), "bs_prefix_for_radius")
     return out.value
+
+
+def prefix_for_radius_batched(rad2s, ms, r2s, stream=None):
+    """bs_prefix_for_radius_batched: (p, r2_at) int arrays for many orderings.
+
+    rad2s: list of CUDA int64 tensors (or raw device addresses); ms, r2s: ints per part."""
+    lib = load()
+    P = len(ms)
+    ptrs = np.ascontiguousarray([t if isinstance(t, (int, np.integer)) else t.data_ptr() for t in rad2s],
+                                dtype=np.uintp)
+    m = np.ascontiguousarray(ms, dtype=np.uint64)
+    r2 = np.ascontiguousarray(r2s, dtype=np.int64)
+    p = np.zeros(P, np.uint64)
+    at = np.zeros(P, np.int64)
+    if P:
+        _check(lib.bs_prefix_for_radius_batched(C.c_void_p(ptrs.ctypes.data), C.c_void_p(m.ctypes.data),
+                                                C.c_void_p(r2.ctypes.data), P, C.c_void_p(p.ctypes.data),
+                                                C.c_void_p(at.ctypes.data), _stream(stream)),
+               "bs_prefix_for_radius_batched")
+    return p, at
 
 
 def prefix_estimate(pm: int, rm2: int, r2: int) -> float:

@@ -173,6 +173,12 @@ bs_status bs_sample_splats(const bs_splat_set *sets, int nsets, const bs_splat_n
     return sample_splats(sets, nsets, nodes, nnodes, dirs, ndirs, out, (cudaStream_t)cuda_stream);
 }
 
+bs_status bs_prefix_for_radius_batched(const int64_t *const *rad2, const uint64_t *m, const int64_t *r2, int nparts,
+                                       uint64_t *p, int64_t *r2_at, void *cuda_stream) {
+    clear_error();
+    return prefix_for_radius_batched(rad2, m, r2, nparts, p, r2_at, (cudaStream_t)cuda_stream);
+}
+
 double bs_prefix_estimate(uint64_t pm, int64_t rm2, int64_t r2) {
     if (r2 <= 0) return (double)INFINITY;
     return (double)pm * (double)rm2 / (double)r2;

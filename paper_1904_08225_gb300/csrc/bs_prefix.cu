@@ -1,6 +1,8 @@
 // bs_prefix.cu -- prefix selection at render time (Sec. 4.1): the median nearest-
 // neighbour distance r_m inside the first p_m surfels of an ordering, and the shortest
 // prefix whose surfels reach every point of the part within a radius.
+#include <vector>
+
 #include "bs_internal.cuh"
 
 namespace bs {
@@ -100,6 +102,66 @@ bs_status prefix_for_radius(const int64_t *rad2, uint64_t m, int64_t r2, uint64_
     if (e != cudaSuccess) { set_error("bs_prefix_for_radius: %s", cudaGetErrorString(e)); return BS_ECUDA; }
     // rad2[1..m) does not increase: the entries above r2 are exactly [1, 1 + h)
     *p = std::min<uint64_t>(1 + h, m);
+    return BS_OK;
+}
+
+// thread per part: binary search of the first k in [1, m) with rad2[k] <= r2 (rad2[1..m)
+// does not increase), m when none
+__global__ void k_prefix_batched(const int64_t *const *__restrict__ rad2, const uint64_t *__restrict__ m,
+                                 const int64_t *__restrict__ r2, int nparts, uint64_t *__restrict__ p,
+                                 int64_t *__restrict__ r2_at) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nparts) return;
+    const int64_t *r = rad2[i];
+    const uint64_t mi = m[i];
+    uint64_t lo = 1, hi = mi;
+    for (int it = 0; it < 64 && lo < hi; ++it) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        if (r[mid] <= r2[i]) hi = mid;
+        else lo = mid + 1;
+    }
+    const uint64_t pi = lo < mi ? lo : mi;
+    p[i] = pi;
+    r2_at[i] = r[pi < mi ? pi : mi - 1];
+}
+
+bs_status prefix_for_radius_batched(const int64_t *const *rad2, const uint64_t *m, const int64_t *r2, int nparts,
+                                    uint64_t *p, int64_t *r2_at, cudaStream_t stream) {
+    if (nparts < 0 || (nparts > 0 && (!rad2 || !m || !r2 || !p))) {
+        set_error("bs_prefix_for_radius_batched: NULL argument");
+        return BS_EINVAL;
+    }
+    for (int i = 0; i < nparts; ++i)
+        if (!rad2[i] || m[i] == 0 || r2[i] < 0) {
+            set_error("bs_prefix_for_radius_batched: part %d: NULL rad2, m = 0 or negative r2", i);
+            return BS_EINVAL;
+        }
+    if (nparts == 0) return BS_OK;
+    const size_t n = (size_t)nparts;
+    char *buf = nullptr;
+    const size_t bytes = n * (8 + 8 + 8 + 8 + 8);
+    cudaError_t e = cudaMallocAsync((void **)&buf, bytes, stream);
+    if (e != cudaSuccess) { cudaGetLastError(); set_error("bs_prefix_for_radius_batched: scratch allocation failed"); return BS_ENOMEM; }
+    const int64_t **d_rad2 = (const int64_t **)buf;
+    uint64_t *d_m = (uint64_t *)(buf + 8 * n);
+    int64_t *d_r2 = (int64_t *)(buf + 16 * n);
+    uint64_t *d_p = (uint64_t *)(buf + 24 * n);
+    int64_t *d_at = (int64_t *)(buf + 32 * n);
+    std::vector<int64_t> at(n);
+    e = cudaMemcpyAsync(d_rad2, rad2, 8 * n, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_m, m, 8 * n, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_r2, r2, 8 * n, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) {
+        k_prefix_batched<<<(nparts + 255) / 256, 256, 0, stream>>>(d_rad2, d_m, d_r2, nparts, d_p, d_at);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p, d_p, 8 * n, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(at.data(), d_at, 8 * n, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    cudaFreeAsync(buf, stream);
+    if (e != cudaSuccess) { set_error("bs_prefix_for_radius_batched: %s", cudaGetErrorString(e)); return BS_ECUDA; }
+    if (r2_at)
+        for (size_t i = 0; i < n; ++i) r2_at[i] = at[i];
     return BS_OK;
 }
 

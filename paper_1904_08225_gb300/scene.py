@@ -138,3 +138,152 @@ def run(seed: int = 0, lines: int = 20, per_line: int = 2500, group: int = 50, n
     torch.cuda.synchronize()
     res.seconds = time.perf_counter() - t0
     return res
+
+
+# ---------------------------------------------------------------------------
+# Bottom-up generation (Sec. 3.4): groups are sampled from their parts' surfels and
+# lines from their groups' surfels, each surfel drawn as an oriented disc
+# (bs_sample_splats), instead of from triangles.
+# ---------------------------------------------------------------------------
+QMAX = 2**21 - 1
+
+
+def parent_frame(mins, scales):
+    """Frame of a parent node that holds its children's quantisation cubes: the smallest
+    corner, and the scale that maps the largest extent onto 2^21 - 1."""
+    mins = np.asarray(mins, np.float64).reshape(-1, 3)
+    scales = np.asarray(scales, np.float64)
+    fmin = mins.min(0).astype(np.float32)
+    ext = float(np.max(mins + (QMAX / scales)[:, None] - fmin.astype(np.float64)[None, :]))
+    return fmin, QMAX / ext
+
+
+def child_target_r2(child_scale: float, parent_scale: float, parent_res: int) -> int:
+    """Squared radius, in the child's units, of one pixel step of the parent's raster: the
+    child prefix drawn for the parent is the shortest one reaching every child surfel
+    within that distance (Sec. 4.1)."""
+    h = (2.0**21 / parent_res) * (child_scale / parent_scale)
+    return int(h * h)
+
+
+def _splat_level(children, nodes_children, level, seed, node_ids, res, ntris, out_res: SceneResult, keep):
+    """Samples parent nodes from child outputs and orders them; returns the parents' outputs.
+
+    children: list of dicts (key, nrm, rgb, perm, rad2, m, bbox_min, scale); nodes_children:
+    per parent the indices of its children."""
+    frames = [parent_frame([children[c]["bbox_min"] for c in cs], [children[c]["scale"] for c in cs])
+              for cs in nodes_children]
+    order_c, targets = [], []
+    for k, cs in enumerate(nodes_children):
+        for c in cs:
+            order_c.append((k, c))
+            targets.append(child_target_r2(children[c]["scale"], frames[k][1], res))
+    p, r2_at = bs.prefix_for_radius_batched([children[c]["rad2"] for _, c in order_c],
+                                            [children[c]["m"] for _, c in order_c], targets)
+    sets = []
+    for (k, c), pk, rk in zip(order_c, p, r2_at):
+        ch = children[c]
+        sets.append(dict(key=ch["key"], nrm=ch["nrm"], rgb=ch["rgb"], perm=ch["perm"], n=int(pk),
+                         bbox_min=list(ch["bbox_min"]), scale=ch["scale"], r2=int(rk), node=k))
+    sv = bs.sample_splats(sets, [(f[0], f[1], res) for f in frames], W.AXIS_DIRS)
+    mc = [node_bound(t, s["n"]) for t, s in zip(ntris, sv)]
+    live = [k for k in range(len(sv)) if mc[k] > 0]
+    got = bs.order_batched([sv[k]["key"] for k in live], seeds=[seed] * len(live),
+                           part_ids=[node_ids[k] for k in live], max_counts=[mc[k] for k in live],
+                           scales=[sv[k]["scale"] for k in live])
+    outs = [None] * len(sv)
+    for k, o in zip(live, got):
+        outs[k] = dict(key=sv[k]["key"], nrm=sv[k]["nrm"], rgb=sv[k]["rgb"], perm=o[0], rad2=o[1], m=mc[k],
+                       bbox_min=sv[k]["bbox_min"], scale=sv[k]["scale"])
+    lv = out_res.per_level.setdefault(level, {"nodes": 0, "sampled": 0, "ordered": 0, "triangles": 0, "splats": 0})
+    lv["nodes"] += len(sv)
+    lv["sampled"] += sum(s["n"] for s in sv)
+    lv["ordered"] += sum(mc)
+    lv["triangles"] += sum(ntris)
+    lv["splats"] += int(np.sum(p))
+    out_res.nodes += len(sv)
+    out_res.surfels_sampled += sum(s["n"] for s in sv)
+    out_res.surfels_ordered += sum(mc)
+    out_res.triangles += sum(ntris)
+    for k, i in enumerate(node_ids):
+        if i in keep:
+            key = sv[k]["key"].cpu().numpy().view(np.uint64)
+            if outs[k] is not None:
+                out_res.kept[i] = (key, outs[k]["perm"].cpu().numpy().view(np.uint32), outs[k]["rad2"].cpu().numpy())
+            else:
+                out_res.kept[i] = (key, None, None)
+    return outs
+
+
+def run_hierarchical(seed: int = 0, lines: int = 20, per_line: int = 2500, group: int = 50, nboxes: int = 200,
+                     ncyl: int = 50, keep=(), groups_per_wave: int = 40, level_res=None) -> SceneResult:
+    """The scene of run() generated bottom-up: parts from their triangles (as in run()),
+    every group from its parts' surfel prefixes and every line from its groups' prefixes,
+    drawn as oriented discs.  A child contributes the shortest prefix of its ordering that
+    reaches all its surfels within one pixel step of the parent's raster, each surfel a
+    disc of that prefix's covering radius."""
+    import torch
+    nodes = W.scene_nodes(lines, per_line, group)
+    keep = set(keep)
+    res = SceneResult()
+    tp = _tris_per_part(nboxes, ncyl)
+    vp = _verts_per_part(nboxes, ncyl)
+    lres = {**LEVEL_RES, **(level_res or {})}
+    index = {(nd.line, nd.first, nd.count, nd.level): i for i, nd in enumerate(nodes)}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for l in range(lines):
+        groups = [(s, min(group, per_line - s)) for s in range(0, per_line, group)]
+        group_outs = []
+        for w in range(0, len(groups), groups_per_wave):
+            gw = groups[w:w + groups_per_wave]
+            slots = [s for g0, cnt in gw for s in range(g0, g0 + cnt)]
+            leaf_ids = [index[(l, s, 1, 0)] for s in slots]
+            npart = len(slots)
+            dev = torch.device("cuda")
+            xyz = torch.empty((npart * vp, 3), dtype=torch.float32, device=dev)
+            tri = torch.empty((npart * tp, 3), dtype=torch.int32, device=dev)
+            rgb = torch.empty((npart * tp, 3), dtype=torch.uint8, device=dev)
+            bs.scene_generate(seed, [(l * per_line + s, l, s) for s in slots], nboxes, ncyl, local_indices=True,
+                              out=(xyz, tri, rgb))
+            q = np.arange(npart, dtype=np.int64)
+            sv = bs.sample_visible_packed(xyz, tri, rgb, q * vp, [vp] * npart, q * tp, [tp] * npart,
+                                          lres[0], W.AXIS_DIRS)
+            del xyz, tri, rgb
+            n = sv["n"]
+            mc = np.minimum(np.minimum(NODE_BOUND, tp // 2), n)
+            perm, rad2, _, mofs = bs.order_packed(sv["key"], sv["ofs"], n, max_counts=mc, seeds=seed,
+                                                  part_ids=leaf_ids, scales=sv["scale"])
+            lv = res.per_level.setdefault(0, {"nodes": 0, "sampled": 0, "ordered": 0, "triangles": 0})
+            lv["nodes"] += npart
+            lv["sampled"] += int(n.sum())
+            lv["ordered"] += int(mc.sum())
+            lv["triangles"] += npart * tp
+            res.nodes += npart
+            res.surfels_sampled += int(n.sum())
+            res.surfels_ordered += int(mc.sum())
+            res.triangles += npart * tp
+            leaves = []
+            for j in range(npart):
+                a, b = int(sv["ofs"][j]), int(sv["ofs"][j]) + int(n[j])
+                lo, hi = int(mofs[j]), int(mofs[j + 1])
+                leaves.append(dict(key=sv["key"][a:b], nrm=sv["nrm"][a:b], rgb=sv["rgb"][a:b], perm=perm[lo:hi],
+                                   rad2=rad2[lo:hi], m=int(mc[j]), bbox_min=sv["bbox_min"][j], scale=float(sv["scale"][j])))
+                if leaf_ids[j] in keep:
+                    res.kept[leaf_ids[j]] = (leaves[j]["key"].cpu().numpy().view(np.uint64),
+                                             leaves[j]["perm"].cpu().numpy().view(np.uint32),
+                                             leaves[j]["rad2"].cpu().numpy())
+            members, j0 = [], 0
+            for g0, cnt in gw:  # parts with no surfels have nothing to draw
+                members.append([j for j in range(j0, j0 + cnt) if leaves[j]["m"] > 0])
+                j0 += cnt
+            group_ids = [index[(l, g0, cnt, 1)] for g0, cnt in gw]
+            group_outs += _splat_level(leaves, members, 1, seed, group_ids, lres[1], [cnt * tp for _, cnt in gw],
+                                       res, keep)
+        line_id = index[(l, 0, per_line, 2)]
+        group_outs = [g for g in group_outs if g is not None]
+        _splat_level(group_outs, [list(range(len(group_outs)))], 2, seed, [line_id], lres[2], [per_line * tp], res,
+                     keep)
+    torch.cuda.synchronize()
+    res.seconds = time.perf_counter() - t0
+    return res

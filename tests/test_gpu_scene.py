@@ -154,3 +154,93 @@ def test_packed_bindings_match_list_bindings(bs):
         lo, hi = int(mofs[q]), int(mofs[q + 1])
         assert torch.equal(perm[lo:hi], got[q][0]) and torch.equal(rad2[lo:hi], got[q][1])
         assert torch.equal(radius[lo:hi], got[q][2])
+
+
+# ---- bottom-up generation (groups from parts' surfels, lines from groups') ----
+
+Q = 2**21 - 1
+
+
+def _oracle_leaf(seed, idx, node, per_line, nb, nc, res):
+    m = W.scene_node_mesh(seed, node, per_line, nb, nc)
+    sv, mn, sc = oracle.sample_mesh(m, W.AXIS_DIRS, res)
+    mc = min(200_000, m.ntris // 2, len(sv["key"]))
+    st = oracle.start_index(len(sv["key"]), seed=seed, part_id=idx)
+    p, r = oracle.greedy(sv["key"], st, max_count=mc)
+    return dict(sv=sv, mn=mn, sc=sc, perm=p, rad2=r, m=mc)
+
+
+def _oracle_parent(children, seed, idx, res, ntris):
+    """A parent from its children's prefixes: the frame holding the children's cubes, each
+    child's shortest prefix reaching its surfels within one parent pixel step (Sec. 4.1),
+    its discs drawn (Sec. 3.4 / 4.2), then the exact ordering with the node bound."""
+    mins = np.array([c["mn"] for c in children], np.float64)
+    scales = np.array([c["sc"] for c in children], np.float64)
+    fmin = mins.min(0).astype(np.float32)
+    ext = float(np.max(mins + (Q / scales)[:, None] - fmin.astype(np.float64)[None, :]))
+    fs = Q / ext
+    sets = []
+    for c in children:
+        h = (2.0**21 / res) * (c["sc"] / fs)
+        p = oracle.prefix_for_radius(c["rad2"], int(h * h))
+        pi = c["perm"][:p]
+        sets.append(dict(key=c["sv"]["key"][pi], nrm=c["sv"]["nrm"][pi], rgb=c["sv"]["rgb"][pi], bbox_min=c["mn"],
+                         scale=c["sc"], r2=int(c["rad2"][min(p, c["m"] - 1)])))
+    sv = oracle.sample_splats(sets, fmin, fs, W.AXIS_DIRS, res)
+    mc = min(200_000, ntris // 2, len(sv["key"]))
+    st = oracle.start_index(len(sv["key"]), seed=seed, part_id=idx)
+    p, r = oracle.greedy(sv["key"], st, max_count=mc)
+    return dict(sv=sv, mn=fmin, sc=fs, perm=p, rad2=r, m=mc)
+
+
+def test_bottom_up_reduced_scene_every_node(bs):
+    """Every node of a 2-line scene generated bottom-up against the oracle chain (parts from
+    triangles, groups from parts' discs, lines from groups' discs)."""
+    from paper_1904_08225_gb300 import scene
+    seed, lines, per_line, group, nb, nc = 23, 2, 7, 3, 20, 5
+    level_res = {0: 96, 1: 256, 2: 1024}
+    nodes = W.scene_nodes(lines, per_line, group)
+    out = scene.run_hierarchical(seed, lines, per_line, group, nb, nc, keep=range(len(nodes)), groups_per_wave=2,
+                                 level_res=level_res)
+    assert out.nodes == len(nodes) and sorted(out.kept) == list(range(len(nodes)))
+    tp = W.BOX_TRIS * nb + W.CYL_TRIS * nc
+    ref = {}
+    for i, nd in enumerate(nodes):
+        if nd.level == 0:
+            ref[i] = _oracle_leaf(seed, i, nd, per_line, nb, nc, level_res[0])
+    for i, nd in enumerate(nodes):
+        if nd.level == 1:
+            kids = [ref[j] for j, c in enumerate(nodes) if c.level == 0 and c.line == nd.line
+                    and nd.first <= c.first < nd.first + nd.count]
+            ref[i] = _oracle_parent(kids, seed, i, level_res[1], nd.count * tp)
+    for i, nd in enumerate(nodes):
+        if nd.level == 2:
+            kids = [ref[j] for j, c in enumerate(nodes) if c.level == 1 and c.line == nd.line]
+            ref[i] = _oracle_parent(kids, seed, i, level_res[2], nd.count * tp)
+    for i, nd in enumerate(nodes):
+        key, perm, rad2 = out.kept[i]
+        assert np.array_equal(key, ref[i]["sv"]["key"]), (i, nd.level)
+        assert np.array_equal(perm, ref[i]["perm"]), (i, nd.level)
+        assert np.array_equal(rad2, ref[i]["rad2"]), (i, nd.level)
+    assert out.per_level[1]["splats"] > 0 and out.per_level[2]["splats"] > 0
+
+
+def test_prefix_for_radius_batched(bs):
+    import torch
+    g = np.random.default_rng(4)
+    rad2s, ms, r2s, want = [], [], [], []
+    for i in range(40):
+        pts = np.unique(g.integers(0, 1 << 16, size=(int(g.integers(2, 3000)), 3)), axis=0)
+        key = oracle.pack(pts)
+        m = int(g.integers(1, len(key) + 1))
+        _, r = oracle.greedy(key, 0, max_count=m)
+        r2 = int(g.choice([0, r[min(1, m - 1)], r[m // 2], r[-1], 10**12, int(g.integers(0, 1 << 30))]))
+        r2s.append(max(r2, 0))
+        ms.append(m)
+        rad2s.append(torch.from_numpy(r).cuda())
+        p = oracle.prefix_for_radius(r, r2s[-1])
+        want.append((p, int(r[min(p, m - 1)])))
+    p, at = bs.prefix_for_radius_batched(rad2s, ms, r2s)
+    assert [(int(a), int(b)) for a, b in zip(p, at)] == want
+    for i in (0, 7, 39):
+        assert bs.prefix_for_radius(rad2s[i], r2s[i]) == want[i][0]
