@@ -593,15 +593,22 @@ def scene_leg(args):
     """Scene scale: every node of a production-line scene (one per part, per group of 50
     parts and per line) regenerated on the device, sampled from the 6 axis directions and
     ordered with the min(200k, triangles / 2) bound; end-to-end wall time of the whole scene
-    (one run, after a one-line warm-up)."""
+    (one run, after a one-line warm-up), from triangles at every level and bottom-up."""
     from paper_1904_08225_gb300 import scene
     scene.run(args.seed, lines=1, per_line=min(args.scene_per_line, 100))
     r = scene.run(args.seed, lines=args.scene_lines, per_line=args.scene_per_line)
-    return {"lines": args.scene_lines, "parts": args.scene_lines * args.scene_per_line, "nodes": r.nodes,
-            "triangles": r.triangles, "surfels_sampled": r.surfels_sampled, "surfels_ordered": r.surfels_ordered,
-            "seconds": r.seconds, "ordered_per_s": r.surfels_ordered / r.seconds,
-            "per_level": {str(k): v for k, v in sorted(r.per_level.items())},
-            "level_res": scene.LEVEL_RES, "dirs": "6 axis"}
+    out = {"lines": args.scene_lines, "parts": args.scene_lines * args.scene_per_line, "nodes": r.nodes,
+           "triangles": r.triangles, "surfels_sampled": r.surfels_sampled, "surfels_ordered": r.surfels_ordered,
+           "seconds": r.seconds, "ordered_per_s": r.surfels_ordered / r.seconds,
+           "per_level": {str(k): v for k, v in sorted(r.per_level.items())},
+           "level_res": scene.LEVEL_RES, "dirs": "6 axis"}
+    # bottom-up: groups from their parts' surfel discs, lines from their groups' (Sec. 3.4)
+    scene.run_hierarchical(args.seed, lines=1, per_line=min(args.scene_per_line, 100))
+    h = scene.run_hierarchical(args.seed, lines=args.scene_lines, per_line=args.scene_per_line)
+    out["bottom_up"] = {"nodes": h.nodes, "seconds": h.seconds, "surfels_sampled": h.surfels_sampled,
+                        "surfels_ordered": h.surfels_ordered,
+                        "per_level": {str(k): v for k, v in sorted(h.per_level.items())}}
+    return out
 
 
 def table2_leg(bs, timed):

@@ -216,12 +216,14 @@ def _splat_level(children, nodes_children, level, seed, node_ids, res, ntris, ou
 
 
 def run_hierarchical(seed: int = 0, lines: int = 20, per_line: int = 2500, group: int = 50, nboxes: int = 200,
-                     ncyl: int = 50, keep=(), groups_per_wave: int = 40, level_res=None) -> SceneResult:
+                     ncyl: int = 50, keep=(), groups_per_wave: int = 25, level_res=None) -> SceneResult:
     """The scene of run() generated bottom-up: parts from their triangles (as in run()),
     every group from its parts' surfel prefixes and every line from its groups' prefixes,
     drawn as oriented discs.  A child contributes the shortest prefix of its ordering that
     reaches all its surfels within one pixel step of the parent's raster, each surfel a
-    disc of that prefix's covering radius."""
+    disc of that prefix's covering radius.  Waves of parts alternate between two streams:
+    a wave's parts are ordered while the next wave's parts are generated and sampled, and
+    its groups are drawn while the next wave's parts are ordered."""
     import torch
     nodes = W.scene_nodes(lines, per_line, group)
     keep = set(keep)
@@ -230,60 +232,96 @@ def run_hierarchical(seed: int = 0, lines: int = 20, per_line: int = 2500, group
     vp = _verts_per_part(nboxes, ncyl)
     lres = {**LEVEL_RES, **(level_res or {})}
     index = {(nd.line, nd.first, nd.count, nd.level): i for i, nd in enumerate(nodes)}
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for st in streams:
+        st.wait_stream(torch.cuda.current_stream())
+    waves = []
+    for l in range(lines):
+        groups = [(s0, min(group, per_line - s0)) for s0 in range(0, per_line, group)]
+        for w in range(0, len(groups), groups_per_wave):
+            waves.append((l, groups[w:w + groups_per_wave]))
+    waves_left = {l: sum(1 for wl, _ in waves if wl == l) for l in range(lines)}
+    line_groups = {l: [] for l in range(lines)}
+
+    def leaf_stage(l, gw):
+        """Parts of the wave from triangles: generated, sampled (returns once sampled) and
+        ordered (left running on the current stream)."""
+        slots = [s0 for g0, cnt in gw for s0 in range(g0, g0 + cnt)]
+        leaf_ids = [index[(l, s0, 1, 0)] for s0 in slots]
+        npart = len(slots)
+        dev = torch.device("cuda")
+        xyz = torch.empty((npart * vp, 3), dtype=torch.float32, device=dev)
+        tri = torch.empty((npart * tp, 3), dtype=torch.int32, device=dev)
+        rgb = torch.empty((npart * tp, 3), dtype=torch.uint8, device=dev)
+        bs.scene_generate(seed, [(l * per_line + s0, l, s0) for s0 in slots], nboxes, ncyl, local_indices=True,
+                          out=(xyz, tri, rgb))
+        q = np.arange(npart, dtype=np.int64)
+        sv = bs.sample_visible_packed(xyz, tri, rgb, q * vp, [vp] * npart, q * tp, [tp] * npart, lres[0],
+                                      W.AXIS_DIRS)
+        del xyz, tri, rgb
+        n = sv["n"]
+        mc = np.minimum(np.minimum(NODE_BOUND, tp // 2), n)
+        perm, rad2, _, mofs = bs.order_packed(sv["key"], sv["ofs"], n, max_counts=mc, seeds=seed,
+                                              part_ids=leaf_ids, scales=sv["scale"])
+        lv = res.per_level.setdefault(0, {"nodes": 0, "sampled": 0, "ordered": 0, "triangles": 0})
+        lv["nodes"] += npart
+        lv["sampled"] += int(n.sum())
+        lv["ordered"] += int(mc.sum())
+        lv["triangles"] += npart * tp
+        res.nodes += npart
+        res.surfels_sampled += int(n.sum())
+        res.surfels_ordered += int(mc.sum())
+        res.triangles += npart * tp
+        leaves = []
+        for j in range(npart):
+            a, b = int(sv["ofs"][j]), int(sv["ofs"][j]) + int(n[j])
+            lo, hi = int(mofs[j]), int(mofs[j + 1])
+            leaves.append(dict(key=sv["key"][a:b], nrm=sv["nrm"][a:b], rgb=sv["rgb"][a:b], perm=perm[lo:hi],
+                               rad2=rad2[lo:hi], m=int(mc[j]), bbox_min=sv["bbox_min"][j], scale=float(sv["scale"][j])))
+        return dict(l=l, gw=gw, leaves=leaves, leaf_ids=leaf_ids, stream=torch.cuda.current_stream())
+
+    def group_stage(wv):
+        """Groups of a wave from its parts' discs; the line once all its groups exist."""
+        l, gw, leaves = wv["l"], wv["gw"], wv["leaves"]
+        for j, i in enumerate(wv["leaf_ids"]):
+            if i in keep:
+                res.kept[i] = (leaves[j]["key"].cpu().numpy().view(np.uint64),
+                               leaves[j]["perm"].cpu().numpy().view(np.uint32), leaves[j]["rad2"].cpu().numpy())
+        members, j0 = [], 0
+        for g0, cnt in gw:  # parts with no surfels have nothing to draw
+            members.append([j for j in range(j0, j0 + cnt) if leaves[j]["m"] > 0])
+            j0 += cnt
+        group_ids = [index[(l, g0, cnt, 1)] for g0, cnt in gw]
+        line_groups[l] += _splat_level(leaves, members, 1, seed, group_ids, lres[1], [cnt * tp for _, cnt in gw],
+                                       res, keep)
+        waves_left[l] -= 1
+        if waves_left[l] == 0:
+            kids = [g for g in line_groups.pop(l) if g is not None]
+            # the line's groups were ordered on both streams: wait for them, and keep their
+            # memory from being reused before this stream is done with it
+            cur = torch.cuda.current_stream()
+            for st in streams:
+                if st != cur:
+                    cur.wait_stream(st)
+            for g in kids:
+                for f in ("key", "nrm", "rgb", "perm", "rad2"):
+                    g[f].record_stream(cur)
+            _splat_level(kids, [list(range(len(kids)))], 2, seed, [index[(l, 0, per_line, 2)]], lres[2],
+                         [per_line * tp], res, keep)
+
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for l in range(lines):
-        groups = [(s, min(group, per_line - s)) for s in range(0, per_line, group)]
-        group_outs = []
-        for w in range(0, len(groups), groups_per_wave):
-            gw = groups[w:w + groups_per_wave]
-            slots = [s for g0, cnt in gw for s in range(g0, g0 + cnt)]
-            leaf_ids = [index[(l, s, 1, 0)] for s in slots]
-            npart = len(slots)
-            dev = torch.device("cuda")
-            xyz = torch.empty((npart * vp, 3), dtype=torch.float32, device=dev)
-            tri = torch.empty((npart * tp, 3), dtype=torch.int32, device=dev)
-            rgb = torch.empty((npart * tp, 3), dtype=torch.uint8, device=dev)
-            bs.scene_generate(seed, [(l * per_line + s, l, s) for s in slots], nboxes, ncyl, local_indices=True,
-                              out=(xyz, tri, rgb))
-            q = np.arange(npart, dtype=np.int64)
-            sv = bs.sample_visible_packed(xyz, tri, rgb, q * vp, [vp] * npart, q * tp, [tp] * npart,
-                                          lres[0], W.AXIS_DIRS)
-            del xyz, tri, rgb
-            n = sv["n"]
-            mc = np.minimum(np.minimum(NODE_BOUND, tp // 2), n)
-            perm, rad2, _, mofs = bs.order_packed(sv["key"], sv["ofs"], n, max_counts=mc, seeds=seed,
-                                                  part_ids=leaf_ids, scales=sv["scale"])
-            lv = res.per_level.setdefault(0, {"nodes": 0, "sampled": 0, "ordered": 0, "triangles": 0})
-            lv["nodes"] += npart
-            lv["sampled"] += int(n.sum())
-            lv["ordered"] += int(mc.sum())
-            lv["triangles"] += npart * tp
-            res.nodes += npart
-            res.surfels_sampled += int(n.sum())
-            res.surfels_ordered += int(mc.sum())
-            res.triangles += npart * tp
-            leaves = []
-            for j in range(npart):
-                a, b = int(sv["ofs"][j]), int(sv["ofs"][j]) + int(n[j])
-                lo, hi = int(mofs[j]), int(mofs[j + 1])
-                leaves.append(dict(key=sv["key"][a:b], nrm=sv["nrm"][a:b], rgb=sv["rgb"][a:b], perm=perm[lo:hi],
-                                   rad2=rad2[lo:hi], m=int(mc[j]), bbox_min=sv["bbox_min"][j], scale=float(sv["scale"][j])))
-                if leaf_ids[j] in keep:
-                    res.kept[leaf_ids[j]] = (leaves[j]["key"].cpu().numpy().view(np.uint64),
-                                             leaves[j]["perm"].cpu().numpy().view(np.uint32),
-                                             leaves[j]["rad2"].cpu().numpy())
-            members, j0 = [], 0
-            for g0, cnt in gw:  # parts with no surfels have nothing to draw
-                members.append([j for j in range(j0, j0 + cnt) if leaves[j]["m"] > 0])
-                j0 += cnt
-            group_ids = [index[(l, g0, cnt, 1)] for g0, cnt in gw]
-            group_outs += _splat_level(leaves, members, 1, seed, group_ids, lres[1], [cnt * tp for _, cnt in gw],
-                                       res, keep)
-        line_id = index[(l, 0, per_line, 2)]
-        group_outs = [g for g in group_outs if g is not None]
-        _splat_level(group_outs, [list(range(len(group_outs)))], 2, seed, [line_id], lres[2], [per_line * tp], res,
-                     keep)
+    pending = None
+    for w, (l, gw) in enumerate(waves):
+        with torch.cuda.stream(streams[w % 2]):
+            cur = leaf_stage(l, gw)
+        if pending is not None:
+            with torch.cuda.stream(pending["stream"]):
+                group_stage(pending)
+        pending = cur
+    if pending is not None:
+        with torch.cuda.stream(pending["stream"]):
+            group_stage(pending)
     torch.cuda.synchronize()
     res.seconds = time.perf_counter() - t0
     return res
