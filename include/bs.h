@@ -184,6 +184,26 @@ typedef struct {
 bs_status bs_sample_splats(const bs_splat_set *sets, int nsets, const bs_splat_node *nodes, int nnodes,
                            const bs_dir *dirs, int ndirs, bs_surfels *out, void *cuda_stream);
 
+/* ---- Headless renders for image-space coverage checks (Sec. 4.1's claim that the
+ * prefix of length p(r), drawn as discs of radius r, covers every pixel of the object;
+ * the discs of Sec. 4.2).  No window or graphics API: the image is a device buffer. ---- */
+
+/* bs_render_mesh -- the depth pass of bs_sample_visible for one direction: image (DEVICE,
+ * res x res uint64, row py at py * res) receives depth << 32 | triangle index of the
+ * nearest triangle covering each pixel centre, all ones where none does, in the mesh's
+ * own frame (the frame bs_sample_visible reports).  Errors as bs_sample_visible.
+ * Synchronises the stream. */
+bs_status bs_render_mesh(const bs_mesh *mesh, const bs_dir *dir, int res, unsigned long long *image,
+                         void *cuda_stream);
+
+/* bs_render_splats -- the depth pass of bs_sample_splats for one node and one axis
+ * direction: image (DEVICE, node->res^2 uint64) receives depth << 32 | global splat index
+ * of the nearest disc covering each pixel centre, all ones where none does.  sets' node
+ * fields are ignored.  BS_EINVAL for a non-axis direction or a bad node.  Stream-ordered
+ * (returns after enqueueing). */
+bs_status bs_render_splats(const bs_splat_set *sets, int nsets, const bs_splat_node *node, const bs_dir *dir,
+                           unsigned long long *image, void *cuda_stream);
+
 /* bs_order -- progressive ordering of one part (Sec. 3.2 goal; Sec. 4.1 radius).
  * Computes the exact greedy permutation (farthest-first traversal) of the
  * points s->key[0..n): perm[0] is the start index; perm[k] (k >= 1) is the

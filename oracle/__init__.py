@@ -72,6 +72,8 @@ def _load():
             lib.or_sample_splats.argtypes = [C.c_uint64, P, P, P, C.c_int, P, P, P, P, P, C.c_double, P, C.c_int,
                                              C.c_int, P, P, P, P, C.c_uint64]
             lib.or_sample_splats.restype = C.c_int64
+            lib.or_render_splats.argtypes = [C.c_uint64, P, P, C.c_int, P, P, P, P, P, C.c_double, P, C.c_int, P]
+            lib.or_render_splats.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -198,6 +200,27 @@ def sample_splats(sets, frame_min, frame_scale: float, dirs, res: int):
     c2 = lib.or_sample_splats(*args, _p(key), _p(nrm), _p(col), _p(src), cnt)
     assert c2 == cnt
     return dict(key=key, nrm=nrm, rgb=col, src=src)
+
+
+def render_splats(sets, frame_min, frame_scale: float, d, res: int) -> np.ndarray:
+    """Headless image of discs for one axis direction (the depth pass of sample_splats):
+    (res, res) u64 of depth << 32 | global splat index, all ones where no disc lands."""
+    lib = _load()
+    keys = [np.ascontiguousarray(st["key"], dtype=np.uint64) for st in sets]
+    ofs = np.concatenate([[0], np.cumsum([len(k) for k in keys])]).astype(np.uint64)
+    skey = np.ascontiguousarray(np.concatenate(keys) if keys else np.zeros(0, np.uint64), dtype=np.uint64)
+    snrm = np.ascontiguousarray(np.concatenate([np.asarray(st["nrm"], np.int16).reshape(-1, 3) for st in sets])
+                                if sets else np.zeros((0, 3), np.int16), dtype=np.int16)
+    bmin = np.ascontiguousarray(np.array([st["bbox_min"] for st in sets], np.float32).reshape(-1))
+    scale = np.ascontiguousarray([float(st["scale"]) for st in sets], dtype=np.float64)
+    r2 = np.ascontiguousarray([int(st["r2"]) for st in sets], dtype=np.int64)
+    fmin = np.ascontiguousarray(frame_min, dtype=np.float32)
+    dd = np.ascontiguousarray(d, dtype=np.int8).reshape(3)
+    depth = np.zeros((res, res), np.uint64)
+    if lib.or_render_splats(len(skey), _p(skey), _p(snrm), len(sets), _p(ofs), _p(bmin), _p(scale), _p(r2), _p(fmin),
+                            float(frame_scale), _p(dd), res, _p(depth)) != 0:
+        raise ValueError("or_render_splats: bad arguments")
+    return depth
 
 
 def start_index(n: int, seed: int = 0, part_id: int = 0, start: int = -1) -> int:

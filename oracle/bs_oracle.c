@@ -538,6 +538,28 @@ static void splat_resolve(const or_view *vw, const or_splat *sp, const int16_t n
     r->morton = or_morton3((uint32_t)pos[0], (uint32_t)pos[1], (uint32_t)pos[2]);
 }
 
+/* Headless render of discs for one axis direction: depth[py * res + px] gets the   */
+/* smallest (depth << 32 | global splat index) of the discs covering the pixel, or  */
+/* all ones (the depth pass of or_sample_splats on its own).  Returns 0, or -1.      */
+int or_render_splats(uint64_t nsplat, const uint64_t *skey, const int16_t *snrm, int nsets, const uint64_t *set_ofs,
+                     const float *bmin, const double *scale, const int64_t *r2, const float fmin[3], double fscale,
+                     const int8_t dir[3], int res, uint64_t *depth)
+{
+    if (res < 1 || res > 4096 || nsets < 0 || nsplat >= 0xFFFFFFFFull) return -1;
+    if ((dir[0] != 0) + (dir[1] != 0) + (dir[2] != 0) != 1) return -1;
+    if (set_ofs[0] != 0 || set_ofs[nsets] != nsplat) return -1;
+    or_view vw;
+    make_view(dir, res, &vw);
+    for (uint64_t i = 0; i < (uint64_t)res * res; i++) depth[i] = ~(uint64_t)0;
+    for (int i = 0; i < nsets; i++)
+        for (uint64_t g = set_ofs[i]; g < set_ofs[i + 1]; g++) {
+            or_splat sp;
+            splat_to_parent(skey[g], bmin + 3 * i, scale[i], r2[i], fmin, fscale, &sp);
+            splat_dir(&vw, &sp, snrm + 3 * g, (uint32_t)g, depth);
+        }
+    return 0;
+}
+
 /* Splat sampling of one parent node.  Splats are concatenated over nsets   */
 /* sets; set i holds splats [set_ofs[i], set_ofs[i+1]) with frame bmin[3i..],  */
 /* scale[i] and squared radius r2[i].  The parent frame is (fmin, fscale).    */

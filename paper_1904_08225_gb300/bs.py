@@ -25,7 +25,7 @@ INT64_MAX = (1 << 63) - 1
 EXPORTS = ["bs_sample_visible", "bs_sample_visible_batched", "bs_order", "bs_order_noalloc", "bs_order_batched", "bs_server_create", "bs_server_submit",
            "bs_server_poll", "bs_server_times", "bs_server_destroy", "bs_set_tuning", "bs_last_launch_ms",
            "bs_prefix_median_nn", "bs_prefix_for_radius", "bs_prefix_estimate", "bs_scene_generate", "bs_sample_splats",
-           "bs_prefix_for_radius_batched",
+           "bs_prefix_for_radius_batched", "bs_render_mesh", "bs_render_splats",
            "bs_last_error"]
 
 
@@ -86,6 +86,8 @@ def load(build_if_stale: bool = True) -> C.CDLL:
             lib.bs_sample_visible_batched.argtypes = [C.POINTER(Mesh), C.POINTER(C.c_int), C.c_int, C.POINTER(Dir),
                                                       C.c_int, C.POINTER(Surfels), P]
             lib.bs_prefix_for_radius_batched.argtypes = [P, P, P, C.c_int, P, P, P]
+            lib.bs_render_mesh.argtypes = [C.POINTER(Mesh), C.POINTER(Dir), C.c_int, P, P]
+            lib.bs_render_splats.argtypes = [C.POINTER(SplatSet), C.c_int, C.POINTER(SplatNode), C.POINTER(Dir), P, P]
             lib.bs_sample_splats.argtypes = [C.POINTER(SplatSet), C.c_int, C.POINTER(SplatNode), C.c_int,
                                              C.POINTER(Dir), C.c_int, C.POINTER(Surfels), P]
             lib.bs_order.argtypes = [C.POINTER(Surfels), C.POINTER(OrderOpts), P, P, P, P]
@@ -347,6 +349,42 @@ def sample_splats(sets, nodes, dirs, caps=None, stream=None):
         out.append(dict(key=key[o:o + n], nrm=nrm[o:o + n], rgb=col[o:o + n], src=src[o:o + n], n=n,
                         bbox_min=onp["bbox_min"][i].copy(), scale=float(onp["scale"][i])))
     return out
+
+
+def render_mesh(xyz, tri, d, res: int, stream=None):
+    """bs_render_mesh: (res, res) CUDA int64 image (uint64 bits) of depth << 32 | triangle."""
+    torch = _torch()
+    lib = load()
+    xyz, tri = xyz.contiguous(), tri.contiguous()
+    m = Mesh(xyz.data_ptr(), xyz.shape[0], tri.data_ptr() if tri.numel() else None, tri.shape[0], None)
+    img = torch.empty((res, res), dtype=torch.int64, device=xyz.device)
+    dd = Dir(*[int(x) for x in d])
+    _check(lib.bs_render_mesh(C.byref(m), C.byref(dd), int(res), C.c_void_p(img.data_ptr()), _stream(stream)),
+           "bs_render_mesh")
+    return img
+
+
+def render_splats(sets, node, d, stream=None):
+    """bs_render_splats: (res, res) CUDA int64 image (uint64 bits) of depth << 32 | splat.
+
+    sets as for sample_splats (node fields ignored); node = (frame_min, scale, res)."""
+    torch = _torch()
+    lib = load()
+    S = len(sets)
+    sarr = (SplatSet * max(S, 1))()
+    for i, st in enumerate(sets):
+        sarr[i] = SplatSet(st["key"].data_ptr(), st["nrm"].data_ptr(),
+                           st["rgb"].data_ptr() if st.get("rgb") is not None else None,
+                           st["perm"].data_ptr() if st.get("perm") is not None else None,
+                           int(st["n"]), (C.c_float * 3)(*[float(x) for x in st["bbox_min"]]), float(st["scale"]),
+                           int(st["r2"]), 0)
+    fm, sc, res = node
+    nd = SplatNode((C.c_float * 3)(*[float(x) for x in fm]), float(sc), int(res))
+    img = torch.empty((res, res), dtype=torch.int64, device=sets[0]["key"].device if sets else torch.device("cuda"))
+    dd = Dir(*[int(x) for x in d])
+    _check(lib.bs_render_splats(sarr, S, C.byref(nd), C.byref(dd), C.c_void_p(img.data_ptr()), _stream(stream)),
+           "bs_render_splats")
+    return img
 
 
 def _np_dtype(ct) -> np.dtype:

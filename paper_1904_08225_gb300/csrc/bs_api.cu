@@ -167,6 +167,17 @@ bs_status bs_scene_generate(uint64_t seed, const uint64_t *part_ids, const int32
                           local_indices, xyz, tri, rgb, (cudaStream_t)cuda_stream);
 }
 
+bs_status bs_render_mesh(const bs_mesh *mesh, const bs_dir *dir, int res, unsigned long long *image, void *cuda_stream) {
+    clear_error();
+    return render_mesh(mesh, dir, res, image, (cudaStream_t)cuda_stream);
+}
+
+bs_status bs_render_splats(const bs_splat_set *sets, int nsets, const bs_splat_node *node, const bs_dir *dir,
+                           unsigned long long *image, void *cuda_stream) {
+    clear_error();
+    return render_splats(sets, nsets, node, dir, image, (cudaStream_t)cuda_stream);
+}
+
 bs_status bs_sample_splats(const bs_splat_set *sets, int nsets, const bs_splat_node *nodes, int nnodes,
                            const bs_dir *dirs, int ndirs, bs_surfels *out, void *cuda_stream) {
     clear_error();

@@ -150,10 +150,13 @@ void order_set_algo(int algo);
 bs_status order_last_launch_ms(int which, double *ms);
 bs_status sample_visible(const bs_mesh *mesh, const bs_dir *dirs, int ndirs, int res, bs_surfels *out,
                          cudaStream_t stream);
+bs_status render_mesh(const bs_mesh *mesh, const bs_dir *dir, int res, unsigned long long *image, cudaStream_t stream);
+bs_status render_splats(const bs_splat_set *sets, int nsets, const bs_splat_node *node, const bs_dir *dir,
+                        unsigned long long *image, cudaStream_t stream);
 bs_status sample_splats(const bs_splat_set *sets, int nsets, const bs_splat_node *nodes, int nnodes, const bs_dir *dirs,
                         int ndirs, bs_surfels *out, cudaStream_t stream);
 bs_status sample_visible_parts(const bs_mesh *meshes, const int *res, int nparts, const bs_dir *dirs, int ndirs,
-                               bs_surfels *out, cudaStream_t stream);
+                               bs_surfels *out, cudaStream_t stream, unsigned long long *image = nullptr);
 
 // ---- warp reductions ----
 __device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {

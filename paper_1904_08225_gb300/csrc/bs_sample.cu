@@ -933,7 +933,7 @@ static bs_status finish_parts(int nparts, SState *d_st, std::vector<SState> &hs,
 }
 
 bs_status sample_visible_parts(const bs_mesh *meshes, const int *res, int nparts, const bs_dir *dirs, int ndirs,
-                               bs_surfels *out, cudaStream_t stream) {
+                               bs_surfels *out, cudaStream_t stream, unsigned long long *image) {
     if (nparts < 1 || nparts > 65535) { set_error("bs_sample_visible: nparts=%d outside [1, 65535]", nparts); return BS_EINVAL; }
     if (!meshes || !res || !dirs || !out) { set_error("bs_sample_visible: NULL argument"); return BS_EINVAL; }
     if (ndirs < 1 || ndirs > BS_MAX_DIRS) { set_error("bs_sample_visible: ndirs=%d outside [1,%d]", ndirs, BS_MAX_DIRS); return BS_EINVAL; }
@@ -989,7 +989,7 @@ bs_status sample_visible_parts(const bs_mesh *meshes, const int *res, int nparts
         probe.take((size_t)nparts * 8);
         probe.take(3 * V * sizeof(int32_t));
         probe.take((size_t)ndirs * T * sizeof(TriSetup));
-        probe.take(NP * sizeof(unsigned long long));
+        if (!image) probe.take(NP * sizeof(unsigned long long));
         probe.take(((size_t)ptiles + 1) * 4);
         probe.take(scan_tmp_words(ptiles) * 4);
         probe.take(16);
@@ -1004,7 +1004,8 @@ bs_status sample_visible_parts(const bs_mesh *meshes, const int *res, int nparts
     uint64_t *d_cofs = (uint64_t *)A.take((size_t)nparts * 8);
     int32_t *q = (int32_t *)A.take(3 * V * sizeof(int32_t));
     TriSetup *setup = (TriSetup *)A.take((size_t)ndirs * T * sizeof(TriSetup));
-    unsigned long long *depth = (unsigned long long *)A.take(NP * sizeof(unsigned long long));
+    // the depth buffer: the caller's image when only the depth pass is wanted
+    unsigned long long *depth = image ? image : (unsigned long long *)A.take(NP * sizeof(unsigned long long));
     uint32_t *bc = (uint32_t *)A.take(((size_t)ptiles + 1) * 4);
     uint32_t *stmp = (uint32_t *)A.take(scan_tmp_words(ptiles) * 4);
     uint32_t *tot = (uint32_t *)A.take(16);
@@ -1032,6 +1033,10 @@ bs_status sample_visible_parts(const bs_mesh *meshes, const int *res, int nparts
             dim3 gr((unsigned)std::min<uint64_t>((T + 255) / 256, (uint64_t)sms * 16), ndirs);
             k_raster<<<gr, 256, 0, stream>>>(d_parts, T, setup, depth);
         }
+        if (image) {  // depth pass only: report the part's state, no surfels
+            rc = finish_parts(nparts, d_st, hs, out, stream, "bs_render_mesh");
+            break;
+        }
         k_cover_count<<<ptiles, 256, 0, stream>>>(depth, NP, bc);
         scan_excl(bc, ptiles, tot, stmp, stream);
         if (cudaGetLastError() != cudaSuccess ||
@@ -1056,7 +1061,7 @@ bs_status sample_visible_parts(const bs_mesh *meshes, const int *res, int nparts
 bs_status sample_visible(const bs_mesh *mesh, const bs_dir *dirs, int ndirs, int res, bs_surfels *out,
                          cudaStream_t stream) {
     if (!mesh || !dirs || !out) { set_error("bs_sample_visible: NULL argument"); return BS_EINVAL; }
-    return sample_visible_parts(mesh, &res, 1, dirs, ndirs, out, stream);
+    return sample_visible_parts(mesh, &res, 1, dirs, ndirs, out, stream, nullptr);
 }
 
 
@@ -1430,6 +1435,96 @@ bs_status sample_splats(const bs_splat_set *sets, int nsets, const bs_splat_node
         rc = finish_parts(nnodes, d_st, hs, out, stream, who);
     } while (0);
     if (B) cudaFreeAsync(B, stream);
+    cudaFreeAsync(A.base, stream);
+    return rc;
+}
+
+// Headless render of a mesh for one direction: the depth pass of bs_sample_visible alone.
+bs_status render_mesh(const bs_mesh *mesh, const bs_dir *dir, int res, unsigned long long *image, cudaStream_t stream) {
+    if (!mesh || !dir || !image) { set_error("bs_render_mesh: NULL argument"); return BS_EINVAL; }
+    bs_surfels out;
+    memset(&out, 0, sizeof(out));
+    return sample_visible_parts(mesh, &res, 1, dir, 1, &out, stream, image);
+}
+
+// Headless render of discs for one axis direction: the depth pass of bs_sample_splats
+// alone, into the caller's res x res image.
+bs_status render_splats(const bs_splat_set *sets, int nsets, const bs_splat_node *node, const bs_dir *dir,
+                        unsigned long long *image, cudaStream_t stream) {
+    const char *who = "bs_render_splats";
+    if ((nsets > 0 && !sets) || nsets < 0 || !node || !dir || !image) { set_error("%s: NULL or bad argument", who); return BS_EINVAL; }
+    const int nz = (dir->x != 0) + (dir->y != 0) + (dir->z != 0);
+    if (nz != 1 || dir->x < -1 || dir->x > 1 || dir->y < -1 || dir->y > 1 || dir->z < -1 || dir->z > 1) {
+        set_error("%s: not an axis direction", who);
+        return BS_EINVAL;
+    }
+    if (node->res < 1 || node->res > BS_MAX_RES || !(node->scale > 0.0) || !std::isfinite(node->scale)) {
+        set_error("%s: bad node resolution or scale", who);
+        return BS_EINVAL;
+    }
+    Views views;
+    views.ndirs = 1;
+    make_frame(*dir, views.v[0]);
+    SPart hp;
+    memset(&hp, 0, sizeof(hp));
+    hp.res = node->res;
+    SState hs;
+    memset(&hs, 0, sizeof(hs));
+    for (int a = 0; a < 3; ++a) hs.mn[a] = node->frame_min[a];
+    hs.scale = node->scale;
+    std::vector<SSet> hsets((size_t)std::max(nsets, 1));
+    std::vector<uint64_t> sofs((size_t)std::max(nsets, 1));
+    uint64_t S = 0;
+    for (int i = 0; i < nsets; ++i) {
+        const bs_splat_set &T = sets[i];
+        if (T.n > 0 && (!T.key || !T.nrm)) { set_error("%s: set %d: NULL key or normal array", who, i); return BS_EINVAL; }
+        if (T.r2 < 0 || !(T.scale > 0.0) || !std::isfinite(T.scale)) { set_error("%s: set %d: bad radius or scale", who, i); return BS_EINVAL; }
+        SSet &D = hsets[(size_t)i];
+        D.key = T.key; D.nrm = T.nrm; D.rgb = T.rgb; D.perm = T.perm;
+        for (int a = 0; a < 3; ++a) D.bmin[a] = T.bbox_min[a];
+        D.node = 0; D.scale = T.scale; D.r2 = T.r2;
+        sofs[(size_t)i] = S;
+        S += T.n;
+        if (S >= 0xFFFFFFFFull) { set_error("%s: more than 2^32 - 1 splats", who); return BS_EINVAL; }
+    }
+    const uint64_t npix = (uint64_t)node->res * node->res;
+    int sms = 152, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    Scratch A;
+    {
+        Scratch probe;
+        probe.take(sizeof(SPart));
+        probe.take(sizeof(SState));
+        probe.take(hsets.size() * sizeof(SSet));
+        probe.take(sofs.size() * 8);
+        probe.take((size_t)std::max<uint64_t>(S, 1) * sizeof(Splat));
+        bs_status rc = alloc_async(&A.base, probe.off, stream, "splat render");
+        if (rc != BS_OK) return rc;
+    }
+    SPart *d_parts = (SPart *)A.take(sizeof(SPart));
+    SState *d_st = (SState *)A.take(sizeof(SState));
+    SSet *d_sets = (SSet *)A.take(hsets.size() * sizeof(SSet));
+    uint64_t *d_sofs = (uint64_t *)A.take(sofs.size() * 8);
+    Splat *d_splats = (Splat *)A.take((size_t)std::max<uint64_t>(S, 1) * sizeof(Splat));
+    bs_status rc = BS_OK;
+    if (cudaMemcpyAsync(d_parts, &hp, sizeof(SPart), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+        cudaMemcpyAsync(d_st, &hs, sizeof(SState), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+        cudaMemcpyAsync(d_sets, hsets.data(), hsets.size() * sizeof(SSet), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+        cudaMemcpyAsync(d_sofs, sofs.data(), sofs.size() * 8, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+        cudaMemsetAsync(image, 0xff, npix * sizeof(unsigned long long), stream) != cudaSuccess) {
+        set_error("%s: upload failed: %s", who, cudaGetErrorString(cudaGetLastError()));
+        rc = BS_ECUDA;
+    } else if (S > 0) {
+        k_splat_setup<<<(unsigned)std::min<uint64_t>((S + 255) / 256, (uint64_t)sms * 32), 256, 0, stream>>>(
+            d_sets, d_sofs, nsets, S, d_st, d_splats);
+        dim3 gr((unsigned)std::min<uint64_t>((S + 255) / 256, (uint64_t)sms * 16), 1);
+        k_splat_raster<<<gr, 256, 0, stream>>>(d_parts, S, d_splats, views, image);
+        if (cudaGetLastError() != cudaSuccess) {
+            set_error("%s: launch failed", who);
+            rc = BS_ECUDA;
+        }
+    }
     cudaFreeAsync(A.base, stream);
     return rc;
 }
