@@ -244,9 +244,10 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip plain / served / cpu baseline legs")
     ap.add_argument("--scene-lines", type=int, default=20, help="production lines of the scene leg (0 skips it)")
     ap.add_argument("--scene-per-line", type=int, default=2500)
-    ap.add_argument("--lead-min", type=int, default=150_000,
-                    help="parts of at least this many surfels are sampled first and ordered on a second stream "
-                         "(0 = one sample call and one order call for all parts)")
+    ap.add_argument("--lead-min", type=int, nargs="+", default=[350_000, 150_000],
+                    help="surfel-count thresholds, largest first: the parts of at least each threshold (and below "
+                         "the previous one) are sampled and then ordered on a stream of their own, largest group "
+                         "first, before the rest (0 = one sample call and one order call for all parts)")
     ap.add_argument("--tune", action="append", default=[], metavar="KNOB=VALUE",
                     help="bs_set_tuning launch-shape knob for the run (repeatable)")
     args = ap.parse_args()
@@ -338,8 +339,12 @@ def main():
     # longest single chain) are sampled first and ordered on a second stream while the
     # others are sampled and ordered on the main stream.  Every part is sampled and
     # ordered exactly once per step; both streams join the main stream at the end.
-    lead = [i for i in range(P) if args.lead_min > 0 and ns[i] >= args.lead_min]
-    rest = [i for i in range(P) if not (args.lead_min > 0 and ns[i] >= args.lead_min)]
+    thresholds = sorted([t for t in args.lead_min if t > 0], reverse=True)
+    bounds = [float("inf")] + thresholds
+    leads = [[i for i in range(P) if bounds[j + 1] <= ns[i] < bounds[j]] for j in range(len(thresholds))]
+    lead = [i for grp in leads for i in grp]
+    lead_set = set(lead)
+    rest = [i for i in range(P) if i not in lead_set]
 
     def subset(idx):
         k = len(idx)
@@ -350,9 +355,9 @@ def main():
                     opts=(bs.OrderOpts * k)(*[opts[i] for i in idx]),
                     pp=(C.c_void_p * k)(*[pp[i] for i in idx]), rp=(C.c_void_p * k)(*[rp[i] for i in idx]),
                     fp=(C.c_void_p * k)(*[fp[i] for i in idx]))
-    sub_lead, sub_rest = subset(lead), subset(rest)
-    lead_stream = torch.cuda.Stream(device=dev)
-    cs_lead = C.c_void_p(lead_stream.cuda_stream)
+    sub_leads, sub_rest = [subset(grp) for grp in leads], subset(rest)
+    lead_streams = [torch.cuda.Stream(device=dev) for _ in leads]
+    cs_leads = [C.c_void_p(st_.cuda_stream) for st_ in lead_streams]
 
     marks = {}
 
@@ -372,13 +377,17 @@ def main():
     def step():
         marks["start"] = torch.cuda.Event(enable_timing=True)
         marks["start"].record(stream)
-        lead_stream.wait_stream(stream)
-        run_subset(sub_lead, cs_lead, "lead", lead_stream)  # returns once the lead parts are sampled; their
-        run_subset(sub_rest, cs, "rest", stream)  # ordering runs on while the rest are sampled and ordered
-        for tag, st_ in (("lead_ordered", lead_stream), ("rest_ordered", stream)):
+        # each call returns once its parts are sampled; their ordering runs on while the
+        # next groups are sampled and ordered
+        for j, (sb, csx, st_) in enumerate(zip(sub_leads, cs_leads, lead_streams)):
+            st_.wait_stream(stream)
+            run_subset(sb, csx, f"lead{j}", st_)
+        run_subset(sub_rest, cs, "rest", stream)
+        for tag, st_ in [(f"lead{j}_ordered", x) for j, x in enumerate(lead_streams)] + [("rest_ordered", stream)]:
             marks[tag] = torch.cuda.Event(enable_timing=True)
             marks[tag].record(st_)
-        stream.wait_stream(lead_stream)
+        for st_ in lead_streams:
+            stream.wait_stream(st_)
 
     def step_breakdown():
         """ms from the step's start to each milestone of the last step (CUDA events)."""
@@ -510,12 +519,13 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": config_dict(args, specs) | {"surfels_per_gpu": total,
-                                                  "pipeline": f"{len(lead)} parts of >= {args.lead_min} surfels sampled "
-                                                              f"first and ordered on a second stream",
+                                                  "pipeline": f"parts in surfel-count bands {thresholds} "
+                                                              f"({[len(g) for g in leads]} parts) sampled first, "
+                                                              f"largest band first, each ordered on its own stream",
                                                   "step_milestones_ms": breakdown},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d_bytes),
                     "d2h_bytes_per_step": int(d2h_bytes)},
-            "gpu_launches": args.steps * (nsample_kernels + 3) * (2 if lead else 1),
+            "gpu_launches": args.steps * (nsample_kernels + 3) * (1 + sum(1 for g in leads if g)),
             "roofline": {"bound": "hbm", "kernel": "k_order_rounds", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak,
                          "traffic": (DRAM_BYTES_PER_SURFEL * float(ns[rest].sum())) if DRAM_BYTES_PER_SURFEL else None,

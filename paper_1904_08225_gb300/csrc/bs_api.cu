@@ -94,6 +94,10 @@ bs_status bs_set_tuning(const char *name, int value) {
         if (value != 0 && value != 1) { set_error("bs_set_tuning: kernel_timing=%d not 0 or 1", value); return BS_EINVAL; }
         order_set_kernel_timing(value == 1);
         return BS_OK;
+    } else if (!strcmp(name, "pool_keep_mb")) {
+        if (value < 0) { set_error("bs_set_tuning: pool_keep_mb=%d negative", value); return BS_EINVAL; }
+        pool_set_keep((uint64_t)value << 20);
+        return BS_OK;
     } else if (!strcmp(name, "order_quarters")) {
         if (value != 0 && value != 1 && value != 2) { set_error("bs_set_tuning: order_quarters=%d not 0, 1 or 2", value); return BS_EINVAL; }
         order_set_quarters(value);
@@ -359,7 +363,7 @@ static void launch_batch(bs_server *S, SrvSlot &slot, std::vector<SrvReq *> &bat
     for (SrvReq *r : batch) {
         r->t[1] = t;
         bool ok = slot.stage != nullptr;
-        if (ok && cudaMallocAsync((void **)&r->dmem, r->bytes, slot.stream) != cudaSuccess) {
+        if (ok && pool_malloc_async((void **)&r->dmem, r->bytes, slot.stream) != cudaSuccess) {
             cudaGetLastError();
             ok = false;
         }

@@ -153,6 +153,9 @@ bs_status sample_visible(const bs_mesh *mesh, const bs_dir *dirs, int ndirs, int
 bs_status render_mesh(const bs_mesh *mesh, const bs_dir *dir, int res, unsigned long long *image, cudaStream_t stream);
 bs_status render_splats(const bs_splat_set *sets, int nsets, const bs_splat_node *node, const bs_dir *dir,
                         unsigned long long *image, cudaStream_t stream);
+// the library's stream-ordered pool (freed with cudaFreeAsync)
+cudaError_t pool_malloc_async(void **ptr, size_t bytes, cudaStream_t stream);
+void pool_set_keep(uint64_t bytes);
 bs_status sample_splats(const bs_splat_set *sets, int nsets, const bs_splat_node *nodes, int nnodes, const bs_dir *dirs,
                         int ndirs, bs_surfels *out, cudaStream_t stream);
 bs_status sample_visible_parts(const bs_mesh *meshes, const int *res, int nparts, const bs_dir *dirs, int ndirs,

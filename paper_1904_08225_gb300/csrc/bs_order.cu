@@ -1163,7 +1163,7 @@ bs_status order_parts(std::vector<PartDesc> &hp, cudaStream_t stream, bool batch
     const size_t gofs_bytes = align_up((size_t)nparts * 4);
     total += desc_bytes + gofs_bytes + 256;
     char *ws = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&ws, total, stream);
+    cudaError_t e = pool_malloc_async((void **)&ws, total, stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error("bs_order: scratch allocation of %zu bytes failed: %s", total, cudaGetErrorString(e));

@@ -71,7 +71,7 @@ bs_status prefix_median_nn(const bs_surfels *s, const uint32_t *perm, uint64_t p
     if (pm > s->n || pm > 65536) { set_error("bs_prefix_median_nn: pm=%llu exceeds n or 65536", (unsigned long long)pm); return BS_EINVAL; }
     if (pm < 2) { *rm2 = 0; return BS_OK; }
     int64_t *buf = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&buf, (pm + 1) * sizeof(int64_t), stream);
+    cudaError_t e = pool_malloc_async((void **)&buf, (pm + 1) * sizeof(int64_t), stream);
     if (e != cudaSuccess) { cudaGetLastError(); set_error("bs_prefix_median_nn: scratch allocation failed"); return BS_ENOMEM; }
     k_prefix_nn<<<(unsigned)std::min<uint64_t>(pm, 4096), 256, 0, stream>>>(s->key, perm, (uint32_t)pm, buf);
     k_select<<<1, 1024, 0, stream>>>(buf, (uint32_t)pm, (uint32_t)((pm + 1) / 2 - 1), buf + pm);
@@ -88,7 +88,7 @@ bs_status prefix_for_radius(const int64_t *rad2, uint64_t m, int64_t r2, uint64_
     if (!rad2 || !p || m == 0) { set_error("bs_prefix_for_radius: NULL argument or m = 0"); return BS_EINVAL; }
     if (r2 < 0) { set_error("bs_prefix_for_radius: negative squared radius"); return BS_EINVAL; }
     unsigned long long *cnt = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&cnt, 8, stream);
+    cudaError_t e = pool_malloc_async((void **)&cnt, 8, stream);
     if (e != cudaSuccess) { cudaGetLastError(); set_error("bs_prefix_for_radius: scratch allocation failed"); return BS_ENOMEM; }
     unsigned long long h = 0;
     e = cudaMemsetAsync(cnt, 0, 8, stream);
@@ -140,7 +140,7 @@ bs_status prefix_for_radius_batched(const int64_t *const *rad2, const uint64_t *
     const size_t n = (size_t)nparts;
     char *buf = nullptr;
     const size_t bytes = n * (8 + 8 + 8 + 8 + 8);
-    cudaError_t e = cudaMallocAsync((void **)&buf, bytes, stream);
+    cudaError_t e = pool_malloc_async((void **)&buf, bytes, stream);
     if (e != cudaSuccess) { cudaGetLastError(); set_error("bs_prefix_for_radius_batched: scratch allocation failed"); return BS_ENOMEM; }
     const int64_t **d_rad2 = (const int64_t **)buf;
     uint64_t *d_m = (uint64_t *)(buf + 8 * n);

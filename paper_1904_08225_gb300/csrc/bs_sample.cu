@@ -826,7 +826,7 @@ struct Scratch {
 };
 
 static bs_status alloc_async(char **p, size_t bytes, cudaStream_t stream, const char *what) {
-    cudaError_t e = cudaMallocAsync((void **)p, bytes ? bytes : 256, stream);
+    cudaError_t e = pool_malloc_async((void **)p, bytes ? bytes : 256, stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error("bs_sample_visible: %s scratch allocation of %zu bytes failed: %s", what, bytes, cudaGetErrorString(e));

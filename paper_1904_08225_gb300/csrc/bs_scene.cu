@@ -168,7 +168,7 @@ bs_status scene_generate(uint64_t seed, const uint64_t *part_ids, const int32_t 
     memcpy(ht.sinv, sin32, sizeof(ht.sinv));
     char *buf = nullptr;
     const size_t bytes = sizeof(SceneTables) + 256 + (size_t)nparts * sizeof(ScenePart);
-    cudaError_t e = cudaMallocAsync((void **)&buf, bytes, stream);
+    cudaError_t e = pool_malloc_async((void **)&buf, bytes, stream);
     if (e != cudaSuccess) { cudaGetLastError(); set_error("bs_scene_generate: scratch allocation failed"); return BS_ENOMEM; }
     SceneTables *dt = (SceneTables *)buf;
     ScenePart *dp = (ScenePart *)(buf + ((sizeof(SceneTables) + 255) & ~(size_t)255));
