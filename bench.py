@@ -49,11 +49,11 @@ IMPROVED_FIT = (-1.06, 0.74)
 BYTES_PER_VISIT = 16   # 8 B key + 8 B D read
 BYTES_PER_IMPROVE = 8  # 8 B D write
 BYTES_OUT = 16         # perm 4 + rad2 8 + radius 4
-# DRAM bytes (read + write) of one k_order_rounds launch per surfel ordered, from an ncu
-# capture of the 1024-part batch (state far above L2, so traffic grows with the surfels):
-# profiles/k_order_rounds_traffic_batch1024_tori.md.  Must be re-measured (or set to None)
-# whenever k_order_rounds changes.
-DRAM_BYTES_PER_SURFEL = None
+# DRAM bytes (read + write) per surfel ordered of the dominant launch (the ordering of the
+# non-lead parts, k_order_rounds<1024, 1>), from an ncu capture of that launch in the
+# full-size bench step: profiles/k_order_rounds_traffic_bench4096_rest.md.  Must be
+# re-measured (or set to None) whenever k_order_rounds changes.
+DRAM_BYTES_PER_SURFEL = 1716.1
 
 
 def algorithmic_bytes(n: int) -> float:
@@ -242,6 +242,8 @@ def main():
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[250.0, 500.0, 1000.0, 2000.0])
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--no-extras", action="store_true", help="skip plain / served / cpu baseline legs")
+    ap.add_argument("--legs", default="order_only,served,table2,scene,cpu_baseline",
+                    help="comma list of the extra legs to run (order_only, served, table2, scene, cpu_baseline)")
     ap.add_argument("--scene-lines", type=int, default=20, help="production lines of the scene leg (0 skips it)")
     ap.add_argument("--scene-per-line", type=int, default=2500)
     ap.add_argument("--lead-min", type=int, nargs="+", default=[350_000, 150_000],
@@ -464,45 +466,50 @@ def main():
     e2e_value = world * total / (ms_e2e / 1e3)
 
     extras = {}
-    if not args.no_extras and rank == 0:
-        # ordering only: batched (one launch) vs plain (one launch per part) on a seeded subset
-        ms_b = timed(order_all, 2) / 2
-        g = np.random.default_rng(args.seed)
-        sub = np.sort(g.choice(P, size=min(args.plain_parts, P), replace=False))
-        sub_n = int(ns[sub].sum())
+    legs = set(args.legs.split(",")) if not args.no_extras else set()
+    if legs and rank == 0:
+        if "order_only" in legs:
+            # ordering only: batched (one launch) vs plain (one launch per part) on a seeded subset
+            ms_b = timed(order_all, 2) / 2
+            g = np.random.default_rng(args.seed)
+            sub = np.sort(g.choice(P, size=min(args.plain_parts, P), replace=False))
+            sub_n = int(ns[sub].sum())
 
-        def plain():
-            for i in sub:
-                st = lib.bs_order(C.byref(parts[i]), C.byref(opts[i]), C.c_void_p(pp[i]), C.c_void_p(rp[i]),
-                                  C.c_void_p(fp[i]), cs)
-                if st != bs.BS_OK:
-                    raise bs.BsError(st, "bs_order", bs.last_error())
-        plain()
-        ms_p = timed(plain, 1)
-        sub_parts = (bs.Surfels * len(sub))(*[parts[i] for i in sub])
-        sub_opts = (bs.OrderOpts * len(sub))(*[opts[i] for i in sub])
-        spp = (C.c_void_p * len(sub))(*[pp[i] for i in sub])
-        srp = (C.c_void_p * len(sub))(*[rp[i] for i in sub])
-        sfp = (C.c_void_p * len(sub))(*[fp[i] for i in sub])
+            def plain():
+                for i in sub:
+                    st = lib.bs_order(C.byref(parts[i]), C.byref(opts[i]), C.c_void_p(pp[i]), C.c_void_p(rp[i]),
+                                      C.c_void_p(fp[i]), cs)
+                    if st != bs.BS_OK:
+                        raise bs.BsError(st, "bs_order", bs.last_error())
+            plain()
+            ms_p = timed(plain, 1)
+            sub_parts = (bs.Surfels * len(sub))(*[parts[i] for i in sub])
+            sub_opts = (bs.OrderOpts * len(sub))(*[opts[i] for i in sub])
+            spp = (C.c_void_p * len(sub))(*[pp[i] for i in sub])
+            srp = (C.c_void_p * len(sub))(*[rp[i] for i in sub])
+            sfp = (C.c_void_p * len(sub))(*[fp[i] for i in sub])
 
-        def batched_sub():
-            lib.bs_order_batched(sub_parts, len(sub), sub_opts, C.cast(spp, C.c_void_p), C.cast(srp, C.c_void_p),
-                                 C.cast(sfp, C.c_void_p), cs)
-        batched_sub()
-        ms_bs = timed(batched_sub, 1)
-        extras["order_only"] = {
-            "batched_all_parts": total / (ms_b / 1e3),
-            "batched_subset": sub_n / (ms_bs / 1e3),
-            "plain_subset": sub_n / (ms_p / 1e3),
-            "batched_over_plain": (sub_n / (ms_bs / 1e3)) / (sub_n / (ms_p / 1e3)),
-            "subset": f"{len(sub)} seeded parts, {sub_n} surfels, one bs_order launch each on one stream",
-            "unit": UNIT,
-        }
-        extras["served"] = serve_leg(bs, key_all, coff, ns, out_structs, args)
-        extras["paper_table2_shape"] = table2_leg(bs, timed)
-        if args.scene_lines > 0:
+            def batched_sub():
+                lib.bs_order_batched(sub_parts, len(sub), sub_opts, C.cast(spp, C.c_void_p), C.cast(srp, C.c_void_p),
+                                     C.cast(sfp, C.c_void_p), cs)
+            batched_sub()
+            ms_bs = timed(batched_sub, 1)
+            extras["order_only"] = {
+                "batched_all_parts": total / (ms_b / 1e3),
+                "batched_subset": sub_n / (ms_bs / 1e3),
+                "plain_subset": sub_n / (ms_p / 1e3),
+                "batched_over_plain": (sub_n / (ms_bs / 1e3)) / (sub_n / (ms_p / 1e3)),
+                "subset": f"{len(sub)} seeded parts, {sub_n} surfels, one bs_order launch each on one stream",
+                "unit": UNIT,
+            }
+        if "served" in legs:
+            extras["served"] = serve_leg(bs, key_all, coff, ns, out_structs, args)
+        if "table2" in legs:
+            extras["paper_table2_shape"] = table2_leg(bs, timed)
+        if "scene" in legs and args.scene_lines > 0:
             extras["scene"] = scene_leg(args)
-        extras["cpu_baseline"] = cpu_baseline(specs, args)
+        if "cpu_baseline" in legs:
+            extras["cpu_baseline"] = cpu_baseline(specs, args)
 
     if rank == 0:
         peak, peak_src = measured_peaks()
@@ -529,7 +536,7 @@ def main():
             "roofline": {"bound": "hbm", "kernel": "k_order_rounds", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak,
                          "traffic": (DRAM_BYTES_PER_SURFEL * float(ns[rest].sum())) if DRAM_BYTES_PER_SURFEL else None,
-                         "traffic_source": "ncu dram__bytes_read+write of the 1024-part batch, scaled by surfels",
+                         "traffic_source": "ncu dram__bytes_read+write of this launch in the full-size step, per surfel",
                          "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured" else "fallback 6800 GB/s",
                          "algorithmic_bytes_per_launch": bytes_launch, "loop_ms_per_launch": loop_avg,
                          "launch": f"bs_order_batched over the {len(rest)} non-lead parts ({int(ns[rest].sum())} surfels)"},

@@ -342,6 +342,8 @@ bs_status bs_scene_generate(uint64_t seed, const uint64_t *part_ids, const int32
  *                       1 = never, 2 = always (parts over 524,288 points stay whole)
  *  "order_full_parts"   k > 0: the k largest parts run on whole CTAs before the quarters
  *                       (0 = the cost model decides)
+ *  "server_slots"       launches a server created afterwards keeps in flight (1..256,
+ *                       16 by default; each holds 64 MB of pinned result staging)
  *  "pool_keep_mb"       freed scratch the library's per-device memory pool keeps for the
  *                       next call, in MiB (65536 by default; lowering it trims the pool)
  *  "order_algo"         2 = exact multi-pick rounds (default), 1 = one pick per step

@@ -73,11 +73,22 @@ static bs_status make_part(const bs_surfels *s, const bs_order_opts *opts, uint3
 
 using namespace bs;
 
+namespace bs {
+// launch slots of servers created from now on (bs_set_tuning("server_slots", v))
+int g_server_slots = 16;
+}  // namespace bs
+using bs::g_server_slots;
+
 extern "C" {
 
 const char *bs_last_error(void) { return g_err; }
 
 bs_status bs_set_tuning(const char *name, int value) {
+    if (name && !strcmp(name, "server_slots")) {
+        if (value < 1 || value > 256) { set_error("bs_set_tuning: server_slots=%d outside [1, 256]", value); return BS_EINVAL; }
+        g_server_slots = value;
+        return BS_OK;
+    }
     static int threads = 0, ctas = 0;
     if (!name) { set_error("bs_set_tuning: NULL name"); return BS_EINVAL; }
     if (!strcmp(name, "order_threads")) {
@@ -467,7 +478,7 @@ bs_server *bs_server_create(uint64_t device_budget_bytes, int max_inflight, bs_s
     S->budget = device_budget_bytes;
     S->max_inflight = max_inflight ? max_inflight : 4096;
     S->t0 = std::chrono::steady_clock::now();
-    S->slots.resize(16);  // launches in flight at once: each holds the requests queued when it started
+    S->slots.resize((size_t)g_server_slots);  // launches in flight at once: each holds the requests queued when it started
     if (cudaStreamCreateWithFlags(&S->copy, cudaStreamNonBlocking) != cudaSuccess) {
         set_error("bs_server_create: stream creation failed: %s", cudaGetErrorString(cudaGetLastError()));
         if (st) *st = BS_ECUDA;
