@@ -242,8 +242,9 @@ def main():
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[250.0, 500.0, 1000.0, 2000.0])
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--no-extras", action="store_true", help="skip plain / served / cpu baseline legs")
-    ap.add_argument("--legs", default="order_only,served,table2,scene,cpu_baseline",
-                    help="comma list of the extra legs to run (order_only, served, table2, scene, cpu_baseline)")
+    ap.add_argument("--legs", default="order_only,autotune,served,table2,scene,cpu_baseline",
+                    help="comma list of the extra legs to run (order_only, autotune, served, table2, scene, "
+                         "cpu_baseline)")
     ap.add_argument("--scene-lines", type=int, default=20, help="production lines of the scene leg (0 skips it)")
     ap.add_argument("--scene-per-line", type=int, default=2500)
     ap.add_argument("--lead-min", type=int, nargs="+", default=[350_000, 150_000],
@@ -312,9 +313,22 @@ def main():
             raise bs.BsError(st, "bs_sample_visible_batched", bs.last_error())
 
     sample_all()
-    out_structs = [out_arr[i] for i in range(len(specs))]
-    ns = np.array([o.n for o in out_structs], np.int64)
+    ns = np.array([out_arr[i].n for i in range(len(specs))], np.int64)
     total = int(ns.sum())
+    # the counts are deterministic: size every part's outputs exactly, so the surfel records
+    # of all parts form one contiguous array (one copy per field for the e2e read-back)
+    coff = np.cumsum([0] + list(ns))
+    key_all = torch.empty(total, dtype=torch.int64, device=dev)
+    nrm_all = torch.empty((total, 3), dtype=torch.int16, device=dev)
+    rgb_all = torch.empty((total, 3), dtype=torch.uint8, device=dev)
+    src_all = torch.empty(total, dtype=torch.int32, device=dev)
+    out_arr = (bs.Surfels * len(specs))(*[
+        bs.Surfels(key_all.data_ptr() + 8 * int(coff[i]), nrm_all.data_ptr() + 6 * int(coff[i]),
+                   rgb_all.data_ptr() + 3 * int(coff[i]), src_all.data_ptr() + 4 * int(coff[i]), 0, int(ns[i]),
+                   (C.c_float * 3)(), 0.0) for i in range(len(specs))])
+    sample_all()
+    out_structs = [out_arr[i] for i in range(len(specs))]
+    assert np.array_equal(np.array([o.n for o in out_structs], np.int64), ns)
     pofs = np.cumsum([0] + list(ns))
     perm_all = torch.empty(total, dtype=torch.int32, device=dev)
     rad2_all = torch.empty(total, dtype=torch.int64, device=dev)
@@ -401,9 +415,9 @@ def main():
         "perm": torch.empty(total, dtype=torch.int32).pin_memory(),
         "rad2": torch.empty(total, dtype=torch.int64).pin_memory(),
         "radius": torch.empty(total, dtype=torch.float32).pin_memory(),
-        "key": torch.empty(int(coff[-1]), dtype=torch.int64).pin_memory(),
-        "nrm": torch.empty((int(coff[-1]), 3), dtype=torch.int16).pin_memory(),
-        "rgb": torch.empty((int(coff[-1]), 3), dtype=torch.uint8).pin_memory(),
+        "key": torch.empty(total, dtype=torch.int64).pin_memory(),
+        "nrm": torch.empty((total, 3), dtype=torch.int16).pin_memory(),
+        "rgb": torch.empty((total, 3), dtype=torch.uint8).pin_memory(),
     }
     d2h_bytes = total * (4 + 8 + 4) + total * (8 + 6 + 3)
 
@@ -415,12 +429,10 @@ def main():
         res_h["perm"].copy_(perm_all, non_blocking=True)
         res_h["rad2"].copy_(rad2_all, non_blocking=True)
         res_h["radius"].copy_(radius_all, non_blocking=True)
-        # surfel records of each part (contiguous per part in the capacity layout)
-        for i in range(P):
-            o, n = int(coff[i]), int(ns[i])
-            res_h["key"][o:o + n].copy_(key_all[o:o + n], non_blocking=True)
-            res_h["nrm"][o:o + n].copy_(nrm_all[o:o + n], non_blocking=True)
-            res_h["rgb"][o:o + n].copy_(rgb_all[o:o + n], non_blocking=True)
+        # the surfel records of all parts (contiguous: outputs sized exactly)
+        res_h["key"].copy_(key_all, non_blocking=True)
+        res_h["nrm"].copy_(nrm_all, non_blocking=True)
+        res_h["rgb"].copy_(rgb_all, non_blocking=True)
         stream.synchronize()
 
     def barrier():
@@ -502,6 +514,16 @@ def main():
                 "subset": f"{len(sub)} seeded parts, {sub_n} surfels, one bs_order launch each on one stream",
                 "unit": UNIT,
             }
+        if "autotune" in legs:
+            # the autotuner over the batch's ordering launch (all parts in one launch)
+            from paper_1904_08225_gb300 import autotune
+            keys_t = [key_all[int(coff[i]):int(coff[i]) + int(ns[i])] for i in range(P)]
+            best, times = autotune.autotune(keys_t, repeats=1, apply=False)
+            extras["autotune"] = {"best": {"order_threads": best[0], "order_quarters": best[1],
+                                           "order_full_parts": best[2]},
+                                  "ms": {f"threads={c[0]},quarters={c[1]},full_parts={c[2]}": round(t, 2)
+                                         for c, t in times.items()},
+                                  "launch": f"bs_order_batched over all {P} parts"}
         if "served" in legs:
             extras["served"] = serve_leg(bs, key_all, coff, ns, out_structs, args)
         if "table2" in legs:

@@ -485,3 +485,25 @@ def test_prefix_line_closed_form(bs):
         gap = 2 ** (m - j) * h
         assert bs.prefix_median_nn(key, perm, 2**j + 1) == gap * gap
         assert bs.prefix_for_radius(rad2, gap * gap) == 2 ** (j - 1) + 1
+
+
+def test_autotune_picks_a_shape_and_keeps_results(bs):
+    """The autotuner times every candidate launch shape on the batch, checks that none
+    changes a result, and leaves the fastest set."""
+    from paper_1904_08225_gb300 import autotune
+    g = np.random.default_rng(21)
+    keys = []
+    for i in range(400):
+        n = int(g.integers(100, 6000))
+        pts = np.unique(g.integers(0, 1 << 18, size=(n, 3)), axis=0)
+        keys.append(_dev(oracle.pack(pts).view(np.int64)))
+    base = bs.order_batched(keys)
+    try:
+        best, times = autotune.autotune(keys, repeats=1)
+        assert best in times and set(times) == set(autotune.DEFAULT_CANDIDATES)
+        got = bs.order_batched(keys)
+    finally:
+        for n in ("order_threads", "order_quarters", "order_full_parts"):
+            bs.set_tuning(n, 0)
+    for a, b in zip(base, got):
+        assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
