@@ -239,7 +239,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--plain-parts", type=int, default=512, help="parts timed one launch each for the plain path")
     ap.add_argument("--serve-requests", type=int, default=1000)
-    ap.add_argument("--serve-rates", type=float, nargs="+", default=[250.0, 500.0, 1000.0, 2000.0])
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[500.0, 1000.0, 2000.0, 4000.0, 8000.0])
+    ap.add_argument("--serve-window", type=float, default=2.0, help="seconds of arrivals per offered rate")
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--no-extras", action="store_true", help="skip plain / served / cpu baseline legs")
     ap.add_argument("--legs", default="order_only,autotune,served,table2,scene,cpu_baseline",
@@ -581,7 +582,9 @@ def serve_leg(bs, key_all, coff, ns, out_structs, args):
     keys = {}
     sweep = []
     for rate in args.serve_rates:
-        nreq = args.serve_requests
+        # enough requests that arrivals last serve_window seconds: the tail of the largest
+        # requests then weighs little in the sustained rate
+        nreq = max(args.serve_requests, int(rate * args.serve_window))
         pick = g.choice(pool, size=nreq)
         for i in np.unique(pick):
             if int(i) not in keys:
