@@ -20,11 +20,18 @@
 // Kernels:
 //   k_order_init  one warp per group over all parts: D from the start point,
 //                 bucket and group records.                       (HBM/L2 sweep)
-//   k_order_loop  persistent, one CTA per part at a time (parts taken from an
-//                 atomic counter): per step a block argmax over the group records,
-//                 a scan of group boxes against the new point, and a warp per
-//                 touched group updating its touched buckets.     (the update sweep)
-//   k_radius      radius[k] = sqrt(rad2[k]) / scale in IEEE double, as float.
+//   k_order_rounds  persistent (parts taken from atomic counters): exact multi-pick
+//                 rounds -- gather the candidates above a threshold, one warp runs
+//                 the greedy on them, every pick of the round applied in one pruned
+//                 sweep (super-group, group and bucket boxes).  The largest parts of a
+//                 launch run on whole CTAs; with quarter mode a 1024-thread CTA then
+//                 takes four more parts at once on 256-thread quarters.  Writes the
+//                 radii and the part's completion flag at the end of each part.
+//   k_order_loop  the same greedy with one pick per step (order_algo 1): per step a
+//                 block argmax over the group records, a scan of group boxes against
+//                 the new point, and a warp per touched group updating its buckets.
+//   k_radius      radius[k] = sqrt(rad2[k]) / scale in IEEE double, as float (after
+//                 k_order_loop).
 #include <algorithm>
 #include <cmath>
 #include <mutex>
