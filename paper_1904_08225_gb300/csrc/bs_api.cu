@@ -342,19 +342,21 @@ static void start_copy(bs_server *S, SrvSlot &slot, SrvReq *r) {
         r->copied = nullptr;
     }
     if (r->copied) cudaEventRecord(r->copied, S->copy);
-    r->state = 5;
 }
 
-static void finish_copy(bs_server *S, SrvSlot &slot, SrvReq *r) {
+// Moves a request's copied result from the slot's pinned staging into its own buffers.
+static void finish_copy(SrvSlot &slot, SrvReq *r) {
     const char *st = slot.stage + r->stage_off;
     memcpy(r->perm.data(), st, r->m * 4);
     memcpy(r->rad2.data(), st + align256(r->m * 4), r->m * 8);
     memcpy(r->radius.data(), st + align256(r->m * 4) + align256(r->m * 8), r->m * 4);
-    r->t[2] = S->now();
-    r->state = 2;
 }
 
-static void launch_batch(bs_server *S, SrvSlot &slot, std::vector<SrvReq *> &batch) {
+// The device work of a launch: memory, host-to-device keys, the ordering launch.  Runs
+// without the server lock; it touches only the slot and fields of the batch's requests
+// that no other thread reads (the requests are still "queued" to poll and times).
+// err[i] receives each request's outcome (BS_OK when it runs).
+static void launch_batch(bs_server *S, SrvSlot &slot, std::vector<SrvReq *> &batch, std::vector<bs_status> &err) {
     // device memory, H2D keys, ordering, D2H results into pinned staging
     size_t stage = 0;
     for (SrvReq *r : batch) {
@@ -369,16 +371,16 @@ static void launch_batch(bs_server *S, SrvSlot &slot, std::vector<SrvReq *> &bat
         else cudaGetLastError();
     }
     std::vector<PartDesc> parts;
-    std::vector<SrvReq *> run;
-    const double t = S->now();
-    for (SrvReq *r : batch) {
-        r->t[1] = t;
+    std::vector<size_t> run;
+    err.assign(batch.size(), BS_OK);
+    for (size_t i = 0; i < batch.size(); ++i) {
+        SrvReq *r = batch[i];
         bool ok = slot.stage != nullptr;
         if (ok && pool_malloc_async((void **)&r->dmem, r->bytes, slot.stream) != cudaSuccess) {
             cudaGetLastError();
             ok = false;
         }
-        if (!ok) { r->state = 3; r->err = BS_ENOMEM; r->dmem = nullptr; continue; }
+        if (!ok) { err[i] = BS_ENOMEM; r->dmem = nullptr; continue; }
         uint64_t *dk = (uint64_t *)r->dmem;
         uint32_t *dp = (uint32_t *)(r->dmem + align256(r->n * 8));
         int64_t *dr = (int64_t *)(r->dmem + align256(r->n * 8) + align256(r->m * 4));
@@ -399,45 +401,71 @@ static void launch_batch(bs_server *S, SrvSlot &slot, std::vector<SrvReq *> &bat
         p.part_id = r->opts.part_id;
         p.seed = r->opts.seed;
         parts.push_back(p);
-        run.push_back(r);
-        r->state = 1;
+        run.push_back(i);
     }
     if (!parts.empty()) {
         bs_status st = order_parts(parts, slot.stream, true);
         if (st != BS_OK)
-            for (SrvReq *r : run) { r->state = 3; r->err = st; r->t[2] = S->now(); }
+            for (size_t i : run) err[i] = st;
     }
     cudaEventRecord(slot.done, slot.stream);
-    slot.reqs = batch;
-    slot.busy = true;
 }
 
+// The driver thread.  The server lock guards the queue, the budget and every request's
+// state; the driver holds it only to read and change those, and drops it for the CUDA
+// calls and copies, so that submit and poll from other threads never wait on them.  The
+// requests it works on meanwhile stay in a state (queued, running, copying) that poll
+// and times answer without touching their buffers, and only this thread changes slots.
 static void driver_loop(bs_server *S) {
     cudaSetDevice(S->device);
     std::unique_lock<std::mutex> lk(S->mu);
+    std::vector<SrvReq *> to_copy, to_finish;
+    std::vector<SrvSlot *> copy_owner, finish_owner;
+    std::vector<bs_status> err;
     while (!S->stop) {
         bool progressed = false;
+        // 1. requests whose part has finished (flag set) or whose result copy has landed
+        to_copy.clear();
+        to_finish.clear();
+        copy_owner.clear();
+        finish_owner.clear();
+        for (SrvSlot &slot : S->slots) {
+            if (!slot.busy) continue;
+            for (SrvReq *r : slot.reqs) {
+                if (r->state == 1 && ((volatile uint32_t *)slot.flags_h)[r->flag] != 0u) {
+                    to_copy.push_back(r);
+                    copy_owner.push_back(&slot);
+                } else if (r->state == 5 && (!r->copied || cudaEventQuery(r->copied) == cudaSuccess)) {
+                    to_finish.push_back(r);
+                    finish_owner.push_back(&slot);
+                }
+            }
+        }
+        if (!to_copy.empty() || !to_finish.empty()) {
+            lk.unlock();
+            for (size_t i = 0; i < to_copy.size(); ++i) start_copy(S, *copy_owner[i], to_copy[i]);
+            bool sync = false;
+            for (SrvReq *r : to_finish) sync |= !r->copied;
+            if (sync) cudaStreamSynchronize(S->copy);
+            for (size_t i = 0; i < to_finish.size(); ++i) finish_copy(*finish_owner[i], to_finish[i]);
+            lk.lock();
+            const double t = S->now();
+            for (SrvReq *r : to_copy) r->state = 5;
+            for (SrvReq *r : to_finish) { r->t[2] = t; r->state = 2; }
+            progressed = true;
+        }
+        // 2. launches whose every request is finished
         for (SrvSlot &slot : S->slots) {
             if (!slot.busy) continue;
             bool all_done = true;
-            for (SrvReq *r : slot.reqs) {
-                if (r->state == 1 && ((volatile uint32_t *)slot.flags_h)[r->flag] != 0u) {
-                    start_copy(S, slot, r);
-                    progressed = true;
-                }
-                if (r->state == 5 && (!r->copied || cudaEventQuery(r->copied) == cudaSuccess)) {
-                    if (!r->copied) cudaStreamSynchronize(S->copy);
-                    finish_copy(S, slot, r);
-                    progressed = true;
-                }
-                all_done &= r->state == 2 || r->state == 3 || r->state == 4;
-            }
+            for (SrvReq *r : slot.reqs) all_done &= r->state == 2 || r->state == 3 || r->state == 4;
             if (all_done && cudaEventQuery(slot.done) == cudaSuccess) {
                 retire(S, slot);
                 progressed = true;
             }
         }
         if (progressed) S->cv.notify_all();
+        // 3. new launches on free slots
         for (SrvSlot &slot : S->slots) {
             if (slot.busy || S->queue.empty()) continue;
             std::vector<SrvReq *> batch;
@@ -450,7 +478,19 @@ static void driver_loop(bs_server *S) {
                 batch.push_back(r);
             }
             if (batch.empty()) break;
-            launch_batch(S, slot, batch);
+            slot.busy = true;
+            const double t1 = S->now();
+            lk.unlock();
+            launch_batch(S, slot, batch, err);
+            lk.lock();
+            const double t2 = S->now();
+            for (size_t i = 0; i < batch.size(); ++i) {
+                SrvReq *r = batch[i];
+                r->t[1] = t1;
+                if (err[i] == BS_OK) r->state = 1;
+                else { r->state = 3; r->err = err[i]; r->t[2] = t2; }
+            }
+            slot.reqs = std::move(batch);
             progressed = true;
         }
         if (!progressed) {
