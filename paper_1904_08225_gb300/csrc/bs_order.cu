@@ -252,7 +252,8 @@ struct RoundsSm {
     int64_t sd[SMAX];    //            its distance to the chosen set
     uint64_t sk[SMAX];   //            its position
     uint32_t ppos[MAXP], tail[MAXP];
-    uint32_t part, ccnt, gcnt, sgcnt, npick, icut, nheavy;
+    uint32_t part, ccnt, gcnt, sgcnt, npick, icut;  // gather counters (reset when the previous round applies)
+    uint32_t agcnt, asgcnt, nheavy;                 // apply counters (reset when the round's picks are written)
     int shift;
     int64_t tieD;
 };
@@ -307,10 +308,13 @@ __device__ __forceinline__ uint64_t pick_mask(uint32_t np, const uint32_t *pi, c
 }
 
 // One part ordered by TP threads (thread tid of them, warp-aligned) that synchronise on
-// named barrier `bar`; S and the record arrays are this part slot's shared memory.
+// named barrier `bar`; S and the record arrays are this part slot's shared memory.  Warp
+// simw runs the serial steps (the candidate greedy, the tie window, the sampler's
+// choice): the quarters of a CTA pass different warps so that their serial steps issue
+// from different schedulers of the SM.
 template <int TP, int SG>
 __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm, unsigned char *slot, int nbsm,
-                                            int ngcap, int tid, int bar) {
+                                            int ngcap, int tid, int bar, int simw) {
     static_assert(TP >= CAP && TP >= SMAX, "the candidate and sample sorts need one thread per entry");
     constexpr int NW = TP / 32;
     const int lane = tid & 31, warp = tid >> 5;
@@ -347,6 +351,7 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
         P.rad2[0] = INT64_MAX;
         Sm.shift = 3;
         Sm.tieD = -2;
+        Sm.ccnt = 0; Sm.gcnt = 0; Sm.sgcnt = 0; Sm.icut = 0xffffffffu;
         if (P.variant == 1) {  // remove the start from the remaining set (swap with the last)
             const uint32_t y = P.R[n - 1];
             P.R[P.start] = y;
@@ -410,7 +415,7 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
         part_sync(bar, TP);
         // (S3) the m_t = 1 + t / step distinct samples farthest from the chosen set
         //      (distances as of the round start), ties to the lowest index
-        if (warp == 0) {
+        if (warp == simw) {
             uint32_t cs[SPL];
             int64_t ds[SPL];
             bool live[SPL];
@@ -490,14 +495,11 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
         const int shift = Sm.shift;
         const bool tie = D1 == Sm.tieD;
         const int64_t tau = tie ? D1 : D1 - (D1 >> shift);
-        part_sync(bar, TP);
-        if (tid == 0) { Sm.ccnt = 0; Sm.gcnt = 0; Sm.sgcnt = 0; Sm.icut = 0xffffffffu; }
-        part_sync(bar, TP);
-        // (3) gather the candidates
+        // (3) gather the candidates (the gather counters were reset before the last barrier)
         if (tie) {
             // D1 points in index order from j on, over up to TIE_GROUPS groups holding D1
             // points, while they fit; icut = first index left out (no D1 point lies below j)
-            if (warp == 0) {
+            if (warp == simw) {
                 uint32_t cnt = 0, icut = n, used = 0;
                 bool full = false;
                 for (uint32_t g0 = j >> 10; g0 < ng && !full && used < TIE_GROUPS; ++g0) {
@@ -593,6 +595,8 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
                     Sm.shift = min(shift + inc, 62);
                 }
             }
+            part_sync(bar, TP);  // every thread has read the counters
+            if (tid == 0) { Sm.ccnt = 0; Sm.gcnt = 0; Sm.sgcnt = 0; Sm.icut = 0xffffffffu; }
             part_sync(bar, TP);
             continue;
         }
@@ -619,7 +623,7 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
         //     slot lane + 32u lives in lane's register u.  The updates are branch-free (a
         //     branch per register keeps the four updates from overlapping); pick t is
         //     recorded in lane t & 31 and written out after the loop.
-        if (warp == 0) {
+        if (warp == simw) {
             const uint32_t budget = min((uint32_t)MAXP, m - k);
             const bool tiecut = icut != 0xffffffffu;
             uint32_t np = 0;
@@ -766,7 +770,12 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
             Sm.py[t] = (int32_t)pos_y(q);
             Sm.pz[t] = (int32_t)pos_z(q);
         }
-        if (tid == 0) { Sm.sgcnt = 0; Sm.gcnt = 0; }
+        if (tid == 0) {
+            // the next round's gather counters (this round read them before the last
+            // barrier) and this round's apply counters
+            Sm.ccnt = 0; Sm.gcnt = 0; Sm.sgcnt = 0; Sm.icut = 0xffffffffu;
+            Sm.asgcnt = 0; Sm.agcnt = 0; Sm.nheavy = 0;
+        }
         part_sync(bar, TP);
         const uint64_t all = np >= 64 ? ~0ull : ((1ull << np) - 1ull);
         for (uint32_t sg = warp; sg < ns; sg += NW) {
@@ -774,13 +783,15 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
                                           (int64_t)(Sm.sgkey[sg] >> 15) - 1);
             if (mk && lane == 0) {
                 Sm.sgmask[sg] = mk;
-                Sm.sglist[atomicAdd(&Sm.sgcnt, 1u)] = sg;
+                Sm.sglist[atomicAdd(&Sm.asgcnt, 1u)] = sg;
             }
         }
         part_sync(bar, TP);
-        const uint32_t nsgl = Sm.sgcnt;
-        if (tid == 0) Sm.nheavy = 0;
-        part_sync(bar, TP);
+        const uint32_t nsgl = Sm.asgcnt;
+        // A super-group's groups are tested against its picks by one warp walking the picks
+        // (lanes = groups) or, with more than four picks, by a warp per group (lanes =
+        // picks): the second takes more instructions but spreads a super-group over all
+        // the part's warps, and measured faster in both modes.
         for (uint32_t li = warp; li < nsgl; li += NW) {
             const uint32_t sg = Sm.sglist[li];
             const uint64_t sgm = Sm.sgmask[sg];
@@ -797,7 +808,7 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
                         mm &= mm - 1;
                         rel |= (Sm.pi[t] >> 10) == g || box_dist2_xyz(gb, Sm.px[t], Sm.py[t], Sm.pz[t]) < gD;
                     }
-                    if (rel) s_glist[atomicAdd(&Sm.gcnt, 1u)] = g;
+                    if (rel) s_glist[atomicAdd(&Sm.agcnt, 1u)] = g;
                 }
             } else if (lane == 0) {
                 Sm.heavy[atomicAdd(&Sm.nheavy, 1u)] = sg;
@@ -813,11 +824,11 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
                 if (g >= ng) continue;
                 const uint64_t gm = pick_mask(np, Sm.pi, Sm.px, Sm.py, Sm.pz, Sm.sgmask[sg], 10, g, s_glo[g], s_ghi[g],
                                               (int64_t)(s_gkey[g] >> 10) - 1);
-                if (gm && lane == 0) s_glist[atomicAdd(&Sm.gcnt, 1u)] = g;
+                if (gm && lane == 0) s_glist[atomicAdd(&Sm.agcnt, 1u)] = g;
             }
         }
         part_sync(bar, TP);
-        const uint32_t ngl = Sm.gcnt;
+        const uint32_t ngl = Sm.agcnt;
         for (uint32_t li = warp; li < ngl; li += NW) {
             const uint32_t g = s_glist[li];
             const uint64_t gm = pick_mask(np, Sm.pi, Sm.px, Sm.py, Sm.pz, Sm.sgmask[g >> 5], 10, g, s_glo[g], s_ghi[g],
@@ -932,7 +943,7 @@ __global__ void __launch_bounds__(CT) k_order_rounds(const PartDesc *__restrict_
         const uint32_t p = s_part[0];
         __syncthreads();
         if (p >= (uint32_t)nfull) break;
-        rounds_part<CT, MAX_SG>(parts[p], *(RoundsSm<MAX_SG> *)smraw, smraw, nbsm, ngmax, threadIdx.x, 0);
+        rounds_part<CT, MAX_SG>(parts[p], *(RoundsSm<MAX_SG> *)smraw, smraw, nbsm, ngmax, threadIdx.x, 0, 0);
     }
     if constexpr (QUARTERS) {
         const int q = threadIdx.x / QT, tid = threadIdx.x % QT;
@@ -943,7 +954,7 @@ __global__ void __launch_bounds__(CT) k_order_rounds(const PartDesc *__restrict_
             const uint32_t p = s_part[q];
             part_sync(1 + q, QT);
             if (p >= (uint32_t)nparts) break;
-            rounds_part<QT, Q_SG>(parts[p], *(RoundsSm<Q_SG> *)slot, slot, nbq, ngq, tid, 1 + q);
+            rounds_part<QT, Q_SG>(parts[p], *(RoundsSm<Q_SG> *)slot, slot, nbq, ngq, tid, 1 + q, q);
         }
     }
 }
