@@ -789,13 +789,13 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
         part_sync(bar, TP);
         const uint32_t nsgl = Sm.asgcnt;
         // A super-group's groups are tested against its picks by one warp walking the picks
-        // (lanes = groups) or, with more than four picks, by a warp per group (lanes =
-        // picks): the second takes more instructions but spreads a super-group over all
-        // the part's warps, and measured faster in both modes.
+        // (lanes = groups) or, with more picks, by a warp per group (lanes = picks): the
+        // second takes more instructions but spreads a super-group over more warps.
+        constexpr int LIGHT_MAX = TP > QT ? 16 : 4;
         for (uint32_t li = warp; li < nsgl; li += NW) {
             const uint32_t sg = Sm.sglist[li];
             const uint64_t sgm = Sm.sgmask[sg];
-            if (__popcll((long long)sgm) <= 4) {
+            if (__popcll((long long)sgm) <= LIGHT_MAX) {
                 // few picks: one lane per group walks them
                 const uint32_t g = sg * 32 + lane;
                 if (g < ng) {
