@@ -53,7 +53,7 @@ BYTES_OUT = 16         # perm 4 + rad2 8 + radius 4
 # non-lead parts, k_order_rounds<1024, 1>), from an ncu capture of that launch in the
 # full-size bench step: profiles/k_order_rounds_traffic_bench4096_rest.md.  Must be
 # re-measured (or set to None) whenever k_order_rounds changes.
-DRAM_BYTES_PER_SURFEL = None
+DRAM_BYTES_PER_SURFEL = 2013.6
 
 
 def algorithmic_bytes(n: int) -> float:
