@@ -275,13 +275,18 @@ def main():
     dev = torch.device("cuda", local)
 
     # ---- inputs: all meshes packed in one buffer (host pinned + device copy) ----
+    specs0 = specs
     meshes = [sp.mesh() for sp in specs]
-    vofs = np.cumsum([0] + [m.nverts for m in meshes])
-    tofs = np.cumsum([0] + [m.ntris for m in meshes])
-    xyz_h = torch.from_numpy(np.concatenate([m.xyz for m in meshes])).pin_memory()
-    tri_h = torch.from_numpy(np.concatenate([m.tri for m in meshes]).view(np.int32)).pin_memory()
-    rgb_h = torch.from_numpy(np.concatenate([m.rgb for m in meshes])).pin_memory()
-    xyz_d, tri_d, rgb_d = xyz_h.to(dev), tri_h.to(dev), rgb_h.to(dev)
+
+    def pack(meshes):
+        vofs = np.cumsum([0] + [m.nverts for m in meshes])
+        tofs = np.cumsum([0] + [m.ntris for m in meshes])
+        xyz_h = torch.from_numpy(np.concatenate([m.xyz for m in meshes])).pin_memory()
+        tri_h = torch.from_numpy(np.concatenate([m.tri for m in meshes]).view(np.int32)).pin_memory()
+        rgb_h = torch.from_numpy(np.concatenate([m.rgb for m in meshes])).pin_memory()
+        return vofs, tofs, xyz_h, tri_h, rgb_h, xyz_h.to(dev), tri_h.to(dev), rgb_h.to(dev)
+
+    vofs, tofs, xyz_h, tri_h, rgb_h, xyz_d, tri_d, rgb_d = pack(meshes)
     h2d_bytes = xyz_h.numel() * 4 + tri_h.numel() * 4 + rgb_h.numel()
     dirs = (bs.Dir * 6)(*[bs.Dir(int(a), int(b), int(c)) for a, b, c in W.AXIS_DIRS])
 
@@ -316,6 +321,26 @@ def main():
     sample_all()
     ns = np.array([out_arr[i].n for i in range(len(specs))], np.int64)
     total = int(ns.sum())
+    # Parts in band order (the largest-band parts first, then the next band, then the
+    # rest; index order within a band): each band's meshes, sampled records and ordered
+    # outputs are then contiguous, so the end-to-end step moves them band by band and
+    # overlaps the copies with the other bands' work.  orig[i] = the part's seeded index.
+    thresholds = sorted([t for t in args.lead_min if t > 0], reverse=True)
+    bounds = [float("inf")] + thresholds
+    band = np.array([next((j for j in range(len(thresholds)) if bounds[j + 1] <= n < bounds[j]), len(thresholds))
+                     for n in ns])
+    orig = np.array(sorted(range(len(specs)), key=lambda i: (band[i], i)), np.int64)
+    if not np.array_equal(orig, np.arange(len(specs))):
+        specs = [specs[i] for i in orig]
+        meshes = [meshes[i] for i in orig]
+        ns, band = ns[orig], band[orig]
+        del xyz_d, tri_d, rgb_d
+        vofs, tofs, xyz_h, tri_h, rgb_h, xyz_d, tri_d, rgb_d = pack(meshes)
+        mesh_structs = [bs.Mesh(xyz_d.data_ptr() + int(vofs[i]) * 12, meshes[i].nverts,
+                                tri_d.data_ptr() + int(tofs[i]) * 12, meshes[i].ntris,
+                                rgb_d.data_ptr() + int(tofs[i]) * 3) for i in range(len(specs))]
+        mesh_arr = (bs.Mesh * len(specs))(*mesh_structs)
+        res_arr = (C.c_int * len(specs))(*[sp.res for sp in specs])
     # the counts are deterministic: size every part's outputs exactly, so the surfel records
     # of all parts form one contiguous array (one copy per field for the e2e read-back)
     coff = np.cumsum([0] + list(ns))
@@ -341,7 +366,7 @@ def main():
     for i in range(P):
         o = out_structs[i]
         parts[i] = bs.Surfels(o.key, None, None, None, o.n, o.n, (C.c_float * 3)(), o.scale)
-        opts[i] = bs.OrderOpts(0, i, -1, 0)
+        opts[i] = bs.OrderOpts(0, int(orig[i]), -1, 0)
         pp[i] = perm_all.data_ptr() + 4 * int(pofs[i])
         rp[i] = rad2_all.data_ptr() + 8 * int(pofs[i])
         fp[i] = radius_all.data_ptr() + 4 * int(pofs[i])
@@ -356,12 +381,8 @@ def main():
     # longest single chain) are sampled first and ordered on a second stream while the
     # others are sampled and ordered on the main stream.  Every part is sampled and
     # ordered exactly once per step; both streams join the main stream at the end.
-    thresholds = sorted([t for t in args.lead_min if t > 0], reverse=True)
-    bounds = [float("inf")] + thresholds
-    leads = [[i for i in range(P) if bounds[j + 1] <= ns[i] < bounds[j]] for j in range(len(thresholds))]
-    lead = [i for grp in leads for i in grp]
-    lead_set = set(lead)
-    rest = [i for i in range(P) if i not in lead_set]
+    leads = [[i for i in range(P) if band[i] == j] for j in range(len(thresholds))]
+    rest = [i for i in range(P) if band[i] == len(thresholds)]
 
     def subset(idx):
         k = len(idx)
@@ -378,9 +399,11 @@ def main():
 
     marks = {}
 
-    def run_subset(sb, csx, tag, tstream):
+    def run_subset(sb, csx, tag, tstream, ready=None):
         if sb["k"] == 0:
             return
+        if ready is not None:
+            tstream.wait_event(ready)
         st = lib.bs_sample_visible_batched(sb["mesh"], sb["res"], sb["k"], dirs, 6, sb["out"], csx)
         if st != bs.BS_OK:
             raise bs.BsError(st, "bs_sample_visible_batched", bs.last_error())
@@ -391,15 +414,16 @@ def main():
         if st != bs.BS_OK:
             raise bs.BsError(st, "bs_order_batched", bs.last_error())
 
-    def step():
+    def step(ready=None):
+        """One step; ready[j] (optional) = event after which band j's meshes are on the device."""
         marks["start"] = torch.cuda.Event(enable_timing=True)
         marks["start"].record(stream)
         # each call returns once its parts are sampled; their ordering runs on while the
         # next groups are sampled and ordered
         for j, (sb, csx, st_) in enumerate(zip(sub_leads, cs_leads, lead_streams)):
             st_.wait_stream(stream)
-            run_subset(sb, csx, f"lead{j}", st_)
-        run_subset(sub_rest, cs, "rest", stream)
+            run_subset(sb, csx, f"lead{j}", st_, ready[j] if ready else None)
+        run_subset(sub_rest, cs, "rest", stream, ready[-1] if ready else None)
         for tag, st_ in [(f"lead{j}_ordered", x) for j, x in enumerate(lead_streams)] + [("rest_ordered", stream)]:
             marks[tag] = torch.cuda.Event(enable_timing=True)
             marks[tag].record(st_)
@@ -421,19 +445,46 @@ def main():
         "rgb": torch.empty((total, 3), dtype=torch.uint8).pin_memory(),
     }
     d2h_bytes = total * (4 + 8 + 4) + total * (8 + 6 + 3)
+    # bands as part ranges [p0, p1) in step order (lead bands, then the rest)
+    band_tags = [f"lead{j}" for j in range(len(leads))] + ["rest"]
+    band_rng = [(int(np.searchsorted(band, j, "left")), int(np.searchsorted(band, j, "right")))
+                for j in range(len(thresholds) + 1)]
+    h2d_stream = torch.cuda.Stream(device=dev)
+    d2h_streams = [torch.cuda.Stream(device=dev) for _ in band_rng]
+    dev_out = {"perm": perm_all, "rad2": rad2_all, "radius": radius_all,
+               "key": key_all, "nrm": nrm_all, "rgb": rgb_all}
 
     def step_e2e():
-        xyz_d.copy_(xyz_h, non_blocking=True)
-        tri_d.copy_(tri_h, non_blocking=True)
-        rgb_d.copy_(rgb_h, non_blocking=True)
-        step()
-        res_h["perm"].copy_(perm_all, non_blocking=True)
-        res_h["rad2"].copy_(rad2_all, non_blocking=True)
-        res_h["radius"].copy_(radius_all, non_blocking=True)
-        # the surfel records of all parts (contiguous: outputs sized exactly)
-        res_h["key"].copy_(key_all, non_blocking=True)
-        res_h["nrm"].copy_(nrm_all, non_blocking=True)
-        res_h["rgb"].copy_(rgb_all, non_blocking=True)
+        # inputs band by band from pinned host memory: a band's sampling starts as soon
+        # as its own meshes have arrived
+        h2d_stream.wait_stream(stream)
+        ready = []
+        with torch.cuda.stream(h2d_stream):
+            for p0, p1 in band_rng:
+                v0, v1, t0, t1 = int(vofs[p0]), int(vofs[p1]), int(tofs[p0]), int(tofs[p1])
+                xyz_d[v0:v1].copy_(xyz_h[v0:v1], non_blocking=True)
+                tri_d[t0:t1].copy_(tri_h[t0:t1], non_blocking=True)
+                rgb_d[t0:t1].copy_(rgb_h[t0:t1], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(h2d_stream)
+                ready.append(ev)
+        step(ready)
+        # results band by band: the sampled surfel records once the band is sampled (while
+        # the ordering runs on), the ordered outputs once it is ordered
+        for (p0, p1), tag, st_ in zip(band_rng, band_tags, d2h_streams):
+            if p1 == p0:
+                continue
+            s0, s1 = int(coff[p0]), int(coff[p1])
+            st_.wait_event(marks[tag + "_sampled"])
+            with torch.cuda.stream(st_):
+                for name in ("key", "nrm", "rgb"):
+                    res_h[name][s0:s1].copy_(dev_out[name][s0:s1], non_blocking=True)
+            st_.wait_event(marks[tag + "_ordered"])
+            with torch.cuda.stream(st_):
+                for name in ("perm", "rad2", "radius"):
+                    res_h[name][s0:s1].copy_(dev_out[name][s0:s1], non_blocking=True)
+        for st_ in d2h_streams:
+            stream.wait_stream(st_)
         stream.synchronize()
 
     def barrier():
@@ -532,7 +583,7 @@ def main():
         if "scene" in legs and args.scene_lines > 0:
             extras["scene"] = scene_leg(args)
         if "cpu_baseline" in legs:
-            extras["cpu_baseline"] = cpu_baseline(specs, args)
+            extras["cpu_baseline"] = cpu_baseline(specs0, args)
 
     if rank == 0:
         peak, peak_src = measured_peaks()
