@@ -536,7 +536,9 @@ def main():
             # ordering only: batched (one launch) vs plain (one launch per part) on a seeded subset
             ms_b = timed(order_all, 2) / 2
             g = np.random.default_rng(args.seed)
-            sub = np.sort(g.choice(P, size=min(args.plain_parts, P), replace=False))
+            at = np.empty(P, np.int64)
+            at[orig] = np.arange(P)  # the subset is drawn by seeded part index, whatever the layout
+            sub = np.sort(at[g.choice(P, size=min(args.plain_parts, P), replace=False)])
             sub_n = int(ns[sub].sum())
 
             def plain():
@@ -577,7 +579,7 @@ def main():
                                          for c, t in times.items()},
                                   "launch": f"bs_order_batched over all {P} parts"}
         if "served" in legs:
-            extras["served"] = serve_leg(bs, key_all, coff, ns, out_structs, args)
+            extras["served"] = serve_leg(bs, key_all, coff, ns, out_structs, args, orig)
         if "table2" in legs:
             extras["paper_table2_shape"] = table2_leg(bs, timed)
         if "scene" in legs and args.scene_lines > 0:
@@ -624,19 +626,25 @@ def main():
     return 0
 
 
-def serve_leg(bs, key_all, coff, ns, out_structs, args):
+def serve_leg(bs, key_all, coff, ns, out_structs, args, orig=None):
     """Poisson arrivals of ordering requests (surfel arrays of the sampled parts with
     1k-1M surfels, each with its own seed) through bs_server at several offered rates;
-    latency = device completion - submit, on the server's clock."""
+    latency = device completion - submit, on the server's clock.  Requests are drawn by
+    the parts' seeded indices (orig[i] = seeded index of the part at position i), so the
+    trace does not depend on how the parts are laid out."""
     g = np.random.default_rng(args.seed + 1)
-    pool = np.where((ns >= 1000) & (ns <= 1_000_000))[0]
+    orig = np.arange(len(ns)) if orig is None else np.asarray(orig)
+    at = np.empty(len(ns), np.int64)
+    at[orig] = np.arange(len(ns))  # seeded index -> position
+    ns_seeded = ns[at]
+    pool = np.where((ns_seeded >= 1000) & (ns_seeded <= 1_000_000))[0]
     keys = {}
     sweep = []
     for rate in args.serve_rates:
         # enough requests that arrivals last serve_window seconds: the tail of the largest
         # requests then weighs little in the sustained rate
         nreq = max(args.serve_requests, int(rate * args.serve_window))
-        pick = g.choice(pool, size=nreq)
+        pick = at[g.choice(pool, size=nreq)]
         for i in np.unique(pick):
             if int(i) not in keys:
                 keys[int(i)] = key_all[int(coff[i]):int(coff[i]) + int(ns[i])].cpu().numpy().view(np.uint64)
@@ -649,7 +657,8 @@ def serve_leg(bs, key_all, coff, ns, out_structs, args):
             if arr[r] > now:
                 time.sleep(arr[r] - now)
             i = int(pick[r])
-            tickets.append((srv.submit(keys[i], scale=out_structs[i].scale, seed=r, part_id=i), int(ns[i])))
+            tickets.append((srv.submit(keys[i], scale=out_structs[i].scale, seed=r, part_id=int(orig[i])),
+                            int(ns[i])))
         lat, done, t_first, t_last = [], 0, None, 0.0
         pending = list(tickets)
         while pending:
