@@ -318,6 +318,58 @@ def test_server_alone_equals_mix(bs):
             assert np.array_equal(r[2].view(np.uint32), oracle.radius(rr, 3.0).view(np.uint32))
 
 
+def test_server_concurrent_clients(bs):
+    """Four client threads submit and poll at once while the driver thread works without
+    the server lock (device calls, key uploads, result copies); every result equals the
+    oracle's."""
+    import threading
+    g = np.random.default_rng(21)
+    reqs = []
+    for t in range(4):
+        rs = []
+        for j in range(40):
+            n = int(g.integers(1, 3000))
+            pts = np.unique(g.integers(0, 1 << 20, size=(n + 8, 3)), axis=0)[:n]
+            rs.append((oracle.pack(pts), 100 * t + j))
+        reqs.append(rs)
+    out = [dict() for _ in range(4)]
+    errs = []
+    with bs.Server(budget_bytes=256 << 20) as srv:
+        def drain(pending, got):
+            for s, tk in list(pending.items()):
+                r = srv.poll(tk)
+                if r is not None:
+                    got[s] = r
+                    del pending[s]
+
+        def client(t):
+            try:
+                pending = {}
+                for k, sid in reqs[t]:
+                    pending[sid] = srv.submit(k, scale=2.0, seed=sid, part_id=sid)
+                    drain(pending, out[t])
+                deadline = time.time() + 60
+                while pending and time.time() < deadline:
+                    drain(pending, out[t])
+                    time.sleep(0.0002)
+                assert not pending, f"{len(pending)} requests not finished"
+            except Exception as e:  # noqa: BLE001 - reported by the main thread
+                errs.append(e)
+
+        threads = [threading.Thread(target=client, args=(t,)) for t in range(4)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+    assert not errs, errs
+    for t in range(4):
+        for k, sid in reqs[t]:
+            rp, rr = oracle.greedy(k, oracle.start_index(len(k), seed=sid, part_id=sid))
+            p, r2, rad = out[t][sid]
+            assert np.array_equal(p, rp) and np.array_equal(r2, rr), sid
+            assert np.array_equal(rad.view(np.uint32), oracle.radius(rr, 2.0).view(np.uint32)), sid
+
+
 def test_server_budget_admission(bs):
     """A budget that fits one large request at a time still completes every request."""
     g = np.random.default_rng(8)
