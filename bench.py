@@ -56,6 +56,29 @@ BYTES_OUT = 16         # perm 4 + rad2 8 + radius 4
 DRAM_BYTES_PER_SURFEL = 2013.6
 
 
+def band_layout(ns, thresholds):
+    """Bands of parts by surfel count and the layout that makes each band contiguous.
+
+    thresholds: descending surfel counts; band j (j < len(thresholds)) holds the parts with
+    thresholds[j] <= n < thresholds[j - 1] (no upper bound for j = 0), the last band the
+    rest.  Returns (orig, band): orig[i] = seeded index of the part at position i (band
+    order, seeded order within a band), band[i] = its band (non-decreasing)."""
+    ns = np.asarray(ns)
+    bounds = [float("inf")] + list(thresholds)
+    band0 = np.array([next((j for j in range(len(thresholds)) if bounds[j + 1] <= n < bounds[j]), len(thresholds))
+                      for n in ns], np.int64)
+    orig = np.array(sorted(range(len(ns)), key=lambda i: (band0[i], i)), np.int64)
+    return orig, band0[orig]
+
+
+def seeded_positions(orig):
+    """at[s] = position of the part whose seeded index is s (the inverse of orig)."""
+    orig = np.asarray(orig)
+    at = np.empty(len(orig), np.int64)
+    at[orig] = np.arange(len(orig))
+    return at
+
+
 def algorithmic_bytes(n: int) -> float:
     """Bytes the ordering of an N-surfel part must move (init sweep + update sweeps + outputs)."""
     if n <= 1:
@@ -326,14 +349,11 @@ def main():
     # outputs are then contiguous, so the end-to-end step moves them band by band and
     # overlaps the copies with the other bands' work.  orig[i] = the part's seeded index.
     thresholds = sorted([t for t in args.lead_min if t > 0], reverse=True)
-    bounds = [float("inf")] + thresholds
-    band = np.array([next((j for j in range(len(thresholds)) if bounds[j + 1] <= n < bounds[j]), len(thresholds))
-                     for n in ns])
-    orig = np.array(sorted(range(len(specs)), key=lambda i: (band[i], i)), np.int64)
+    orig, band = band_layout(ns, thresholds)
     if not np.array_equal(orig, np.arange(len(specs))):
         specs = [specs[i] for i in orig]
         meshes = [meshes[i] for i in orig]
-        ns, band = ns[orig], band[orig]
+        ns = ns[orig]
         del xyz_d, tri_d, rgb_d
         vofs, tofs, xyz_h, tri_h, rgb_h, xyz_d, tri_d, rgb_d = pack(meshes)
         mesh_structs = [bs.Mesh(xyz_d.data_ptr() + int(vofs[i]) * 12, meshes[i].nverts,
@@ -536,8 +556,7 @@ def main():
             # ordering only: batched (one launch) vs plain (one launch per part) on a seeded subset
             ms_b = timed(order_all, 2) / 2
             g = np.random.default_rng(args.seed)
-            at = np.empty(P, np.int64)
-            at[orig] = np.arange(P)  # the subset is drawn by seeded part index, whatever the layout
+            at = seeded_positions(orig)  # the subset is drawn by seeded part index, whatever the layout
             sub = np.sort(at[g.choice(P, size=min(args.plain_parts, P), replace=False)])
             sub_n = int(ns[sub].sum())
 
@@ -634,8 +653,7 @@ def serve_leg(bs, key_all, coff, ns, out_structs, args, orig=None):
     trace does not depend on how the parts are laid out."""
     g = np.random.default_rng(args.seed + 1)
     orig = np.arange(len(ns)) if orig is None else np.asarray(orig)
-    at = np.empty(len(ns), np.int64)
-    at[orig] = np.arange(len(ns))  # seeded index -> position
+    at = seeded_positions(orig)  # seeded index -> position
     ns_seeded = ns[at]
     pool = np.where((ns_seeded >= 1000) & (ns_seeded <= 1_000_000))[0]
     keys = {}
