@@ -1291,7 +1291,22 @@ constexpr size_t NA_BUCKETS = NA_RAD2 + 8ull * NOALLOC_MAX_POINTS;          // 4
 constexpr size_t NA_GROUPS = NA_BUCKETS + 4 * 8ull * NOALLOC_MAX_BUCKETS;   // 4 x u64 [ng]
 constexpr size_t NA_BYTES = NA_GROUPS + 4 * 8ull * NOALLOC_MAX_GROUPS;
 
+static_assert(sizeof(PartDesc) <= NA_NEXT - NA_DESC, "the descriptor must fit before the part counter");
+static_assert(NA_D % 8 == 0 && NA_RAD2 % 8 == 0 && NA_BUCKETS % 8 == 0 && NA_GROUPS % 8 == 0,
+              "scratch regions hold 8-byte words");
+
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+// Writes the part descriptor (passed by value, so nothing is read from host memory
+// once the launch is queued) into the scratch array and zeroes the part counter and
+// the group offset that follow it.
+__global__ void k_noalloc_setup(PartDesc p, PartDesc *d_desc, uint32_t *d_next) {
+    if (threadIdx.x == 0) {
+        *d_desc = p;
+        d_next[0] = 0u;
+        d_next[1] = 0u;
+    }
+}
 
 std::mutex g_noalloc_mu;
 char *g_noalloc_addr[64] = {nullptr};
@@ -1346,9 +1361,9 @@ bs_status order_part_noalloc(PartDesc p, cudaStream_t stream) {
     p.ghi = gk + 3 * NOALLOC_MAX_GROUPS;
     PartDesc *d_desc = (PartDesc *)(base + NA_DESC);
     uint32_t *d_next = (uint32_t *)(base + NA_NEXT);
-    cudaError_t e = cudaMemcpyAsync(d_desc, &p, sizeof(PartDesc), cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_next, 0, 8, stream);  // d_next[0] counter, d_next[1] = gofs[0] = 0
-    if (e != cudaSuccess) { set_error("bs_order_noalloc: descriptor upload failed: %s", cudaGetErrorString(e)); return BS_ECUDA; }
+    k_noalloc_setup<<<1, 32, 0, stream>>>(p, d_desc, d_next);  // d_next[0] counter, d_next[1] = gofs[0] = 0
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { set_error("bs_order_noalloc: descriptor setup failed: %s", cudaGetErrorString(e)); return BS_ECUDA; }
     k_order_init<<<(p.ng + 7) / 8, 256, 0, stream>>>(d_desc, d_next + 1, 1, p.ng);
     const int T = pick_threads((int)p.ng, false, g_order_algo);
     switch (T) {
@@ -1358,7 +1373,7 @@ bs_status order_part_noalloc(PartDesc p, cudaStream_t stream) {
         case 512: e = launch_loop<512>(d_desc, 1, d_next, (int)p.ng, 1, stream, g_order_algo); break;
         default: e = launch_loop<1024>(d_desc, 1, d_next, (int)p.ng, 1, stream, g_order_algo); break;
     }
-    if (e == cudaSuccess && p.radius) {
+    if (e == cudaSuccess && p.radius && g_order_algo == 1) {  // the rounds kernel writes radii itself
         k_radius<<<dim3(std::min<uint32_t>((p.m + 255) / 256, 64), 1), 256, 0, stream>>>(d_desc, 1);
         e = cudaGetLastError();
     }
