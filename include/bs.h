@@ -184,6 +184,27 @@ typedef struct {
 bs_status bs_sample_splats(const bs_splat_set *sets, int nsets, const bs_splat_node *nodes, int nnodes,
                            const bs_dir *dirs, int ndirs, bs_surfels *out, void *cuda_stream);
 
+/* bs_parent_frames -- the frames parent nodes are sampled in, and the child prefixes they
+ * draw (Sec. 3.4 bottom-up generation with Sec. 4.1's prefix rule).  Parent k's children
+ * are c in [child_ofs[k], child_ofs[k + 1]); child c's quantisation cube is
+ * [child_min[3c + a], child_min[3c + a] + (2^21 - 1) / child_scale[c]] on axis a.
+ *  - frame_min[3k + a] = the smallest child_min over parent k's children (float32);
+ *  - frame_scale[k] = (2^21 - 1) / E, E = the largest (child_min + (2^21 - 1) /
+ *    child_scale) - frame_min over the children and axes (IEEE double, in this order):
+ *    the largest child cube maps onto 2^21 - 1;
+ *  - child_r2[c] = (int64)(h * h), h = (2^21 / parent_res[k]) * (child_scale[c] /
+ *    frame_scale[k]): one pixel step of the parent's raster in child units.  A child is
+ *    drawn with the shortest prefix of its exact ordering reaching every child surfel
+ *    within sqrt(child_r2) (bs_prefix_for_radius_batched).
+ * All arrays are HOST arrays owned by the caller: child_min 3 * nchildren, child_scale
+ * nchildren, child_ofs nparents + 1 (child_ofs[0] = 0, non-decreasing), parent_res
+ * nparents, outputs frame_min 3 * nparents, frame_scale nparents, child_r2 nchildren
+ * (nchildren = child_ofs[nparents]).  Host arithmetic only; no device work.
+ * BS_EINVAL for NULL arrays, a parent without children, a non-positive or non-finite
+ * scale, a non-finite corner or a resolution outside 1..BS_MAX_RES. */
+bs_status bs_parent_frames(const float *child_min, const double *child_scale, const uint64_t *child_ofs, int nparents,
+                           const int32_t *parent_res, float *frame_min, double *frame_scale, int64_t *child_r2);
+
 /* ---- Headless renders for image-space coverage checks (Sec. 4.1's claim that the
  * prefix of length p(r), drawn as discs of radius r, covers every pixel of the object;
  * the discs of Sec. 4.2).  No window or graphics API: the image is a device buffer. ---- */

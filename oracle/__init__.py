@@ -74,6 +74,10 @@ def _load():
             lib.or_sample_splats.restype = C.c_int64
             lib.or_render_splats.argtypes = [C.c_uint64, P, P, C.c_int, P, P, P, P, P, C.c_double, P, C.c_int, P]
             lib.or_render_splats.restype = C.c_int
+            lib.or_parent_frame.argtypes = [P, P, C.c_uint64, P, P]
+            lib.or_parent_frame.restype = C.c_int
+            lib.or_child_target_r2.argtypes = [C.c_double, C.c_double, C.c_int]
+            lib.or_child_target_r2.restype = C.c_int64
             _lib = lib
     return _lib
 
@@ -221,6 +225,26 @@ def render_splats(sets, frame_min, frame_scale: float, d, res: int) -> np.ndarra
                             float(frame_scale), _p(dd), res, _p(depth)) != 0:
         raise ValueError("or_render_splats: bad arguments")
     return depth
+
+
+def parent_frame(mins, scales):
+    """Frame of a parent node (Sec. 3.4): (min float32 (3,), scale) holding every child's
+    quantisation cube [m_c, m_c + Q/s_c]; the largest extent maps onto 2^21 - 1."""
+    mn = np.ascontiguousarray(np.asarray(mins, np.float32).reshape(-1, 3))
+    sc = np.ascontiguousarray(np.asarray(scales, np.float64).reshape(-1))
+    if mn.shape[0] != sc.shape[0]:
+        raise ValueError("one bbox minimum per child scale")
+    fmin = np.zeros(3, np.float32)
+    fs = np.zeros(1, np.float64)
+    if _load().or_parent_frame(_p(mn), _p(sc), mn.shape[0], _p(fmin), _p(fs)) != 0:
+        raise ValueError("no children, or a non-positive scale")
+    return fmin, float(fs[0])
+
+
+def child_target_r2(child_scale: float, parent_scale: float, parent_res: int) -> int:
+    """Squared length, in child units, of one pixel step of the parent's raster: the child
+    prefix a parent draws is the shortest reaching every child surfel within it (Sec. 4.1)."""
+    return int(_load().or_child_target_r2(float(child_scale), float(parent_scale), int(parent_res)))
 
 
 def start_index(n: int, seed: int = 0, part_id: int = 0, start: int = -1) -> int:

@@ -897,3 +897,51 @@ uint64_t or_prefix_for_radius(const int64_t *rad2, uint64_t m, int64_t r2)
         if (rad2[p] <= r2) return p;
     return m;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Bottom-up generation (Sec. 3.4) with the prefix rule of Sec. 4.1: the     */
+/* frame a parent node is sampled in, and the child prefix it draws.         */
+/* Reading (the paper leaves both open):                                     */
+/*  - child c's quantisation cube is [m_c, m_c + Q / s_c] on every axis     */
+/*    (bbox minimum m_c, float32; scale s_c, double; Q = 2^21 - 1);          */
+/*  - the parent frame's minimum is the per-axis smallest m_c (a float32,   */
+/*    so it is one of the children's own corners) and its scale maps the    */
+/*    largest child cube extent from that minimum, max over c and axes of   */
+/*    (m_c + Q / s_c) - min, onto Q: S = Q / extent (IEEE double, in this   */
+/*    order);                                                               */
+/*  - a child is drawn with the shortest prefix of its ordering that        */
+/*    reaches every child surfel within one pixel step of the parent's      */
+/*    raster: 2^21 / res parent units = (2^21 / res) * (s_c / S) child      */
+/*    units; the target is the square of that, truncated to an integer.    */
+/* ------------------------------------------------------------------------ */
+int or_parent_frame(const float *mins, const double *scales, uint64_t nchildren, float *frame_min,
+                    double *frame_scale)
+{
+    if (nchildren == 0) return 1;
+    for (int a = 0; a < 3; a++) {
+        float lo = mins[a];
+        for (uint64_t c = 1; c < nchildren; c++)
+            if (mins[3 * c + a] < lo) lo = mins[3 * c + a];
+        frame_min[a] = lo;
+    }
+    double ext = 0.0;
+    for (uint64_t c = 0; c < nchildren; c++) {
+        if (!(scales[c] > 0.0)) return 1;
+        double side = (double)OR_Q / scales[c];
+        for (int a = 0; a < 3; a++) {
+            double hi = (double)mins[3 * c + a] + side;
+            double e = hi - (double)frame_min[a];
+            if (e > ext) ext = e;
+        }
+    }
+    if (!(ext > 0.0)) return 1;
+    *frame_scale = (double)OR_Q / ext;
+    return 0;
+}
+
+int64_t or_child_target_r2(double child_scale, double parent_scale, int parent_res)
+{
+    double step = 2097152.0 / (double)parent_res;  /* one parent pixel, parent units */
+    double h = step * (child_scale / parent_scale);  /* the same length, child units */
+    return (int64_t)(h * h);
+}

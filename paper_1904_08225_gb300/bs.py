@@ -25,7 +25,7 @@ INT64_MAX = (1 << 63) - 1
 EXPORTS = ["bs_sample_visible", "bs_sample_visible_batched", "bs_order", "bs_order_noalloc", "bs_order_batched", "bs_server_create", "bs_server_submit",
            "bs_server_poll", "bs_server_times", "bs_server_destroy", "bs_set_tuning", "bs_last_launch_ms",
            "bs_prefix_median_nn", "bs_prefix_for_radius", "bs_prefix_estimate", "bs_scene_generate", "bs_sample_splats",
-           "bs_prefix_for_radius_batched", "bs_render_mesh", "bs_render_splats",
+           "bs_prefix_for_radius_batched", "bs_render_mesh", "bs_render_splats", "bs_parent_frames",
            "bs_last_error"]
 
 
@@ -86,6 +86,7 @@ def load(build_if_stale: bool = True) -> C.CDLL:
             lib.bs_sample_visible_batched.argtypes = [C.POINTER(Mesh), C.POINTER(C.c_int), C.c_int, C.POINTER(Dir),
                                                       C.c_int, C.POINTER(Surfels), P]
             lib.bs_prefix_for_radius_batched.argtypes = [P, P, P, C.c_int, P, P, P]
+            lib.bs_parent_frames.argtypes = [P, P, P, C.c_int, P, P, P, P]
             lib.bs_render_mesh.argtypes = [C.POINTER(Mesh), C.POINTER(Dir), C.c_int, P, P]
             lib.bs_render_splats.argtypes = [C.POINTER(SplatSet), C.c_int, C.POINTER(SplatNode), C.POINTER(Dir), P, P]
             lib.bs_sample_splats.argtypes = [C.POINTER(SplatSet), C.c_int, C.POINTER(SplatNode), C.c_int,
@@ -224,6 +225,30 @@ def prefix_for_radius_batched(rad2s, ms, r2s, stream=None):
                                                 C.c_void_p(at.ctypes.data), _stream(stream)),
                "bs_prefix_for_radius_batched")
     return p, at
+
+
+def parent_frames(child_mins, child_scales, children_of, parent_res):
+    """bs_parent_frames: frames of parent nodes and their children's prefix targets (Sec. 3.4).
+
+    child_mins (C,3) float32 and child_scales (C,) of every child; children_of: per parent
+    the list of its child indices (each child listed once, parents in order); parent_res:
+    per parent.  Returns (frame_min float32 (P,3), frame_scale float64 (P,), child_r2
+    int64 per listed child in listing order)."""
+    lib = load()
+    order = [c for cs in children_of for c in cs]
+    mins = np.ascontiguousarray(np.asarray(child_mins, np.float32).reshape(-1, 3)[order])
+    scales = np.ascontiguousarray(np.asarray(child_scales, np.float64).reshape(-1)[order])
+    ofs = np.ascontiguousarray(np.concatenate([[0], np.cumsum([len(cs) for cs in children_of])]), dtype=np.uint64)
+    res = np.ascontiguousarray(parent_res, dtype=np.int32)
+    P = len(children_of)
+    fmin = np.zeros((P, 3), np.float32)
+    fs = np.zeros(P, np.float64)
+    r2 = np.zeros(len(order), np.int64)
+    _check(lib.bs_parent_frames(C.c_void_p(mins.ctypes.data), C.c_void_p(scales.ctypes.data),
+                                C.c_void_p(ofs.ctypes.data), P, C.c_void_p(res.ctypes.data),
+                                C.c_void_p(fmin.ctypes.data), C.c_void_p(fs.ctypes.data), C.c_void_p(r2.ctypes.data)),
+           "bs_parent_frames")
+    return fmin, fs, r2
 
 
 def prefix_estimate(pm: int, rm2: int, r2: int) -> float:

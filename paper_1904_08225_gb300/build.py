@@ -22,7 +22,7 @@ OBJDIR = os.path.join(PKG, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
-              "-Xcompiler", "-Wall", "-fmad=false", "-I", INCLUDE, "-I", CSRC]
+              "-Xcompiler", "-Wall", "-Xcompiler", "-ffp-contract=off", "-fmad=false", "-I", INCLUDE, "-I", CSRC]
 
 
 def nvcc() -> str:

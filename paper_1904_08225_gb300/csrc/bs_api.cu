@@ -210,6 +210,12 @@ double bs_prefix_estimate(uint64_t pm, int64_t rm2, int64_t r2) {
     return (double)pm * (double)rm2 / (double)r2;
 }
 
+bs_status bs_parent_frames(const float *child_min, const double *child_scale, const uint64_t *child_ofs, int nparents,
+                           const int32_t *parent_res, float *frame_min, double *frame_scale, int64_t *child_r2) {
+    clear_error();
+    return parent_frames(child_min, child_scale, child_ofs, nparents, parent_res, frame_min, frame_scale, child_r2);
+}
+
 bs_status bs_order_noalloc(const bs_surfels *s, const bs_order_opts *opts, uint32_t *perm, int64_t *rad2,
                            float *radius, void *cuda_stream) {
     clear_error();

@@ -138,6 +138,8 @@ bs_status prefix_median_nn(const bs_surfels *s, const uint32_t *perm, uint64_t p
 bs_status prefix_for_radius_batched(const int64_t *const *rad2, const uint64_t *m, const int64_t *r2, int nparts,
                                     uint64_t *p, int64_t *r2_at, cudaStream_t stream);
 bs_status prefix_for_radius(const int64_t *rad2, uint64_t m, int64_t r2, uint64_t *p, cudaStream_t stream);
+bs_status parent_frames(const float *child_min, const double *child_scale, const uint64_t *child_ofs, int nparents,
+                        const int32_t *parent_res, float *frame_min, double *frame_scale, int64_t *child_r2);
 bs_status scene_generate(uint64_t seed, const uint64_t *part_ids, const int32_t *lines, const int32_t *slots, int nparts,
                          int nboxes, int ncyl, const float *size_table, const float *cos32, const float *sin32,
                          float dx, float dy, int local_indices, float *xyz, uint32_t *tri, uint8_t *rgb,

@@ -1,6 +1,7 @@
 // bs_prefix.cu -- prefix selection at render time (Sec. 4.1): the median nearest-
 // neighbour distance r_m inside the first p_m surfels of an ordering, and the shortest
 // prefix whose surfels reach every point of the part within a radius.
+#include <cmath>
 #include <vector>
 
 #include "bs_internal.cuh"
@@ -162,6 +163,57 @@ bs_status prefix_for_radius_batched(const int64_t *const *rad2, const uint64_t *
     if (e != cudaSuccess) { set_error("bs_prefix_for_radius_batched: %s", cudaGetErrorString(e)); return BS_ECUDA; }
     if (r2_at)
         for (size_t i = 0; i < n; ++i) r2_at[i] = at[i];
+    return BS_OK;
+}
+
+// Parent frames and child prefix targets of the bottom-up generation (Sec. 3.4 with the
+// prefix rule of Sec. 4.1).  Host arithmetic on a handful of numbers per node: IEEE
+// double operations in the stated order (the library's host code is compiled without
+// floating-point contraction).
+bs_status parent_frames(const float *child_min, const double *child_scale, const uint64_t *child_ofs, int nparents,
+                        const int32_t *parent_res, float *frame_min, double *frame_scale, int64_t *child_r2) {
+    if (nparents < 0 || (nparents > 0 && (!child_min || !child_scale || !child_ofs || !parent_res || !frame_min ||
+                                          !frame_scale || !child_r2))) {
+        set_error("bs_parent_frames: NULL argument or negative count");
+        return BS_EINVAL;
+    }
+    const double Qd = (double)QMAX;
+    for (int k = 0; k < nparents; ++k) {
+        const uint64_t c0 = child_ofs[k], c1 = child_ofs[k + 1];
+        if (c1 <= c0) { set_error("bs_parent_frames: parent %d has no children", k); return BS_EINVAL; }
+        if (parent_res[k] < 1 || parent_res[k] > BS_MAX_RES) {
+            set_error("bs_parent_frames: parent %d: resolution %d outside 1..%d", k, parent_res[k], BS_MAX_RES);
+            return BS_EINVAL;
+        }
+        float lo[3] = {child_min[3 * c0], child_min[3 * c0 + 1], child_min[3 * c0 + 2]};
+        for (uint64_t c = c0; c < c1; ++c) {
+            const double s = child_scale[c];
+            if (!(s > 0.0) || !std::isfinite(s)) { set_error("bs_parent_frames: child %llu: bad scale", (unsigned long long)c); return BS_EINVAL; }
+            for (int a = 0; a < 3; ++a) {
+                const float m = child_min[3 * c + a];
+                if (!std::isfinite(m)) { set_error("bs_parent_frames: child %llu: non-finite corner", (unsigned long long)c); return BS_EINVAL; }
+                lo[a] = m < lo[a] ? m : lo[a];
+            }
+        }
+        double ext = 0.0;
+        for (uint64_t c = c0; c < c1; ++c) {
+            const double side = Qd / child_scale[c];
+            for (int a = 0; a < 3; ++a) {
+                const double hi = (double)child_min[3 * c + a] + side;
+                const double e = hi - (double)lo[a];
+                ext = e > ext ? e : ext;
+            }
+        }
+        if (!(ext > 0.0) || !std::isfinite(ext)) { set_error("bs_parent_frames: parent %d: zero extent", k); return BS_EINVAL; }
+        const double S = Qd / ext;
+        for (int a = 0; a < 3; ++a) frame_min[3 * k + a] = lo[a];
+        frame_scale[k] = S;
+        const double step = 2097152.0 / (double)parent_res[k];
+        for (uint64_t c = c0; c < c1; ++c) {
+            const double h = step * (child_scale[c] / S);
+            child_r2[c] = (int64_t)(h * h);
+        }
+    }
     return BS_OK;
 }
 

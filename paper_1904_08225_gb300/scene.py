@@ -145,39 +145,21 @@ def run(seed: int = 0, lines: int = 20, per_line: int = 2500, group: int = 50, n
 # lines from their groups' surfels, each surfel drawn as an oriented disc
 # (bs_sample_splats), instead of from triangles.
 # ---------------------------------------------------------------------------
-QMAX = 2**21 - 1
-
-
-def parent_frame(mins, scales):
-    """Frame of a parent node that holds its children's quantisation cubes: the smallest
-    corner, and the scale that maps the largest extent onto 2^21 - 1."""
-    mins = np.asarray(mins, np.float64).reshape(-1, 3)
-    scales = np.asarray(scales, np.float64)
-    fmin = mins.min(0).astype(np.float32)
-    ext = float(np.max(mins + (QMAX / scales)[:, None] - fmin.astype(np.float64)[None, :]))
-    return fmin, QMAX / ext
-
-
-def child_target_r2(child_scale: float, parent_scale: float, parent_res: int) -> int:
-    """Squared radius, in the child's units, of one pixel step of the parent's raster: the
-    child prefix drawn for the parent is the shortest one reaching every child surfel
-    within that distance (Sec. 4.1)."""
-    h = (2.0**21 / parent_res) * (child_scale / parent_scale)
-    return int(h * h)
-
-
 def _splat_level(children, nodes_children, level, seed, node_ids, res, ntris, out_res: SceneResult, keep):
     """Samples parent nodes from child outputs and orders them; returns the parents' outputs.
 
     children: list of dicts (key, nrm, rgb, perm, rad2, m, bbox_min, scale); nodes_children:
     per parent the indices of its children."""
-    frames = [parent_frame([children[c]["bbox_min"] for c in cs], [children[c]["scale"] for c in cs])
-              for cs in nodes_children]
-    order_c, targets = [], []
-    for k, cs in enumerate(nodes_children):
-        for c in cs:
-            order_c.append((k, c))
-            targets.append(child_target_r2(children[c]["scale"], frames[k][1], res))
+    # the parents' frames and each child's prefix target, from the library (Sec. 3.4 / 4.1)
+    listed = sorted({c for cs in nodes_children for c in cs})
+    cmin = np.zeros((len(children), 3), np.float32)
+    cscale = np.ones(len(children), np.float64)
+    for c in listed:
+        cmin[c] = children[c]["bbox_min"]
+        cscale[c] = children[c]["scale"]
+    fmin, fscale, targets = bs.parent_frames(cmin, cscale, nodes_children, [res] * len(nodes_children))
+    frames = [(fmin[k], float(fscale[k])) for k in range(len(nodes_children))]
+    order_c = [(k, c) for k, cs in enumerate(nodes_children) for c in cs]
     p, r2_at = bs.prefix_for_radius_batched([children[c]["rad2"] for _, c in order_c],
                                             [children[c]["m"] for _, c in order_c], targets)
     sets = []

@@ -174,15 +174,10 @@ def _oracle_parent(children, seed, idx, res, ntris):
     """A parent from its children's prefixes: the frame holding the children's cubes, each
     child's shortest prefix reaching its surfels within one parent pixel step (Sec. 4.1),
     its discs drawn (Sec. 3.4 / 4.2), then the exact ordering with the node bound."""
-    mins = np.array([c["mn"] for c in children], np.float64)
-    scales = np.array([c["sc"] for c in children], np.float64)
-    fmin = mins.min(0).astype(np.float32)
-    ext = float(np.max(mins + (Q / scales)[:, None] - fmin.astype(np.float64)[None, :]))
-    fs = Q / ext
+    fmin, fs = oracle.parent_frame([c["mn"] for c in children], [c["sc"] for c in children])
     sets = []
     for c in children:
-        h = (2.0**21 / res) * (c["sc"] / fs)
-        p = oracle.prefix_for_radius(c["rad2"], int(h * h))
+        p = oracle.prefix_for_radius(c["rad2"], oracle.child_target_r2(c["sc"], fs, res))
         pi = c["perm"][:p]
         sets.append(dict(key=c["sv"]["key"][pi], nrm=c["sv"]["nrm"][pi], rgb=c["sv"]["rgb"][pi], bbox_min=c["mn"],
                          scale=c["sc"], r2=int(c["rad2"][min(p, c["m"] - 1)])))
@@ -223,6 +218,41 @@ def test_bottom_up_reduced_scene_every_node(bs):
         assert np.array_equal(perm, ref[i]["perm"]), (i, nd.level)
         assert np.array_equal(rad2, ref[i]["rad2"]), (i, nd.level)
     assert out.per_level[1]["splats"] > 0 and out.per_level[2]["splats"] > 0
+
+
+def test_parent_frames_match_oracle(bs):
+    """bs_parent_frames (the frames and child prefix targets of the bottom-up generation)
+    equals the oracle's parent_frame / child_target_r2 bit for bit: random child frames,
+    dyadic ones, parents of one child and children sharing no corner."""
+    g = np.random.default_rng(12)
+    mins, scales, kids, res = [], [], [], []
+    c = 0
+    for k in range(60):
+        nk = int(g.integers(1, 12))
+        if k % 3 == 0:
+            m = g.integers(-8, 8, size=(nk, 3)).astype(np.float32) / 4
+            sc = Q / 2.0 ** g.integers(-3, 4, size=nk)
+        else:
+            m = g.uniform(-100, 100, size=(nk, 3)).astype(np.float32)
+            sc = Q / np.exp(g.uniform(np.log(0.01), np.log(50), size=nk))
+        mins.append(m)
+        scales.append(sc)
+        kids.append(list(range(c, c + nk)))
+        c += nk
+        res.append(int(g.choice([96, 128, 256, 1000, 1024, 4096])))
+    mins, scales = np.concatenate(mins), np.concatenate(scales)
+    fmin, fs, r2 = bs.parent_frames(mins, scales, kids, res)
+    j = 0
+    for k, cs in enumerate(kids):
+        om, os_ = oracle.parent_frame(mins[cs], scales[cs])
+        assert np.array_equal(fmin[k].view(np.uint32), om.view(np.uint32)) and fs[k] == os_, k
+        for ci in cs:
+            assert r2[j] == oracle.child_target_r2(scales[ci], os_, res[k]), (k, ci)
+            j += 1
+    with pytest.raises(bs.BsError):
+        bs.parent_frames(mins[:2], scales[:2], [[]], [128])
+    with pytest.raises(bs.BsError):
+        bs.parent_frames(mins[:2], np.array([1.0, -1.0]), [[0, 1]], [128])
 
 
 def test_prefix_for_radius_batched(bs):

@@ -105,10 +105,7 @@ def _children(bs, res=64, seeds=(1, 2, 3)):
 
 
 def _parent_frame(kids):
-    mins = np.array([k["mn"] for k in kids], np.float64)
-    fmin = mins.min(0).astype(np.float32)
-    ext = max(float(np.max(mins[i] + Q / kids[i]["sc"] - fmin.astype(np.float64))) for i in range(len(kids)))
-    return fmin, Q / ext
+    return oracle.parent_frame([k["mn"] for k in kids], [k["sc"] for k in kids])
 
 
 def test_children_prefixes_match_oracle(bs):
