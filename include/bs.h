@@ -367,6 +367,12 @@ bs_status bs_scene_generate(uint64_t seed, const uint64_t *part_ids, const int32
  *                       16 by default; each holds 64 MB of pinned result staging)
  *  "pool_keep_mb"       freed scratch the library's per-device memory pool keeps for the
  *                       next call, in MiB (65536 by default; lowering it trims the pool)
+ *  "order_cluster"      parts of at least "order_cluster_min" points (exact ordering)
+ *                       split over a thread-block cluster of this many CTAs, one SM each:
+ *                       1 = never (default: measured slower on GB300 at every size),
+ *                       0 = automatic size (up to 16, one CTA per 32,768 points at most),
+ *                       2..16 = that size (capped by the part's size)
+ *  "order_cluster_min"  smallest part ordered on a cluster (262,144 points by default)
  *  "order_algo"         2 = exact multi-pick rounds (default), 1 = one pick per step
  *  "kernel_timing"      1 = record CUDA events around internal kernels (bs_last_launch_ms)
  * Process-wide; BS_EINVAL for an unknown name or value. */

@@ -117,6 +117,14 @@ bs_status bs_set_tuning(const char *name, int value) {
         if (value < 0) { set_error("bs_set_tuning: order_full_parts=%d negative", value); return BS_EINVAL; }
         order_set_full_parts(value);
         return BS_OK;
+    } else if (!strcmp(name, "order_cluster")) {
+        if (value < 0 || value > 16) { set_error("bs_set_tuning: order_cluster=%d outside [0,16]", value); return BS_EINVAL; }
+        order_set_cluster(value, 0);
+        return BS_OK;
+    } else if (!strcmp(name, "order_cluster_min")) {
+        if (value < 1) { set_error("bs_set_tuning: order_cluster_min=%d not positive", value); return BS_EINVAL; }
+        order_set_cluster(-1, value);
+        return BS_OK;
     } else if (!strcmp(name, "order_ctas_per_sm")) {
         if (value < 0 || value > 32) { set_error("bs_set_tuning: order_ctas_per_sm=%d outside [0,32]", value); return BS_EINVAL; }
         ctas = value;

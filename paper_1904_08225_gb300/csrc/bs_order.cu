@@ -37,7 +37,11 @@
 #include <mutex>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "bs_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace bs {
 
@@ -256,6 +260,10 @@ struct RoundsSm {
     uint32_t agcnt, asgcnt, nheavy;                 // apply counters (reset when the round's picks are written)
     int shift;
     int64_t tieD;
+    // cluster mode: this CTA's best (top key) and the leader's candidate counters, one
+    // per gather attempt parity (an attempt's counter is reset while the other is in use)
+    uint64_t ctop;
+    uint32_t cc2[2];
 };
 
 // Bytes of one part slot: the state, then bucket (bkey, blo, bhi: nbcap each) and group
@@ -312,9 +320,18 @@ __device__ __forceinline__ uint64_t pick_mask(uint32_t np, const uint32_t *pi, c
 // simw runs the serial steps (the candidate greedy, the tie window, the sampler's
 // choice): the quarters of a CTA pass different warps so that their serial steps issue
 // from different schedulers of the SM.
-template <int TP, int SG>
+//
+// Cluster mode (CL): the part is split over the csize CTAs of a thread-block cluster.
+// CTA crank owns super-groups [sg0, sg1) -- their points, buckets and groups -- and
+// applies every pick of a round to them; candidates are gathered into the leader's
+// (rank 0) shared memory through distributed shared memory, the leader runs the
+// candidate greedy and the others copy its picks.  Every control decision (threshold,
+// retry, pick count, loop exit) is taken by every CTA from the same values read after
+// the same cluster barrier, so all CTAs pass the same sequence of barriers.  Only the
+// exact ordering (variant 0) runs in cluster mode, with bucket records in global memory.
+template <int TP, int SG, bool CL = false>
 __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm, unsigned char *slot, int nbsm,
-                                            int ngcap, int tid, int bar, int simw) {
+                                            int ngcap, int tid, int bar, int simw, int crank = 0, int csize = 1) {
     static_assert(TP >= CAP && TP >= SMAX, "the candidate and sample sorts need one thread per entry");
     constexpr int NW = TP / 32;
     const int lane = tid & 31, warp = tid >> 5;
@@ -329,12 +346,21 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
     const uint32_t n = P.n, nb = P.nb, m = P.m;
     const uint64_t *__restrict__ key = P.key;
     int64_t *__restrict__ Dg = P.D;
+    // this CTA's super-groups (all of them outside cluster mode)
+    const uint32_t sg0 = CL ? (uint32_t)(((uint64_t)crank * ns) / (uint32_t)csize) : 0u;
+    const uint32_t sg1 = CL ? (uint32_t)(((uint64_t)(crank + 1) * ns) / (uint32_t)csize) : ns;
+    const uint32_t og0 = sg0 * 32, og1 = min(ng, sg1 * 32);  // this CTA's groups
+    const bool leader = !CL || crank == 0;
+    cg::cluster_group cl = cg::this_cluster();
+    // the leader's candidate state (this CTA's own outside cluster mode)
+    RoundsSm<SG> &Ld = CL ? *cl.map_shared_rank(&Sm, 0) : Sm;
+    uint32_t attempt = 0;  // gather attempts of this part (cluster mode: picks the leader's counter)
     // bucket records: shared memory when they fit (generic pointers either way)
-    const bool bsm = nb <= (uint32_t)nbsm;
+    const bool bsm = !CL && nb <= (uint32_t)nbsm;
     uint64_t *bkey = bsm ? s_bkey : P.bkey;
     const uint64_t *blo_p = bsm ? s_blo : P.blo;
     const uint64_t *bhi_p = bsm ? s_bhi : P.bhi;
-    for (uint32_t g = tid; g < ng; g += TP) {
+    for (uint32_t g = og0 + tid; g < og1; g += TP) {
         s_gkey[g] = P.gkey[g];
         s_glo[g] = P.glo[g];
         s_ghi[g] = P.ghi[g];
@@ -347,12 +373,15 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
         }
     }
     if (tid == 0) {
-        P.perm[0] = P.start;
-        P.rad2[0] = INT64_MAX;
+        if (leader) {
+            P.perm[0] = P.start;
+            P.rad2[0] = INT64_MAX;
+        }
         Sm.shift = 3;
         Sm.tieD = -2;
         Sm.ccnt = 0; Sm.gcnt = 0; Sm.sgcnt = 0; Sm.icut = 0xffffffffu;
-        if (P.variant == 1) {  // remove the start from the remaining set (swap with the last)
+        Sm.cc2[0] = 0; Sm.cc2[1] = 0;
+        if (!CL && P.variant == 1) {  // remove the start from the remaining set (swap with the last)
             const uint32_t y = P.R[n - 1];
             P.R[P.start] = y;
             P.pos[y] = P.start;
@@ -360,7 +389,7 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
     }
     part_sync(bar, TP);
     uint32_t round_t = 0;
-    for (uint32_t sg = warp; sg < ns; sg += NW) {
+    for (uint32_t sg = sg0 + warp; sg < sg1; sg += NW) {
         const uint32_t g = sg * 32 + lane;
         const bool vg = g < ng;
         const uint64_t gk = vg ? s_gkey[g] : 0ull;
@@ -382,7 +411,7 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
     part_sync(bar, TP);
     uint32_t k = 1;
     while (k < m) {
-      if (P.variant == 1) {
+      if (!CL && P.variant == 1) {
         // (S1) the round's random subset of the remaining set R[0, n - k)
         const uint32_t L = n - k, S = P.sample_size;
         uint32_t c = 0, slot = 0;
@@ -483,13 +512,19 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
         ++round_t;
         part_sync(bar, TP);
       } else {
-        // (1) current maximum (every warp computes it; no barrier needed)
+        // (1) current maximum (every warp computes it; no barrier needed).  Cluster mode:
+        //     each CTA's best over its own super-groups, combined after a cluster barrier
+        //     (super-group indices are global, so the largest key is the global argmax)
         uint64_t top = 0;
-        for (uint32_t sg = lane; sg < ns; sg += 32) top = max(top, ((Sm.sgkey[sg] >> 15) << 8) | (uint64_t)(255 - sg));
+        for (uint32_t sg = sg0 + lane; sg < sg1; sg += 32) top = max(top, ((Sm.sgkey[sg] >> 15) << 8) | (uint64_t)(255 - sg));
         top = warp_max_u64(top);
+        if constexpr (CL) {
+            if (tid == 0) Sm.ctop = top;
+            cl.sync();
+            top = warp_max_u64(lane < csize ? cl.map_shared_rank(&Sm, lane)->ctop : 0ull);
+        }
         const int64_t D1 = (int64_t)(top >> 8) - 1;
         const uint32_t sgj = 255u - (uint32_t)(top & 255u);
-        const uint32_t j = sgj * 32768u + (32767u - (uint32_t)(Sm.sgkey[sgj] & 32767u));
         // (2) threshold: tau = D1 (1 - 2^-shift); when more than CAP points tie at D1, a tie
         //     window instead: tau = D1 and an index cut (the lowest-index tied points fit)
         const int shift = Sm.shift;
@@ -498,21 +533,32 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
         // (3) gather the candidates (the gather counters were reset before the last barrier)
         if (tie) {
             // D1 points in index order from j on, over up to TIE_GROUPS groups holding D1
-            // points, while they fit; icut = first index left out (no D1 point lies below j)
-            if (warp == simw) {
+            // points, while they fit; icut = first index left out (no D1 point lies below j).
+            // Cluster mode: the leader walks the groups of every CTA (group keys through
+            // distributed shared memory, bucket keys and distances from L2)
+            if (leader && warp == simw) {
+                // owner of a super-group in cluster mode: the CTA whose range holds it
+                auto owner = [&](uint32_t sg) {
+                    int r = 0;
+                    while (r + 1 < csize && sg >= (uint32_t)(((uint64_t)(r + 1) * ns) / (uint32_t)csize)) ++r;
+                    return r;
+                };
+                const uint64_t sgkj = CL ? cl.map_shared_rank(&Sm, owner(sgj))->sgkey[sgj] : Sm.sgkey[sgj];
+                const uint32_t j = sgj * 32768u + (32767u - (uint32_t)(sgkj & 32767u));
                 uint32_t cnt = 0, icut = n, used = 0;
                 bool full = false;
                 for (uint32_t g0 = j >> 10; g0 < ng && !full && used < TIE_GROUPS; ++g0) {
-                    if ((int64_t)(s_gkey[g0] >> 10) - 1 < tau) continue;
+                    const uint64_t gk0 = CL ? cl.map_shared_rank(s_gkey, owner(g0 >> 5))[g0] : s_gkey[g0];
+                    if ((int64_t)(gk0 >> 10) - 1 < tau) continue;
                     ++used;
                     const uint32_t b = g0 * 32 + lane;
-                    const uint64_t bk = (b < nb && b >= (j >> 5)) ? bkey[b] : 0ull;
+                    const uint64_t bk = (b < nb && b >= (j >> 5)) ? (CL ? __ldcg(&bkey[b]) : bkey[b]) : 0ull;
                     uint32_t mask = __ballot_sync(FULL, (int64_t)(bk >> 5) - 1 >= tau);
                     while (mask) {
                         const int bb = __ffs(mask) - 1;
                         mask &= mask - 1;
                         const uint32_t i = (g0 * 32 + bb) * 32 + lane;
-                        const int64_t d = i < n ? Dg[i] : -1;
+                        const int64_t d = i < n ? (CL ? __ldcg(&Dg[i]) : Dg[i]) : -1;
                         const uint64_t ki = i < n ? key[i] : 0ull;
                         const bool c = d >= tau;
                         const uint32_t cm = __ballot_sync(FULL, c);
@@ -531,10 +577,13 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
                     }
                     if (!full && used == TIE_GROUPS) icut = min(n, (g0 + 1) * 1024u);
                 }
-                if (lane == 0) { Sm.ccnt = cnt; Sm.icut = icut; }
+                if (lane == 0) {
+                    if (CL) Sm.cc2[attempt & 1] = cnt; else Sm.ccnt = cnt;
+                    Sm.icut = icut;
+                }
             }
         } else {
-            for (uint32_t sg = tid; sg < ns; sg += TP)
+            for (uint32_t sg = sg0 + tid; sg < sg1; sg += TP)
                 if ((int64_t)(Sm.sgkey[sg] >> 15) - 1 >= tau) Sm.sglist[atomicAdd(&Sm.sgcnt, 1u)] = sg;
             part_sync(bar, TP);
             const uint32_t nsgl = Sm.sgcnt;
@@ -569,19 +618,55 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
 #pragma unroll
                     for (int u = 0; u < LB; ++u) {
                         if (u < nb8 && d[u] >= tau && d[u] >= 0) {
+                            // cluster mode: staged in this CTA's (otherwise unused) sample
+                            // arrays, then moved to the leader in one block per CTA
                             const uint32_t slot = atomicAdd(&Sm.ccnt, 1u);
-                            if (slot < CAP) {
-                                Sm.ci[slot] = (g * 32 + bbs[u]) * 32 + lane;
-                                Sm.cd[slot] = d[u];
-                                Sm.ck[slot] = ki[u];
+                            if (CL ? slot < (uint32_t)SMAX : slot < (uint32_t)CAP) {
+                                if (CL) {
+                                    Sm.sc[slot] = (g * 32 + bbs[u]) * 32 + lane;
+                                    Sm.sd[slot] = d[u];
+                                    Sm.sk[slot] = ki[u];
+                                } else {
+                                    Sm.ci[slot] = (g * 32 + bbs[u]) * 32 + lane;
+                                    Sm.cd[slot] = d[u];
+                                    Sm.ck[slot] = ki[u];
+                                }
                             }
                         }
                     }
                 }
             }
         }
-        part_sync(bar, TP);
-        const uint32_t ccnt = Sm.ccnt;
+        uint32_t ccnt;
+        if constexpr (CL) {
+            if (!tie) {
+                // this CTA's candidates into the leader's arrays: one remote atomic for the
+                // block's slots (the full count, so the leader's total is exact), then the
+                // entries that fall below CAP
+                part_sync(bar, TP);
+                const uint32_t mine = Sm.ccnt;
+                if (tid == 0) Sm.icut = mine ? atomicAdd(&Ld.cc2[attempt & 1], mine) : 0u;  // icut: base, for now
+                part_sync(bar, TP);
+                const uint32_t base = Sm.icut;
+                for (uint32_t t = tid; t < min(mine, (uint32_t)SMAX) && base + t < (uint32_t)CAP; t += TP) {
+                    Ld.ci[base + t] = Sm.sc[t];
+                    Ld.cd[base + t] = Sm.sd[t];
+                    Ld.ck[base + t] = Sm.sk[t];
+                }
+                part_sync(bar, TP);
+                if (tid == 0) Sm.icut = 0xffffffffu;
+            }
+            // every CTA reads the leader's count of this attempt; the leader clears the
+            // other parity's counter for the next attempt (its readers, the previous
+            // attempt's, all passed the barrier before this one)
+            cl.sync();
+            ccnt = Ld.cc2[attempt & 1];
+            if (leader && tid == 0) Sm.cc2[(attempt + 1) & 1] = 0;
+            ++attempt;
+        } else {
+            part_sync(bar, TP);
+            ccnt = Sm.ccnt;
+        }
         const uint32_t icut = Sm.icut;
         if (ccnt > CAP) {
             // too many candidates: move tau toward D1 by about log2(ccnt / CAP) halvings;
@@ -600,8 +685,9 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
             part_sync(bar, TP);
             continue;
         }
-        // (4) candidates in index order: slot order is the lowest-index tie-break
-        if (!tie) {
+        // (4) candidates in index order: slot order is the lowest-index tie-break (the
+        //     leader's candidates in cluster mode; the other CTAs wait at the next barrier)
+        if (leader && !tie) {
             uint32_t ci = 0, rank = 0;
             int64_t cd = 0;
             uint64_t ck = 0;
@@ -623,7 +709,7 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
         //     slot lane + 32u lives in lane's register u.  The updates are branch-free (a
         //     branch per register keeps the four updates from overlapping); pick t is
         //     recorded in lane t & 31 and written out after the loop.
-        if (warp == simw) {
+        if (leader && warp == simw) {
             const uint32_t budget = min((uint32_t)MAXP, m - k);
             const bool tiecut = icut != 0xffffffffu;
             uint32_t np = 0;
@@ -757,15 +843,22 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
             if (lane == 0) Sm.npick = np;
         }
         if (tid == 0 && !tie && ccnt < CAP / 4 && shift > 1) Sm.shift = shift - 1;
-        part_sync(bar, TP);
+        if constexpr (CL) cl.sync(); else part_sync(bar, TP);
       }
-        const uint32_t np = Sm.npick;
-        // (6) apply the round's picks to the whole part
+        const uint32_t np = CL ? Ld.npick : Sm.npick;
+        // (6) apply the round's picks to the whole part (cluster mode: to this CTA's
+        //     points; each CTA copies the leader's picks, marks those it owns chosen, and
+        //     the leader writes the outputs)
+        const uint32_t own_lo = sg0 * 32768u, own_hi = sg1 * 32768u;
         for (uint32_t t = tid; t < np; t += TP) {
-            Dg[Sm.pi[t]] = -1;
-            P.perm[k + t] = Sm.pi[t];
-            P.rad2[k + t] = Sm.pd[t];
-            const uint64_t q = Sm.pk[t];
+            const uint32_t pit = Ld.pi[t];
+            const uint64_t q = Ld.pk[t];
+            if (CL && !leader) Sm.pi[t] = pit;
+            if (!CL || (pit >= own_lo && pit < own_hi)) Dg[pit] = -1;
+            if (leader) {
+                P.perm[k + t] = pit;
+                P.rad2[k + t] = Sm.pd[t];
+            }
             Sm.px[t] = (int32_t)pos_x(q);
             Sm.py[t] = (int32_t)pos_y(q);
             Sm.pz[t] = (int32_t)pos_z(q);
@@ -778,7 +871,7 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
         }
         part_sync(bar, TP);
         const uint64_t all = np >= 64 ? ~0ull : ((1ull << np) - 1ull);
-        for (uint32_t sg = warp; sg < ns; sg += NW) {
+        for (uint32_t sg = sg0 + warp; sg < sg1; sg += NW) {
             const uint64_t mk = pick_mask(np, Sm.pi, Sm.px, Sm.py, Sm.pz, all, 15, sg, Sm.sglo[sg], Sm.sghi[sg],
                                           (int64_t)(Sm.sgkey[sg] >> 15) - 1);
             if (mk && lane == 0) {
@@ -913,15 +1006,17 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
         part_sync(bar, TP);
     }
     // the part's radii, then its completion flag (host-mapped memory, after a
-    // system-scope fence so the host sees every output of the part first)
+    // system-scope fence so the host sees every output of the part first).  Cluster
+    // mode: the CTAs share the radii, reading the leader's rad2 from L2 after a barrier
+    if constexpr (CL) cl.sync();
     if (P.radius)
-        for (uint32_t q = tid; q < m; q += TP) {
-            const int64_t r2 = P.rad2[q];
+        for (uint32_t q = (uint32_t)crank * TP + tid; q < m; q += (uint32_t)csize * TP) {
+            const int64_t r2 = CL ? __ldcg(&P.rad2[q]) : P.rad2[q];
             P.radius[q] = r2 == INT64_MAX ? __int_as_float(0x7f800000)
                                           : (float)__ddiv_rn(__dsqrt_rn((double)r2), P.scale);
         }
-    part_sync(bar, TP);
-    if (tid == 0 && P.done) {
+    if constexpr (CL) cl.sync(); else part_sync(bar, TP);
+    if (tid == 0 && leader && P.done) {
         __threadfence_system();
         *(volatile uint32_t *)P.done = 1u;
     }
@@ -959,6 +1054,26 @@ __global__ void __launch_bounds__(CT) k_order_rounds(const PartDesc *__restrict_
     }
 }
 
+// Persistent cluster kernel: each thread-block cluster orders one part at a time on all
+// of its CTAs (the largest parts of a launch; next[0] is the work counter).
+template <int CT>
+__global__ void __launch_bounds__(CT) k_order_cluster(const PartDesc *__restrict__ parts, int nparts,
+                                                      uint32_t *__restrict__ next, int ngmax) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ uint32_t s_part;
+    cg::cluster_group cl = cg::this_cluster();
+    const int crank = (int)cl.block_rank(), csize = (int)cl.num_blocks();
+    for (;;) {
+        if (crank == 0 && threadIdx.x == 0) s_part = atomicAdd(&next[0], 1u);
+        cl.sync();
+        const uint32_t p = *cl.map_shared_rank(&s_part, 0);
+        cl.sync();  // every CTA has its part index before the leader takes the next one
+        if (p >= (uint32_t)nparts) break;
+        rounds_part<CT, MAX_SG, true>(parts[p], *(RoundsSm<MAX_SG> *)smraw, smraw, 0, ngmax, threadIdx.x, 0, 0, crank,
+                                      csize);
+    }
+}
+
 __global__ void k_radius(const PartDesc *__restrict__ parts, int nparts) {
     for (int p = blockIdx.y; p < nparts; p += gridDim.y) {
         const PartDesc P = parts[p];
@@ -985,6 +1100,8 @@ static int g_order_algo = 2;              // 1 = one pick per step, 2 = exact mu
 static int g_ctas_per_sm_override = 0;    // set by bs_set_tuning("order_ctas_per_sm", v)
 static int g_quarters = 0;                // set by bs_set_tuning("order_quarters", v): 0 auto, 1 off, 2 on
 static int g_full_parts = 0;              // set by bs_set_tuning("order_full_parts", k); 0 = cost model
+static int g_cluster = 1;                 // bs_set_tuning("order_cluster", c): 0 auto, 1 off, 2..16 CTAs
+static uint32_t g_cluster_min = 262144;   // bs_set_tuning("order_cluster_min", n): smallest cluster part
 
 void order_set_tuning(int threads, int ctas_per_sm) {
     g_loop_threads_override = threads;
@@ -996,6 +1113,11 @@ void order_set_algo(int algo) { g_order_algo = algo; }
 void order_set_quarters(int v) { g_quarters = v; }
 
 void order_set_full_parts(int k) { g_full_parts = k; }
+
+void order_set_cluster(int c, int min_points) {
+    if (c >= 0) g_cluster = c;
+    if (min_points > 0) g_cluster_min = (uint32_t)min_points;
+}
 
 // Optional per-kernel timing: events recorded on the launch stream around one kernel.
 static bool g_kernel_timing = false;
@@ -1161,6 +1283,57 @@ static cudaError_t launch_set(const PartDesc *d_parts, int nparts, uint32_t *d_n
     }
 }
 
+// Cluster launch over parts[0..nparts) (all of at least csize super-groups, exact
+// ordering): csize CTAs of 1024 threads per part, at most nclusters clusters resident
+// (persistent over the parts).  The cluster size shrinks until the device can hold one.
+static cudaError_t launch_cluster(const PartDesc *d_parts, int nparts, uint32_t *d_next, int ngmax, int csize,
+                                  int nclusters, cudaStream_t stream) {
+    const size_t smem = slot_bytes<MAX_SG>(0, ngmax);
+    auto kern = k_order_cluster<1024>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(1024, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    for (; csize >= 2; --csize) {
+        attr[0].val.clusterDim.x = (unsigned)csize;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)csize, 1, 1);
+        int maxc = 0;
+        if (cudaOccupancyMaxActiveClusters(&maxc, kern, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            maxc = 0;
+        }
+        if (maxc >= 1) {
+            const int nc = std::max(1, std::min(std::min(nclusters, maxc), nparts));
+            cfg.gridDim = dim3((unsigned)(csize * nc), 1, 1);
+            return cudaLaunchKernelEx(&cfg, kern, d_parts, nparts, d_next, ngmax);
+        }
+    }
+    return cudaErrorInvalidConfiguration;
+}
+
+// The library's side stream of the current device (cluster launches beside the rest).
+static cudaStream_t side_stream() {
+    static std::mutex mu;
+    static cudaStream_t streams[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        streams[dev] = nullptr;
+    }
+    return streams[dev];
+}
+
 // Orders nparts parts.  host descriptors: keys, outputs, n, m, start, scale filled in.
 bs_status order_parts(std::vector<PartDesc> &hp, cudaStream_t stream, bool batched) {
     const int nparts = (int)hp.size();
@@ -1220,7 +1393,7 @@ bs_status order_parts(std::vector<PartDesc> &hp, cudaStream_t stream, bool batch
     do {
         if (cudaMemcpyAsync(d_parts, sorted.data(), (size_t)nparts * sizeof(PartDesc), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
             cudaMemcpyAsync(d_gofs, gofs.data(), (size_t)nparts * 4, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
-            cudaMemsetAsync(d_next, 0, 8, stream) != cudaSuccess) {
+            cudaMemsetAsync(d_next, 0, 32, stream) != cudaSuccess) {
             set_error("bs_order: descriptor upload failed: %s", cudaGetErrorString(cudaGetLastError()));
             rc = BS_ECUDA;
             break;
@@ -1240,8 +1413,54 @@ bs_status order_parts(std::vector<PartDesc> &hp, cudaStream_t stream, bool batch
         timing_mark(1, 0, stream);
         std::vector<uint32_t> ns(nparts), ngs(nparts);
         for (int r = 0; r < nparts; ++r) { ns[r] = sorted[r].n; ngs[r] = sorted[r].ng; }
-        e = launch_set(d_parts, nparts, d_next, (int)ngmax, pick_threads((int)ngmax, batched, algo), sms, stream, algo,
-                       ns, ngs);
+        // the largest parts (exact ordering, at least order_cluster_min points) on thread-block
+        // clusters, the rest as before; with both, the clusters run on the side stream
+        int kc = 0, csize = 0;
+        if (algo == 2 && g_cluster != 1) {
+            while (kc < nparts && sorted[kc].variant == 0 && sorted[kc].n >= g_cluster_min) ++kc;
+            if (kc > 0) {
+                const int ns_min = (int)((sorted[kc - 1].ng + 31) / 32);
+                if (g_cluster >= 2) {
+                    csize = g_cluster;
+                } else {
+                    const int budget = kc == nparts ? sms : sms / 2;
+                    csize = std::min(16, ns_min);
+                    while (csize > 2 && kc * csize > budget) --csize;
+                }
+                csize = std::min(csize, ns_min);
+                if (csize < 2) kc = 0;
+            }
+        }
+        if (kc > 0) {
+            const int nclusters = std::max(1, std::min(kc, sms / csize));
+            uint32_t ngc = 1;
+            for (int r = 0; r < kc; ++r) ngc = std::max(ngc, sorted[r].ng);
+            if (kc == nparts) {
+                e = launch_cluster(d_parts, kc, d_next + 4, (int)ngc, csize, nclusters, stream);
+            } else {
+                cudaStream_t side = side_stream();
+                cudaEvent_t ev[2] = {nullptr, nullptr};
+                e = side ? cudaSuccess : cudaErrorNotReady;
+                for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+                if (e == cudaSuccess) e = cudaEventRecord(ev[0], stream);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ev[0], 0);
+                if (e == cudaSuccess) e = launch_cluster(d_parts, kc, d_next + 4, (int)ngc, csize, nclusters, side);
+                if (e == cudaSuccess) {
+                    std::vector<uint32_t> ns2(ns.begin() + kc, ns.end()), ngs2(ngs.begin() + kc, ngs.end());
+                    uint32_t ngr = 1;
+                    for (int r = kc; r < nparts; ++r) ngr = std::max(ngr, sorted[r].ng);
+                    e = launch_set(d_parts + kc, nparts - kc, d_next, (int)ngr,
+                                   pick_threads((int)ngr, batched, algo), sms, stream, algo, ns2, ngs2);
+                }
+                if (e == cudaSuccess) e = cudaEventRecord(ev[1], side);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, ev[1], 0);
+                for (int i = 0; i < 2; ++i)
+                    if (ev[i]) cudaEventDestroy(ev[i]);
+            }
+        } else {
+            e = launch_set(d_parts, nparts, d_next, (int)ngmax, pick_threads((int)ngmax, batched, algo), sms, stream,
+                           algo, ns, ngs);
+        }
         timing_mark(1, 1, stream);
         if (e != cudaSuccess) {
             set_error("bs_order: loop launch failed: %s", cudaGetErrorString(e));
