@@ -355,6 +355,10 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
     // the leader's candidate state (this CTA's own outside cluster mode)
     RoundsSm<SG> &Ld = CL ? *cl.map_shared_rank(&Sm, 0) : Sm;
     uint32_t attempt = 0;  // gather attempts of this part (cluster mode: picks the leader's counter)
+    // a part of one super-group (most parts of a batch) keeps no super-group key: every
+    // warp takes it from the group keys when it looks for the round's maximum, so the
+    // key update and its barrier at the end of the round are skipped
+    const bool one_sg = !CL && ns == 1 && P.variant == 0;
     // bucket records: shared memory when they fit (generic pointers either way)
     const bool bsm = !CL && nb <= (uint32_t)nbsm;
     uint64_t *bkey = bsm ? s_bkey : P.bkey;
@@ -515,9 +519,16 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
         // (1) current maximum (every warp computes it; no barrier needed).  Cluster mode:
         //     each CTA's best over its own super-groups, combined after a cluster barrier
         //     (super-group indices are global, so the largest key is the global argmax)
-        uint64_t top = 0;
-        for (uint32_t sg = sg0 + lane; sg < sg1; sg += 32) top = max(top, ((Sm.sgkey[sg] >> 15) << 8) | (uint64_t)(255 - sg));
-        top = warp_max_u64(top);
+        uint64_t top = 0, sk1 = 0;
+        if (one_sg) {
+            const uint64_t gk = lane < (int)ng ? s_gkey[lane] : 0ull;
+            sk1 = warp_max_u64(lane < (int)ng ? (((gk >> 10) << 15) | (uint64_t)(32767 - (lane * 1024 + (1023 - (int)(gk & 1023)))))
+                                              : 0ull);
+            top = ((sk1 >> 15) << 8) | 255ull;
+        } else {
+            for (uint32_t sg = sg0 + lane; sg < sg1; sg += 32) top = max(top, ((Sm.sgkey[sg] >> 15) << 8) | (uint64_t)(255 - sg));
+            top = warp_max_u64(top);
+        }
         if constexpr (CL) {
             if (tid == 0) Sm.ctop = top;
             cl.sync();
@@ -543,7 +554,7 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
                     while (r + 1 < csize && sg >= (uint32_t)(((uint64_t)(r + 1) * ns) / (uint32_t)csize)) ++r;
                     return r;
                 };
-                const uint64_t sgkj = CL ? cl.map_shared_rank(&Sm, owner(sgj))->sgkey[sgj] : Sm.sgkey[sgj];
+                const uint64_t sgkj = CL ? cl.map_shared_rank(&Sm, owner(sgj))->sgkey[sgj] : (one_sg ? sk1 : Sm.sgkey[sgj]);
                 const uint32_t j = sgj * 32768u + (32767u - (uint32_t)(sgkj & 32767u));
                 uint32_t cnt = 0, icut = n, used = 0;
                 bool full = false;
@@ -584,7 +595,7 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
             }
         } else {
             for (uint32_t sg = sg0 + tid; sg < sg1; sg += TP)
-                if ((int64_t)(Sm.sgkey[sg] >> 15) - 1 >= tau) Sm.sglist[atomicAdd(&Sm.sgcnt, 1u)] = sg;
+                if (one_sg || (int64_t)(Sm.sgkey[sg] >> 15) - 1 >= tau) Sm.sglist[atomicAdd(&Sm.sgcnt, 1u)] = sg;
             part_sync(bar, TP);
             const uint32_t nsgl = Sm.sgcnt;
             for (uint32_t li = warp; li < nsgl; li += NW) {
@@ -873,7 +884,7 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
         const uint64_t all = np >= 64 ? ~0ull : ((1ull << np) - 1ull);
         for (uint32_t sg = sg0 + warp; sg < sg1; sg += NW) {
             const uint64_t mk = pick_mask(np, Sm.pi, Sm.px, Sm.py, Sm.pz, all, 15, sg, Sm.sglo[sg], Sm.sghi[sg],
-                                          (int64_t)(Sm.sgkey[sg] >> 15) - 1);
+                                          one_sg ? INT64_MAX : (int64_t)(Sm.sgkey[sg] >> 15) - 1);
             if (mk && lane == 0) {
                 Sm.sgmask[sg] = mk;
                 Sm.sglist[atomicAdd(&Sm.asgcnt, 1u)] = sg;
@@ -994,16 +1005,20 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
             if (lane == 0) s_gkey[g] = ngk;
         }
         part_sync(bar, TP);
-        for (uint32_t li = warp; li < nsgl; li += NW) {
-            const uint32_t sg = Sm.sglist[li];
-            const uint32_t g = sg * 32 + lane;
-            const uint64_t gk = g < ng ? s_gkey[g] : 0ull;
-            const uint64_t cand = g < ng ? (((gk >> 10) << 15) | (uint64_t)(32767 - (lane * 1024 + (1023 - (int)(gk & 1023))))) : 0ull;
-            const uint64_t sk = warp_max_u64(cand);
-            if (lane == 0) Sm.sgkey[sg] = sk;
+        if (!one_sg) {
+            for (uint32_t li = warp; li < nsgl; li += NW) {
+                const uint32_t sg = Sm.sglist[li];
+                const uint32_t g = sg * 32 + lane;
+                const uint64_t gk = g < ng ? s_gkey[g] : 0ull;
+                const uint64_t cand = g < ng ? (((gk >> 10) << 15) | (uint64_t)(32767 - (lane * 1024 + (1023 - (int)(gk & 1023))))) : 0ull;
+                const uint64_t sk = warp_max_u64(cand);
+                if (lane == 0) Sm.sgkey[sg] = sk;
+            }
         }
         k += np;
-        part_sync(bar, TP);
+        // the next round reads the super-group keys; one_sg parts read only group keys,
+        // which the bucket updates wrote before the last barrier
+        if (!one_sg) part_sync(bar, TP);
     }
     // the part's radii, then its completion flag (host-mapped memory, after a
     // system-scope fence so the host sees every output of the part first).  Cluster
