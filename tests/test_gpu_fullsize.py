@@ -67,6 +67,21 @@ def test_batch_subset_bit_exact(batch):
         assert np.array_equal(radius.cpu().numpy().view(np.uint32), oracle.radius(rr, s).view(np.uint32)), i
 
 
+def test_batch_largest_parts_equal_the_oracle(batch):
+    """The three largest parts of the batch (421k-475k surfels), ordered inside the full
+    4096-part launch: their whole perm / rad2 / radius equal the oracle's complete
+    O(N^2) orderings, stored as digests by tests/golden/make_order_golden.py."""
+    import golden_order as G
+    bs, specs, meshes, sv, orders = batch
+    ns = np.array([s["n"] for s in sv])
+    recs = G.read("batch4096_largest_order.txt")
+    assert sorted(r["id"] for r in recs) == sorted(int(i) for i in np.argsort(-ns)[:3])
+    for r in recs:
+        i = r["id"]
+        perm, rad2, radius = (t.cpu().numpy() for t in orders[i])
+        G.check(r, sv[i]["key"].cpu().numpy().view(np.uint64), perm, rad2, radius)
+
+
 def test_batch_largest_parts_properties(batch):
     """The largest parts: a permutation with non-increasing radii whose first 500 entries
     equal the oracle's truncated ordering, and sampled prefixes that are r-separated."""
