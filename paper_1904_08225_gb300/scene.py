@@ -17,6 +17,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import bs
+from . import shard
 from . import workloads as W
 
 # Raster resolution per node level.  Node images are squares over the node's cube extent
@@ -51,10 +52,14 @@ def _verts_per_part(nboxes, ncyl):
 
 
 def run(seed: int = 0, lines: int = 20, per_line: int = 2500, group: int = 50, nboxes: int = 200, ncyl: int = 50,
-        keep=(), leaf_wave: int = 2048, group_wave: int = 32, levels=(0, 1, 2), level_res=None) -> SceneResult:
+        keep=(), leaf_wave: int = 2048, group_wave: int = 32, levels=(0, 1, 2), level_res=None, world: int = 1,
+        rank: int = 0) -> SceneResult:
     """Samples and orders every node; returns totals and the outputs of the nodes in `keep`.
 
-    Node i's ordering starts from the Philox start of (seed, part_id=i)."""
+    Node i's ordering starts from the Philox start of (seed, part_id=i), so a node's result
+    does not depend on which rank orders it.  With world > 1 this rank takes only its
+    share of each level's nodes: the longest-processing-time assignment by triangle count
+    (shard.lpt_assign), no collective on the data path."""
     import torch
     dirs = W.AXIS_DIRS
     nodes = W.scene_nodes(lines, per_line, group)
@@ -117,6 +122,9 @@ def run(seed: int = 0, lines: int = 20, per_line: int = 2500, group: int = 50, n
     by_level = {0: [], 1: [], 2: []}
     for i, nd in enumerate(nodes):
         by_level[nd.level].append(i)
+    if world > 1:
+        for lv_, ids_ in by_level.items():
+            by_level[lv_] = [ids_[j] for j in shard.shard([nodes[i].count * tp for i in ids_], world, rank)]
     # leaves in waves of single parts, groups in waves of nodes, one line at a time.  Waves
     # alternate between two streams: a wave's sampling call returns once its surfels exist
     # and its ordering then runs on the GPU while the next wave is generated and sampled.

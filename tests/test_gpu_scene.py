@@ -94,6 +94,28 @@ def test_reduced_scene_every_node(bs):
         _check_node(seed, i, nd, per_line, nb, nc, level_res[nd.level], out.kept[i])
 
 
+def test_scene_lpt_shards_cover_every_node_once(bs):
+    """The scene's nodes split over two ranks by LPT (run here one rank after the other on
+    one GPU; ranks share nothing): the shards are disjoint, cover every node, and each
+    node's output equals the unsharded run's."""
+    from paper_1904_08225_gb300 import scene
+    seed, lines, per_line, group, nb, nc = 21, 2, 7, 3, 20, 5
+    level_res = {0: 96, 1: 256, 2: 1024}
+    nodes = W.scene_nodes(lines, per_line, group)
+    full = scene.run(seed, lines, per_line, group, nb, nc, keep=range(len(nodes)), leaf_wave=5, group_wave=2,
+                     level_res=level_res)
+    parts = [scene.run(seed, lines, per_line, group, nb, nc, keep=range(len(nodes)), leaf_wave=5, group_wave=2,
+                       level_res=level_res, world=2, rank=r) for r in range(2)]
+    assert parts[0].nodes > 0 and parts[1].nodes > 0
+    assert not set(parts[0].kept) & set(parts[1].kept)
+    assert sorted(list(parts[0].kept) + list(parts[1].kept)) == list(range(len(nodes)))
+    assert parts[0].surfels_ordered + parts[1].surfels_ordered == full.surfels_ordered
+    for pr in parts:
+        for i, (key, perm, rad2) in pr.kept.items():
+            fk, fp, fr = full.kept[i]
+            assert np.array_equal(key, fk) and np.array_equal(perm, fp) and np.array_equal(rad2, fr), i
+
+
 def _invariants(key, perm, rad2, picks):
     P = oracle.unpack(key[perm])
     assert len(np.unique(perm)) == len(perm) and perm.max() < len(key)

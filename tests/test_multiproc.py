@@ -50,3 +50,70 @@ def test_two_gloo_ranks_shard_parts_and_take_max_time():
     assert ms0 == ms1 == 15.0                    # both ranks see the slowest rank's time
     assert not set(seeds0) & set(seeds1)         # disjoint parts per rank
     assert tot0 == tot1 > 0
+
+
+def _shard_worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import oracle
+    from paper_1904_08225_gb300 import shard
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    keys = _seeded_parts()
+
+    def oracle_fn(ks, ids):
+        return [oracle.greedy(k, oracle.start_index(len(k), seed=5, part_id=i), nthreads=1) for k, i in zip(ks, ids)]
+
+    got = shard.order_sharded(keys, oracle_fn, world=world, rank=rank, dist=dist)
+    mine = shard.shard([len(k) for k in keys], world, rank)
+    q.put((rank, mine, None if got is None else [(p.tobytes(), r.tobytes()) for p, r in got]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def _seeded_parts():
+    import oracle
+    g = np.random.default_rng(11)
+    out = []
+    for n in g.integers(50, 2500, size=23):
+        pts = np.unique(g.integers(0, 1 << 16, size=(int(n) + 20, 3)), axis=0)[:int(n)]
+        out.append(oracle.pack(pts))
+    return out
+
+
+def test_lpt_assignment():
+    from paper_1904_08225_gb300 import shard
+    sizes = [1000, 50, 50, 999, 400, 400, 10, 2000]
+    a = shard.lpt_assign(sizes, 3)
+    assert sorted(i for r in a for i in r) == list(range(len(sizes)))
+    loads = [sum(shard.part_cost(sizes[i]) for i in r) for r in a]
+    # LPT: the largest part alone first; every rank within the largest part's cost of the others
+    assert a[0][0] == 7 or 7 in a[0]
+    assert max(loads) - min(loads) <= shard.part_cost(2000)
+    assert shard.lpt_assign(sizes, 1) == [list(range(len(sizes)))]
+    assert shard.lpt_assign([], 4) == [[], [], [], []]
+    with pytest.raises(ValueError):
+        shard.shard(sizes, 2, 2)
+
+
+def test_two_gloo_ranks_order_lpt_shards_and_gather():
+    """Two gloo ranks each order their LPT shard of one seeded part set (the oracle as the
+    ordering function, on CPU); rank 0's gathered results equal a single-rank run."""
+    import oracle
+    from paper_1904_08225_gb300 import shard
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=240) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (r0, mine0, got0), (r1, mine1, got1) = out
+    assert got1 is None and got0 is not None
+    assert mine0 and mine1 and not set(mine0) & set(mine1)
+    keys = _seeded_parts()
+    assert sorted(mine0 + mine1) == list(range(len(keys)))
+    single = shard.order_sharded(keys, lambda ks, ids: [oracle.greedy(k, oracle.start_index(len(k), seed=5, part_id=i),
+                                                                       nthreads=1) for k, i in zip(ks, ids)])
+    assert [(p.tobytes(), r.tobytes()) for p, r in single] == got0
