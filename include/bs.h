@@ -31,10 +31,11 @@ typedef enum {
     BS_EINVAL = 1,     /* argument out of range, non-finite vertex, zero extent */
     BS_ENOMEM = 2,     /* device scratch or admission budget exhausted */
     BS_EOVERFLOW = 3,  /* output capacity too small (the needed size is reported) */
-    BS_ETIMEOUT = 4,   /* a bounded device wait ran out of iterations */
+    BS_ETIMEOUT = 4,   /* a bounded wait ran out (a server request past its timeout) */
     BS_EBUSY = 5,      /* server queue full; retry later */
     BS_ECUDA = 6,      /* CUDA runtime error */
-    BS_ENOTREADY = 7   /* server result not finished yet */
+    BS_ENOTREADY = 7,  /* server result not finished yet */
+    BS_ECANCELED = 8   /* server request cancelled by bs_server_cancel */
 } bs_status;
 
 /* Largest quantised coordinate: positions are integers in [0, 2^21 - 1]. */
@@ -323,14 +324,24 @@ bs_status bs_server_submit(bs_server *srv, const uint64_t *key, uint64_t n, doub
  * (m entries; rad2/radius may be NULL) and releases it.  With perm == NULL the
  * call only reports the status (BS_OK when ready) and keeps the result.
  * BS_ENOTREADY while the request is queued or running; BS_EINVAL for an
- * unknown or already collected ticket.  The server's own host thread admits,
- * launches and retires requests; polling does not drive it. */
+ * unknown or already collected ticket; BS_ECANCELED for a cancelled one; the
+ * request's own error for a failed one (BS_ENOMEM when its launch could not get
+ * device memory, BS_ETIMEOUT when it stayed on the device longer than the
+ * server's timeout).  The server's own host thread admits, launches and retires
+ * requests; polling does not drive it. */
 bs_status bs_server_poll(bs_server *srv, uint64_t ticket, uint32_t *perm, int64_t *rad2, float *radius);
 
 /* Per-ticket timestamps in seconds on the server's monotonic clock:
  * t[0] submit, t[1] admitted to the device, t[2] finished on the device.
  * Valid after bs_server_poll returned BS_OK for the ticket. */
 bs_status bs_server_times(bs_server *srv, uint64_t ticket, double t[3]);
+
+/* Cancels a request.  A queued one leaves the queue at once; one on the device is
+ * dropped when its launch ends (the kernel is not interrupted), which then releases
+ * its device memory and budget; a finished, uncollected result is dropped.  Polling
+ * the ticket afterwards returns BS_ECANCELED.  BS_EINVAL for an unknown ticket or a
+ * request that already failed or was collected. */
+bs_status bs_server_cancel(bs_server *srv, uint64_t ticket);
 
 /* Waits for all in-flight work, frees device memory and the server. */
 void bs_server_destroy(bs_server *srv);
@@ -365,6 +376,11 @@ bs_status bs_scene_generate(uint64_t seed, const uint64_t *part_ids, const int32
  *                       (0 = the cost model decides)
  *  "server_slots"       launches a server created afterwards keeps in flight (1..256,
  *                       16 by default; each holds 64 MB of pinned result staging)
+ *  "server_timeout_ms"  a request of a server created afterwards that is still on the
+ *                       device this long after its launch fails with BS_ETIMEOUT
+ *                       (0 = no timeout, the default)
+ *  "fail_next_allocs"   the library's next k device-scratch allocations fail as if the
+ *                       device were out of memory (error-path tests; host-side only)
  *  "pool_keep_mb"       freed scratch the library's per-device memory pool keeps for the
  *                       next call, in MiB (65536 by default; lowering it trims the pool)
  *  "order_cluster"      parts of at least "order_cluster_min" points (exact ordering)

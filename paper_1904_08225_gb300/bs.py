@@ -16,14 +16,14 @@ import numpy as np
 
 from . import build as _build
 
-BS_OK, BS_EINVAL, BS_ENOMEM, BS_EOVERFLOW, BS_ETIMEOUT, BS_EBUSY, BS_ECUDA, BS_ENOTREADY = range(8)
+BS_OK, BS_EINVAL, BS_ENOMEM, BS_EOVERFLOW, BS_ETIMEOUT, BS_EBUSY, BS_ECUDA, BS_ENOTREADY, BS_ECANCELED = range(9)
 STATUS_NAMES = ["BS_OK", "BS_EINVAL", "BS_ENOMEM", "BS_EOVERFLOW", "BS_ETIMEOUT", "BS_EBUSY", "BS_ECUDA",
-                "BS_ENOTREADY"]
+                "BS_ENOTREADY", "BS_ECANCELED"]
 INT64_MAX = (1 << 63) - 1
 
 # symbols include/bs.h declares; the library must export every one
 EXPORTS = ["bs_sample_visible", "bs_sample_visible_batched", "bs_order", "bs_order_noalloc", "bs_order_batched", "bs_server_create", "bs_server_submit",
-           "bs_server_poll", "bs_server_times", "bs_server_destroy", "bs_set_tuning", "bs_last_launch_ms",
+           "bs_server_poll", "bs_server_times", "bs_server_cancel", "bs_server_destroy", "bs_set_tuning", "bs_last_launch_ms",
            "bs_prefix_median_nn", "bs_prefix_for_radius", "bs_prefix_estimate", "bs_scene_generate", "bs_sample_splats",
            "bs_prefix_for_radius_batched", "bs_render_mesh", "bs_render_splats", "bs_parent_frames",
            "bs_last_error"]
@@ -31,7 +31,7 @@ EXPORTS = ["bs_sample_visible", "bs_sample_visible_batched", "bs_order", "bs_ord
 
 class BsError(RuntimeError):
     def __init__(self, status: int, where: str, msg: str):
-        super().__init__(f"{where}: {STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        super().__init__(f"{where}: {STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
         self.status = status
 
 
@@ -100,6 +100,7 @@ def load(build_if_stale: bool = True) -> C.CDLL:
             lib.bs_server_poll.argtypes = [P, C.c_uint64, P, P, P]
             lib.bs_server_times.argtypes = [P, C.c_uint64, P]
             lib.bs_server_destroy.argtypes = [P]
+            lib.bs_server_cancel.argtypes = [P, C.c_uint64]
             lib.bs_set_tuning.argtypes = [C.c_char_p, C.c_int]
             lib.bs_last_launch_ms.argtypes = [C.c_char_p, C.POINTER(C.c_double)]
             lib.bs_prefix_median_nn.argtypes = [C.POINTER(Surfels), P, C.c_uint64, C.POINTER(C.c_int64), P]
@@ -651,6 +652,10 @@ class Server:
             return None
         _check(st, "bs_server_poll")
         return perm, rad2, radius
+
+    def cancel(self, ticket: int) -> None:
+        """bs_server_cancel: the request is dropped (polling it then raises BS_ECANCELED)."""
+        _check(self._lib.bs_server_cancel(self._h, ticket), "bs_server_cancel")
 
     def times(self, ticket: int):
         t = (C.c_double * 3)()

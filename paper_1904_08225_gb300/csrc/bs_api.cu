@@ -76,14 +76,27 @@ using namespace bs;
 namespace bs {
 // launch slots of servers created from now on (bs_set_tuning("server_slots", v))
 int g_server_slots = 16;
+// request timeout of servers created from now on (bs_set_tuning("server_timeout_ms", v); 0 = none)
+int g_server_timeout_ms = 0;
 }  // namespace bs
 using bs::g_server_slots;
+using bs::g_server_timeout_ms;
 
 extern "C" {
 
 const char *bs_last_error(void) { return g_err; }
 
 bs_status bs_set_tuning(const char *name, int value) {
+    if (name && !strcmp(name, "server_timeout_ms")) {
+        if (value < 0) { set_error("bs_set_tuning: server_timeout_ms=%d negative", value); return BS_EINVAL; }
+        g_server_timeout_ms = value;
+        return BS_OK;
+    }
+    if (name && !strcmp(name, "fail_next_allocs")) {
+        if (value < 0) { set_error("bs_set_tuning: fail_next_allocs=%d negative", value); return BS_EINVAL; }
+        pool_fail_next(value);
+        return BS_OK;
+    }
     if (name && !strcmp(name, "server_slots")) {
         if (value < 1 || value > 256) { set_error("bs_set_tuning: server_slots=%d outside [1, 256]", value); return BS_EINVAL; }
         g_server_slots = value;
@@ -266,13 +279,17 @@ struct SrvReq {
     double scale;
     bs_order_opts opts;
     uint64_t n, m, bytes;
-    char *dmem;  // device block: key | perm | rad2 | radius
+    uint64_t *dk;   // its keys and outputs inside the launch's device block
+    uint32_t *dp;
+    int64_t *dr;
+    float *df;
     size_t stage_off;
     std::vector<uint32_t> perm;
     std::vector<int64_t> rad2;
     std::vector<float> radius;
     double t[3];
-    int state;  // 0 queued, 1 running, 5 copying its result, 2 done, 3 failed, 4 collected
+    int state;  // 0 queued, 1 running, 5 copying its result, 2 done, 3 failed, 4 collected, 6 cancelled
+    bool cancel;  // cancelled while on the device: its result is dropped when the launch ends
     bs_status err;
     uint32_t flag;          // index of its completion flag in the slot
     cudaEvent_t copied;     // recorded on the copy stream after its result copies
@@ -287,6 +304,9 @@ struct SrvSlot {
     std::vector<SrvReq *> reqs;
     char *stage = nullptr;  // pinned host staging for results
     size_t stage_cap = 0;
+    char *kstage = nullptr;  // pinned host staging for the launch's keys (one upload)
+    size_t kstage_cap = 0;
+    char *dblock = nullptr;  // the launch's device block: every request's keys, then outputs
     uint32_t *flags_h = nullptr;  // host-mapped completion flags, set by the ordering kernel
     uint32_t *flags_d = nullptr;  // the same memory as the device sees it
     bool busy = false;
@@ -304,11 +324,13 @@ struct bs_server {
     std::unordered_map<uint64_t, bs::SrvReq *> all;
     std::vector<bs::SrvSlot> slots;
     cudaStream_t copy = nullptr;  // device-to-host copies of finished requests
+    cudaEvent_t copy_tail = nullptr;  // the copy stream's last work, ordered before a launch's memory is freed
     uint64_t next_ticket = 1;
     bool stop = false;
     std::thread driver;
     std::chrono::steady_clock::time_point t0;
     size_t max_queue = 1u << 20;
+    double timeout_s = 0.0;  // a request on the device longer than this fails with BS_ETIMEOUT (0: none)
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
@@ -325,11 +347,22 @@ static size_t req_bytes(uint64_t n) {
 }
 
 // Releases a finished launch: device memory and budget (every request's result has
-// been copied by then, see driver_loop).
+// been copied by then, see driver_loop).  A request cancelled on the device ends here.
 static void retire(bs_server *S, SrvSlot &slot) {
+    // a request that timed out may still have its result copy in flight on the copy
+    // stream: the block is freed after it
+    if (slot.dblock && cudaEventRecord(S->copy_tail, S->copy) == cudaSuccess)
+        cudaStreamWaitEvent(slot.stream, S->copy_tail, 0);
+    if (slot.dblock) cudaFreeAsync(slot.dblock, slot.stream);
+    slot.dblock = nullptr;
     for (SrvReq *r : slot.reqs) {
-        if (r->dmem) cudaFreeAsync(r->dmem, slot.stream);
-        r->dmem = nullptr;
+        r->dk = nullptr; r->dp = nullptr; r->dr = nullptr; r->df = nullptr;
+        if (r->cancel && r->state != 4) {
+            r->state = 6;
+            std::vector<uint32_t>().swap(r->perm);
+            std::vector<int64_t>().swap(r->rad2);
+            std::vector<float>().swap(r->radius);
+        }
         if (r->copied) {
             cudaEventDestroy(r->copied);
             r->copied = nullptr;
@@ -344,13 +377,10 @@ static void retire(bs_server *S, SrvSlot &slot) {
 // Starts the device-to-host copy of a request whose part has finished (its flag is
 // set) on the copy stream, while the rest of the launch keeps running.
 static void start_copy(bs_server *S, SrvSlot &slot, SrvReq *r) {
-    const uint32_t *dp = (const uint32_t *)(r->dmem + align256(r->n * 8));
-    const int64_t *dr = (const int64_t *)(r->dmem + align256(r->n * 8) + align256(r->m * 4));
-    const float *df = (const float *)(r->dmem + align256(r->n * 8) + align256(r->m * 4) + align256(r->m * 8));
     char *st = slot.stage + r->stage_off;
-    cudaMemcpyAsync(st, dp, r->m * 4, cudaMemcpyDeviceToHost, S->copy);
-    cudaMemcpyAsync(st + align256(r->m * 4), dr, r->m * 8, cudaMemcpyDeviceToHost, S->copy);
-    cudaMemcpyAsync(st + align256(r->m * 4) + align256(r->m * 8), df, r->m * 4, cudaMemcpyDeviceToHost, S->copy);
+    cudaMemcpyAsync(st, r->dp, r->m * 4, cudaMemcpyDeviceToHost, S->copy);
+    cudaMemcpyAsync(st + align256(r->m * 4), r->dr, r->m * 8, cudaMemcpyDeviceToHost, S->copy);
+    cudaMemcpyAsync(st + align256(r->m * 4) + align256(r->m * 8), r->df, r->m * 4, cudaMemcpyDeviceToHost, S->copy);
     if (!r->copied && cudaEventCreateWithFlags(&r->copied, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         r->copied = nullptr;
@@ -366,44 +396,64 @@ static void finish_copy(SrvSlot &slot, SrvReq *r) {
     memcpy(r->radius.data(), st + align256(r->m * 4) + align256(r->m * 8), r->m * 4);
 }
 
-// The device work of a launch: memory, host-to-device keys, the ordering launch.  Runs
-// without the server lock; it touches only the slot and fields of the batch's requests
-// that no other thread reads (the requests are still "queued" to poll and times).
-// err[i] receives each request's outcome (BS_OK when it runs).
+// Grows a pinned host staging buffer to at least `need` bytes (twice that when it grows).
+static bool ensure_pinned(char **buf, size_t *cap, size_t need) {
+    if (need <= *cap) return true;
+    if (*buf) cudaFreeHost(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    if (cudaHostAlloc((void **)buf, need * 2, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        *buf = nullptr;
+        return false;
+    }
+    *cap = need * 2;
+    return true;
+}
+
+// The device work of a launch: one device block for every request's keys and outputs,
+// the keys gathered into pinned staging and uploaded in one copy, the ordering launch.
+// Runs without the server lock; it touches only the slot and fields of the batch's
+// requests that no other thread reads (the requests are still "queued" to poll and
+// times).  err[i] receives each request's outcome (BS_OK when it runs); when the block
+// cannot be had, every request of the launch fails with BS_ENOMEM and the device is
+// left as it was.
 static void launch_batch(bs_server *S, SrvSlot &slot, std::vector<SrvReq *> &batch, std::vector<bs_status> &err) {
-    // device memory, H2D keys, ordering, D2H results into pinned staging
-    size_t stage = 0;
+    size_t stage = 0, keys = 0, outs = 0;
     for (SrvReq *r : batch) {
         r->stage_off = stage;
         stage += align256(r->m * 4) + align256(r->m * 8) + align256(r->m * 4);
+        keys += align256(r->n * 8);
+        outs += align256(r->m * 4) + align256(r->m * 8) + align256(r->m * 4);
     }
-    if (stage > slot.stage_cap) {
-        if (slot.stage) cudaFreeHost(slot.stage);
-        slot.stage = nullptr;
-        slot.stage_cap = 0;
-        if (cudaHostAlloc((void **)&slot.stage, stage * 2, cudaHostAllocDefault) == cudaSuccess) slot.stage_cap = stage * 2;
-        else cudaGetLastError();
+    err.assign(batch.size(), BS_OK);
+    bool ok = ensure_pinned(&slot.stage, &slot.stage_cap, stage) && ensure_pinned(&slot.kstage, &slot.kstage_cap, keys);
+    if (ok && pool_malloc_async((void **)&slot.dblock, keys + outs, slot.stream) != cudaSuccess) {
+        cudaGetLastError();
+        slot.dblock = nullptr;
+        ok = false;
+    }
+    if (!ok) {
+        for (size_t i = 0; i < batch.size(); ++i) err[i] = BS_ENOMEM;
+        cudaEventRecord(slot.done, slot.stream);
+        return;
     }
     std::vector<PartDesc> parts;
-    std::vector<size_t> run;
-    err.assign(batch.size(), BS_OK);
+    parts.reserve(batch.size());
+    size_t ko = 0, oo = keys;
     for (size_t i = 0; i < batch.size(); ++i) {
         SrvReq *r = batch[i];
-        bool ok = slot.stage != nullptr;
-        if (ok && pool_malloc_async((void **)&r->dmem, r->bytes, slot.stream) != cudaSuccess) {
-            cudaGetLastError();
-            ok = false;
-        }
-        if (!ok) { err[i] = BS_ENOMEM; r->dmem = nullptr; continue; }
-        uint64_t *dk = (uint64_t *)r->dmem;
-        uint32_t *dp = (uint32_t *)(r->dmem + align256(r->n * 8));
-        int64_t *dr = (int64_t *)(r->dmem + align256(r->n * 8) + align256(r->m * 4));
-        float *df = (float *)(r->dmem + align256(r->n * 8) + align256(r->m * 4) + align256(r->m * 8));
-        cudaMemcpyAsync(dk, r->key.data(), r->n * 8, cudaMemcpyHostToDevice, slot.stream);
-        std::vector<uint64_t>().swap(r->key);  // a pageable-source copy has been staged when the call returns
+        memcpy(slot.kstage + ko, r->key.data(), r->n * 8);
+        std::vector<uint64_t>().swap(r->key);
+        r->dk = (uint64_t *)(slot.dblock + ko);
+        ko += align256(r->n * 8);
+        r->dp = (uint32_t *)(slot.dblock + oo);
+        r->dr = (int64_t *)(slot.dblock + oo + align256(r->m * 4));
+        r->df = (float *)(slot.dblock + oo + align256(r->m * 4) + align256(r->m * 8));
+        oo += align256(r->m * 4) + align256(r->m * 8) + align256(r->m * 4);
         PartDesc p;
         memset(&p, 0, sizeof(p));
-        p.key = dk; p.perm = dp; p.rad2 = dr; p.radius = df; p.scale = r->scale;
+        p.key = r->dk; p.perm = r->dp; p.rad2 = r->dr; p.radius = r->df; p.scale = r->scale;
         r->flag = (uint32_t)parts.size();
         slot.flags_h[r->flag] = 0u;
         p.done = slot.flags_d + r->flag;
@@ -415,12 +465,15 @@ static void launch_batch(bs_server *S, SrvSlot &slot, std::vector<SrvReq *> &bat
         p.part_id = r->opts.part_id;
         p.seed = r->opts.seed;
         parts.push_back(p);
-        run.push_back(i);
     }
-    if (!parts.empty()) {
-        bs_status st = order_parts(parts, slot.stream, true);
+    if (cudaMemcpyAsync(slot.dblock, slot.kstage, keys, cudaMemcpyHostToDevice, slot.stream) != cudaSuccess) {
+        set_error("bs_server: key upload failed: %s", cudaGetErrorString(cudaGetLastError()));
+        for (size_t i = 0; i < batch.size(); ++i) err[i] = BS_ECUDA;
+    } else {
+        // several requests share the GPU as quarters of CTAs, like a large batch
+        const bs_status st = order_parts(parts, slot.stream, true, true);
         if (st != BS_OK)
-            for (size_t i : run) err[i] = st;
+            for (size_t i = 0; i < batch.size(); ++i) err[i] = st;
     }
     cudaEventRecord(slot.done, slot.stream);
 }
@@ -443,9 +496,19 @@ static void driver_loop(bs_server *S) {
         to_finish.clear();
         copy_owner.clear();
         finish_owner.clear();
+        const double tnow = S->now();
         for (SrvSlot &slot : S->slots) {
             if (!slot.busy) continue;
             for (SrvReq *r : slot.reqs) {
+                if ((r->state == 1 || r->state == 5) && S->timeout_s > 0.0 && tnow - r->t[1] > S->timeout_s) {
+                    // a bounded wait: the request fails now; its launch keeps running and its
+                    // memory and budget are released when the launch ends
+                    r->state = 3;
+                    r->err = BS_ETIMEOUT;
+                    r->t[2] = tnow;
+                    progressed = true;
+                    continue;
+                }
                 if (r->state == 1 && ((volatile uint32_t *)slot.flags_h)[r->flag] != 0u) {
                     to_copy.push_back(r);
                     copy_owner.push_back(&slot);
@@ -464,15 +527,18 @@ static void driver_loop(bs_server *S) {
             for (size_t i = 0; i < to_finish.size(); ++i) finish_copy(*finish_owner[i], to_finish[i]);
             lk.lock();
             const double t = S->now();
-            for (SrvReq *r : to_copy) r->state = 5;
-            for (SrvReq *r : to_finish) { r->t[2] = t; r->state = 2; }
+            // (a request that timed out meanwhile keeps its failed state)
+            for (SrvReq *r : to_copy)
+                if (r->state == 1) r->state = 5;
+            for (SrvReq *r : to_finish)
+                if (r->state == 5) { r->t[2] = t; r->state = 2; }
             progressed = true;
         }
         // 2. launches whose every request is finished
         for (SrvSlot &slot : S->slots) {
             if (!slot.busy) continue;
             bool all_done = true;
-            for (SrvReq *r : slot.reqs) all_done &= r->state == 2 || r->state == 3 || r->state == 4;
+            for (SrvReq *r : slot.reqs) all_done &= r->state == 2 || r->state == 3 || r->state == 4 || r->state == 6;
             if (all_done && cudaEventQuery(slot.done) == cudaSuccess) {
                 retire(S, slot);
                 progressed = true;
@@ -531,9 +597,11 @@ bs_server *bs_server_create(uint64_t device_budget_bytes, int max_inflight, bs_s
     cudaGetDevice(&S->device);
     S->budget = device_budget_bytes;
     S->max_inflight = max_inflight ? max_inflight : 4096;
+    S->timeout_s = g_server_timeout_ms * 1e-3;
     S->t0 = std::chrono::steady_clock::now();
     S->slots.resize((size_t)g_server_slots);  // launches in flight at once: each holds the requests queued when it started
-    if (cudaStreamCreateWithFlags(&S->copy, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&S->copy, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&S->copy_tail, cudaEventDisableTiming) != cudaSuccess) {
         set_error("bs_server_create: stream creation failed: %s", cudaGetErrorString(cudaGetLastError()));
         if (st) *st = BS_ECUDA;
         delete S;
@@ -595,7 +663,8 @@ bs_status bs_server_submit(bs_server *S, const uint64_t *key, uint64_t n, double
     r->radius.resize(r->m);
     r->state = 0;
     r->err = BS_OK;
-    r->dmem = nullptr;
+    r->dk = nullptr; r->dp = nullptr; r->dr = nullptr; r->df = nullptr;
+    r->cancel = false;
     r->flag = 0;
     r->copied = nullptr;
     std::lock_guard<std::mutex> lk(S->mu);
@@ -622,6 +691,10 @@ bs_status bs_server_poll(bs_server *S, uint64_t ticket, uint32_t *perm, int64_t 
         return r->err == BS_OK ? BS_ECUDA : r->err;
     }
     if (r->state == 4) { set_error("bs_server_poll: ticket %llu already collected", (unsigned long long)ticket); return BS_EINVAL; }
+    if (r->state == 6 || r->cancel) {
+        set_error("bs_server_poll: request %llu was cancelled", (unsigned long long)ticket);
+        return BS_ECANCELED;
+    }
     if (!perm) return BS_OK;  // status query only
     memcpy(perm, r->perm.data(), r->m * 4);
     if (rad2) memcpy(rad2, r->rad2.data(), r->m * 8);
@@ -641,9 +714,46 @@ bs_status bs_server_times(bs_server *S, uint64_t ticket, double t[3]) {
     auto it = S->all.find(ticket);
     if (it == S->all.end()) { set_error("bs_server_times: unknown ticket"); return BS_EINVAL; }
     SrvReq *r = it->second;
-    if (r->state != 2 && r->state != 3 && r->state != 4) return BS_ENOTREADY;
+    if (r->state != 2 && r->state != 3 && r->state != 4 && r->state != 6) return BS_ENOTREADY;
     t[0] = r->t[0]; t[1] = r->t[1]; t[2] = r->t[2];
     return BS_OK;
+}
+
+bs_status bs_server_cancel(bs_server *S, uint64_t ticket) {
+    clear_error();
+    if (!S) { set_error("bs_server_cancel: NULL server"); return BS_EINVAL; }
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->all.find(ticket);
+    if (it == S->all.end()) { set_error("bs_server_cancel: unknown ticket %llu", (unsigned long long)ticket); return BS_EINVAL; }
+    SrvReq *r = it->second;
+    switch (r->state) {
+        case 0: {  // queued: leaves the queue now (no budget was charged yet)
+            for (auto q = S->queue.begin(); q != S->queue.end(); ++q)
+                if (*q == r) { S->queue.erase(q); break; }
+            r->state = 6;
+            r->t[1] = r->t[2] = S->now();
+            std::vector<uint64_t>().swap(r->key);
+            std::vector<uint32_t>().swap(r->perm);
+            std::vector<int64_t>().swap(r->rad2);
+            std::vector<float>().swap(r->radius);
+            return BS_OK;
+        }
+        case 1:
+        case 5:  // on the device: dropped when its launch ends, which releases its memory and budget
+            r->cancel = true;
+            return BS_OK;
+        case 2:  // finished, not collected: the result is dropped
+            r->state = 6;
+            std::vector<uint32_t>().swap(r->perm);
+            std::vector<int64_t>().swap(r->rad2);
+            std::vector<float>().swap(r->radius);
+            return BS_OK;
+        case 6:
+            return BS_OK;
+        default:
+            set_error("bs_server_cancel: request %llu already failed or collected", (unsigned long long)ticket);
+            return BS_EINVAL;
+    }
 }
 
 void bs_server_destroy(bs_server *S) {
@@ -660,10 +770,12 @@ void bs_server_destroy(bs_server *S) {
             retire(S, slot);
         }
         if (slot.stage) cudaFreeHost(slot.stage);
+        if (slot.kstage) cudaFreeHost(slot.kstage);
         if (slot.flags_h) cudaFreeHost(slot.flags_h);
         cudaEventDestroy(slot.done);
         cudaStreamDestroy(slot.stream);
     }
+    cudaEventDestroy(S->copy_tail);
     cudaStreamDestroy(S->copy);
     for (auto &kv : S->all) delete kv.second;
     delete S;

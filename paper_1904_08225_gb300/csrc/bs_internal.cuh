@@ -132,7 +132,9 @@ struct PartDesc {
 
 namespace bs {
 
-bs_status order_parts(std::vector<PartDesc> &parts, cudaStream_t stream, bool batched);
+// throughput: several parts of a launch share SMs as quarters of CTAs even when the
+// launch is small (the server's launches), instead of one whole CTA per part
+bs_status order_parts(std::vector<PartDesc> &parts, cudaStream_t stream, bool batched, bool throughput = false);
 bs_status order_part_noalloc(PartDesc part, cudaStream_t stream);
 bs_status prefix_median_nn(const bs_surfels *s, const uint32_t *perm, uint64_t pm, int64_t *rm2, cudaStream_t stream);
 bs_status prefix_for_radius_batched(const int64_t *const *rad2, const uint64_t *m, const int64_t *r2, int nparts,
@@ -159,6 +161,7 @@ bs_status render_splats(const bs_splat_set *sets, int nsets, const bs_splat_node
 // the library's stream-ordered pool (freed with cudaFreeAsync)
 cudaError_t pool_malloc_async(void **ptr, size_t bytes, cudaStream_t stream);
 void pool_set_keep(uint64_t bytes);
+void pool_fail_next(int k);
 bs_status sample_splats(const bs_splat_set *sets, int nsets, const bs_splat_node *nodes, int nnodes, const bs_dir *dirs,
                         int ndirs, bs_surfels *out, cudaStream_t stream);
 bs_status sample_visible_parts(const bs_mesh *meshes, const int *res, int nparts, const bs_dir *dirs, int ndirs,

@@ -1266,7 +1266,7 @@ static int quarter_split(const std::vector<uint32_t> &ns, int sms, int kmin) {
 // their sizes, ngs their group counts); d_next holds two zeroed work counters
 static cudaError_t launch_set(const PartDesc *d_parts, int nparts, uint32_t *d_next, int ngmax, int T, int sms,
                               cudaStream_t stream, int algo, const std::vector<uint32_t> &ns,
-                              const std::vector<uint32_t> &ngs) {
+                              const std::vector<uint32_t> &ngs, bool throughput = false) {
     if (algo == 2 && g_quarters != 1 && !(g_loop_threads_override && g_loop_threads_override != 1024)) {
         int kmin = 0;
         while (kmin < nparts && ngs[kmin] > (uint32_t)(Q_SG * 32)) ++kmin;
@@ -1274,9 +1274,12 @@ static cudaError_t launch_set(const PartDesc *d_parts, int nparts, uint32_t *d_n
         if (g_full_parts > 0) nfull = std::max(kmin, std::min(g_full_parts, nparts));
         else if (g_quarters == 2) nfull = kmin;
         else if (nparts >= 2 * sms) nfull = quarter_split(ns, sms, kmin);
+        else if (throughput && nparts - kmin >= 8) nfull = kmin;
         if (nfull >= 0 && nfull < nparts) {
             const int ngq = (int)ngs[nfull];
-            return launch_rounds<1024, true>(d_parts, nparts, nfull, d_next, ngmax, ngq, sms, stream);
+            // a small launch takes only the CTAs its parts fill (other launches share the GPU)
+            const int grid = throughput ? std::min(sms, nfull + (nparts - nfull + 3) / 4) : sms;
+            return launch_rounds<1024, true>(d_parts, nparts, nfull, d_next, ngmax, ngq, grid, stream);
         }
     }
     int per_sm = 1;
@@ -1350,7 +1353,7 @@ static cudaStream_t side_stream() {
 }
 
 // Orders nparts parts.  host descriptors: keys, outputs, n, m, start, scale filled in.
-bs_status order_parts(std::vector<PartDesc> &hp, cudaStream_t stream, bool batched) {
+bs_status order_parts(std::vector<PartDesc> &hp, cudaStream_t stream, bool batched, bool throughput) {
     const int nparts = (int)hp.size();
     if (nparts == 0) return BS_OK;
     // LPT: largest parts first so the persistent CTAs finish together
@@ -1474,7 +1477,7 @@ bs_status order_parts(std::vector<PartDesc> &hp, cudaStream_t stream, bool batch
             }
         } else {
             e = launch_set(d_parts, nparts, d_next, (int)ngmax, pick_threads((int)ngmax, batched, algo), sms, stream,
-                           algo, ns, ngs);
+                           algo, ns, ngs, throughput);
         }
         timing_mark(1, 1, stream);
         if (e != cudaSuccess) {

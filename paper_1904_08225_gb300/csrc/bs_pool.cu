@@ -4,11 +4,18 @@
 // default pool (which returns freed memory to the system at each synchronisation, so
 // the next large call maps it again), this pool keeps up to `keep` bytes of freed
 // memory for the next call (bs_set_tuning("pool_keep_mb", v); 64 GiB by default).
+#include <atomic>
 #include <mutex>
 
 #include "bs_internal.cuh"
 
 namespace bs {
+
+// Failure injection for tests of the error paths (bs_set_tuning("fail_next_allocs", k)):
+// the next k pool allocations fail as if the device were out of memory.  Host-side only.
+static std::atomic<int> g_fail_allocs{0};
+
+void pool_fail_next(int k) { g_fail_allocs.store(k < 0 ? 0 : k); }
 
 static std::mutex g_pool_mu;
 static cudaMemPool_t g_pool[64];
@@ -41,6 +48,11 @@ static cudaMemPool_t current_pool() {
 }
 
 cudaError_t pool_malloc_async(void **ptr, size_t bytes, cudaStream_t stream) {
+    for (int left = g_fail_allocs.load(); left > 0; left = g_fail_allocs.load())
+        if (g_fail_allocs.compare_exchange_weak(left, left - 1)) {
+            *ptr = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
     cudaMemPool_t p = current_pool();
     if (!p) return cudaMallocAsync(ptr, bytes, stream);
     return cudaMallocFromPoolAsync(ptr, bytes, p, stream);
