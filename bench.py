@@ -326,7 +326,7 @@ def main():
     for i, sp in enumerate(specs):
         mesh_structs.append(bs.Mesh(xyz_d.data_ptr() + int(vofs[i]) * 12, meshes[i].nverts,
                                     tri_d.data_ptr() + int(tofs[i]) * 12, meshes[i].ntris,
-                                    rgb_d.data_ptr() + int(tofs[i]) * 3))
+                                    rgb_d.data_ptr() + int(tofs[i]) * 3, 1))
         o = int(coff[i])
         out_structs.append(bs.Surfels(key_all.data_ptr() + 8 * o, nrm_all.data_ptr() + 6 * o,
                                       rgb_all.data_ptr() + 3 * o, src_all.data_ptr() + 4 * o, 0, caps[i],
@@ -358,7 +358,7 @@ def main():
         vofs, tofs, xyz_h, tri_h, rgb_h, xyz_d, tri_d, rgb_d = pack(meshes)
         mesh_structs = [bs.Mesh(xyz_d.data_ptr() + int(vofs[i]) * 12, meshes[i].nverts,
                                 tri_d.data_ptr() + int(tofs[i]) * 12, meshes[i].ntris,
-                                rgb_d.data_ptr() + int(tofs[i]) * 3) for i in range(len(specs))]
+                                rgb_d.data_ptr() + int(tofs[i]) * 3, 1) for i in range(len(specs))]
         mesh_arr = (bs.Mesh * len(specs))(*mesh_structs)
         res_arr = (C.c_int * len(specs))(*[sp.res for sp in specs])
     # the counts are deterministic: size every part's outputs exactly, so the surfel records
@@ -455,7 +455,10 @@ def main():
         torch.cuda.synchronize()
         return {k: round(marks["start"].elapsed_time(v), 2) for k, v in marks.items() if k != "start"}
 
-    # e2e: host meshes in, ordered surfels out (perm, rad2, radius, key, nrm, rgb)
+    # e2e: host meshes in, ordered surfels out (perm, rad2, radius, key, nrm, rgb), through
+    # the C ABI: bs_sample_order_batched uploads the (pinned, packed) host meshes itself and
+    # writes every result into pinned host arrays; one call per band, each on its own
+    # stream from its own host thread, so the bands overlap as in the device-resident step
     res_h = {
         "perm": torch.empty(total, dtype=torch.int32).pin_memory(),
         "rad2": torch.empty(total, dtype=torch.int64).pin_memory(),
@@ -465,47 +468,41 @@ def main():
         "rgb": torch.empty((total, 3), dtype=torch.uint8).pin_memory(),
     }
     d2h_bytes = total * (4 + 8 + 4) + total * (8 + 6 + 3)
-    # bands as part ranges [p0, p1) in step order (lead bands, then the rest)
-    band_tags = [f"lead{j}" for j in range(len(leads))] + ["rest"]
     band_rng = [(int(np.searchsorted(band, j, "left")), int(np.searchsorted(band, j, "right")))
                 for j in range(len(thresholds) + 1)]
-    h2d_stream = torch.cuda.Stream(device=dev)
-    d2h_streams = [torch.cuda.Stream(device=dev) for _ in band_rng]
-    dev_out = {"perm": perm_all, "rad2": rad2_all, "radius": radius_all,
-               "key": key_all, "nrm": nrm_all, "rgb": rgb_all}
+    band_cs = cs_leads + [cs]
+    e2e_calls = []
+    for (p0, p1), csx in zip(band_rng, band_cs):
+        k = p1 - p0
+        if k == 0:
+            continue
+        hm = (bs.Mesh * k)(*[bs.Mesh(xyz_h.data_ptr() + int(vofs[i]) * 12, meshes[i].nverts,
+                                     tri_h.data_ptr() + int(tofs[i]) * 12, meshes[i].ntris,
+                                     rgb_h.data_ptr() + int(tofs[i]) * 3, 0) for i in range(p0, p1)])
+        ho = (bs.PartResult * k)()
+        for j, i in enumerate(range(p0, p1)):
+            o = int(coff[i])
+            ho[j] = bs.PartResult(res_h["key"].data_ptr() + 8 * o, res_h["nrm"].data_ptr() + 6 * o,
+                                  res_h["rgb"].data_ptr() + 3 * o, None, res_h["perm"].data_ptr() + 4 * o,
+                                  res_h["rad2"].data_ptr() + 8 * o, res_h["radius"].data_ptr() + 4 * o, int(ns[i]))
+        e2e_calls.append((hm, (C.c_int * k)(*[specs[i].res for i in range(p0, p1)]), k,
+                          (bs.OrderOpts * k)(*[opts[i] for i in range(p0, p1)]), ho, csx))
 
     def step_e2e():
-        # inputs band by band from pinned host memory: a band's sampling starts as soon
-        # as its own meshes have arrived
-        h2d_stream.wait_stream(stream)
-        ready = []
-        with torch.cuda.stream(h2d_stream):
-            for p0, p1 in band_rng:
-                v0, v1, t0, t1 = int(vofs[p0]), int(vofs[p1]), int(tofs[p0]), int(tofs[p1])
-                xyz_d[v0:v1].copy_(xyz_h[v0:v1], non_blocking=True)
-                tri_d[t0:t1].copy_(tri_h[t0:t1], non_blocking=True)
-                rgb_d[t0:t1].copy_(rgb_h[t0:t1], non_blocking=True)
-                ev = torch.cuda.Event()
-                ev.record(h2d_stream)
-                ready.append(ev)
-        step(ready)
-        # results band by band: the sampled surfel records once the band is sampled (while
-        # the ordering runs on), the ordered outputs once it is ordered
-        for (p0, p1), tag, st_ in zip(band_rng, band_tags, d2h_streams):
-            if p1 == p0:
-                continue
-            s0, s1 = int(coff[p0]), int(coff[p1])
-            st_.wait_event(marks[tag + "_sampled"])
-            with torch.cuda.stream(st_):
-                for name in ("key", "nrm", "rgb"):
-                    res_h[name][s0:s1].copy_(dev_out[name][s0:s1], non_blocking=True)
-            st_.wait_event(marks[tag + "_ordered"])
-            with torch.cuda.stream(st_):
-                for name in ("perm", "rad2", "radius"):
-                    res_h[name][s0:s1].copy_(dev_out[name][s0:s1], non_blocking=True)
-        for st_ in d2h_streams:
-            stream.wait_stream(st_)
-        stream.synchronize()
+        errs = []
+
+        def call(args):
+            hm, hres, k, hopts, ho, csx = args
+            st = lib.bs_sample_order_batched(hm, hres, k, dirs, 6, hopts, ho, 0, csx)
+            if st != bs.BS_OK:
+                errs.append(bs.BsError(st, "bs_sample_order_batched", bs.last_error()))
+        th = [threading.Thread(target=call, args=(a,)) for a in e2e_calls]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        if errs:
+            raise errs[0]
 
     def barrier():
         if dist is not None:
@@ -546,6 +543,12 @@ def main():
 
     # e2e through the public API with host buffers
     step_e2e()
+    # the host path gives the device-resident step's results, array for array
+    torch.cuda.synchronize()
+    for name, dv in (("perm", perm_all), ("rad2", rad2_all), ("radius", radius_all), ("key", key_all),
+                     ("nrm", nrm_all), ("rgb", rgb_all)):
+        if not torch.equal(res_h[name].view(torch.uint8), dv.cpu().view(torch.uint8)):
+            raise RuntimeError(f"e2e {name} differs from the device-resident step")
     ms_e2e = timed(step_e2e, args.steps) / args.steps
     e2e_value = world * total / (ms_e2e / 1e3)
 

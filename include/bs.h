@@ -48,13 +48,19 @@ typedef enum {
 
 /* A triangle mesh of one scene node (Sec. 3: geometry in the node's subtree).
  * xyz: nverts*3 float32 positions; tri: ntris*3 vertex indices (< nverts);
- * face_rgb: ntris*3 bytes of per-face colour, or NULL (colour 0).  Device pointers. */
+ * face_rgb: ntris*3 bytes of per-face colour, or NULL (colour 0).
+ * on_device: nonzero when the three arrays are device pointers; 0 when they are HOST
+ * pointers, which the library copies to the device on the call's stream before use
+ * (page-locked arrays directly; pageable ones through pinned staging the library owns,
+ * reused once its previous copy has finished; arrays of consecutive meshes that lie
+ * back to back in host memory move as one copy).  The caller keeps ownership. */
 typedef struct {
     const float *xyz;
     uint32_t nverts;
     const uint32_t *tri;
     uint32_t ntris;
     const uint8_t *face_rgb;
+    int32_t on_device;
 } bs_mesh;
 
 /* A view direction with integer components in {-1, 0, 1}, not all zero.  The
@@ -118,7 +124,8 @@ typedef struct {
  * depth wins, equal depth to the lower triangle id), emits one surfel per
  * covered pixel, merges surfels with identical positions (keeping the smallest
  * emission index) and writes them in ascending Morton order.
- *  mesh  : device geometry (see bs_mesh); dirs: HOST array of ndirs directions.
+ *  mesh  : geometry (see bs_mesh: device, or host arrays the library uploads);
+ *          dirs: HOST array of ndirs directions.
  *  res   : pixels per side, 1..BS_MAX_RES; ndirs: 1..BS_MAX_DIRS.
  *  out   : caller-owned device arrays of out->cap rows (nrm, rgb, src may be NULL).
  * Returns BS_OK with out->n, out->bbox_min, out->scale set; BS_EOVERFLOW with
@@ -130,7 +137,7 @@ bs_status bs_sample_visible(const bs_mesh *mesh, const bs_dir *dirs, int ndirs, 
 
 /* bs_sample_visible_batched -- bs_sample_visible for many meshes in one set of
  * launches (the per-node sampling of Sec. 3.4 run for a whole scene).
- *  meshes : HOST array of nparts device meshes (1 <= nparts <= 65535)
+ *  meshes : HOST array of nparts meshes (device or host, see bs_mesh; 1 <= nparts <= 65535)
  *  res    : HOST array of nparts resolutions; dirs: HOST array of ndirs directions
  *           shared by all parts; the total pixel count must stay below 2^32
  *  out    : HOST array of nparts descriptors of caller-owned device arrays
@@ -140,6 +147,44 @@ bs_status bs_sample_visible(const bs_mesh *mesh, const bs_dir *dirs, int ndirs, 
  * are written).  BS_EINVAL names the first invalid part.  Synchronises the stream. */
 bs_status bs_sample_visible_batched(const bs_mesh *meshes, const int *res, int nparts, const bs_dir *dirs,
                                     int ndirs, bs_surfels *out, void *cuda_stream);
+
+/* One part's results of bs_sample_order_batched.  The caller owns every array (HOST
+ * arrays, or DEVICE ones when the call's out_on_device is nonzero).
+ *  key, nrm, rgb, src : the sampled surfel records in canonical order, as
+ *         bs_sample_visible writes them (cap rows; each may be NULL: not returned)
+ *  perm, rad2, radius : the ordering and per-prefix radii, as bs_order writes them
+ *         (m = min(max_count or n, n) entries; rad2 and radius may be NULL)
+ *  cap  : rows of the surfel arrays (and entries of perm/rad2/radius)
+ *  n, bbox_min, scale : out, as in bs_surfels */
+typedef struct {
+    uint64_t *key;
+    int16_t *nrm;
+    uint8_t *rgb;
+    uint32_t *src;
+    uint32_t *perm;
+    int64_t *rad2;
+    float *radius;
+    uint64_t cap;
+    uint64_t n;
+    float bbox_min[3];
+    double scale;
+} bs_part_result;
+
+/* bs_sample_order_batched -- the whole path for many meshes in one call: each mesh is
+ * sampled as bs_sample_visible_batched samples it (Sec. 3.1) and its surfels ordered as
+ * bs_order_batched orders them (Sec. 3.2 greedy permutation, Sec. 4.1 radii), with the
+ * results written to the caller's arrays -- host to host for a caller without device
+ * buffers: host meshes (on_device = 0) are uploaded by the library, and with
+ * out_on_device = 0 every output is a host array.  The surfel records are read back
+ * while the ordering runs.  Results are bit-identical to the two calls.
+ *  meshes, res, dirs : as bs_sample_visible_batched (meshes may be host or device)
+ *  opts  : HOST array of nparts ordering options; out: HOST array of nparts results
+ * BS_EOVERFLOW (every out[p].n set, nothing ordered) when a part has more than cap
+ * surfels; the other errors as the two calls.  Synchronises the stream: host outputs
+ * are complete on return. */
+bs_status bs_sample_order_batched(const bs_mesh *meshes, const int *res, int nparts, const bs_dir *dirs, int ndirs,
+                                  const bs_order_opts *opts, bs_part_result *out, int out_on_device,
+                                  void *cuda_stream);
 
 /* ---- Bottom-up generation from child surfels (Sec. 3.4), each surfel drawn as the
  * oriented disc of Sec. 4.2. ---- */

@@ -26,6 +26,7 @@ EXPORTS = ["bs_sample_visible", "bs_sample_visible_batched", "bs_order", "bs_ord
            "bs_server_poll", "bs_server_times", "bs_server_cancel", "bs_server_destroy", "bs_set_tuning", "bs_last_launch_ms",
            "bs_prefix_median_nn", "bs_prefix_for_radius", "bs_prefix_estimate", "bs_scene_generate", "bs_sample_splats",
            "bs_prefix_for_radius_batched", "bs_render_mesh", "bs_render_splats", "bs_parent_frames",
+           "bs_sample_order_batched",
            "bs_last_error"]
 
 
@@ -36,8 +37,16 @@ class BsError(RuntimeError):
 
 
 class Mesh(C.Structure):
+    """bs_mesh: device pointers with on_device=1; host pointers (uploaded by the library) with 0."""
     _fields_ = [("xyz", C.c_void_p), ("nverts", C.c_uint32), ("tri", C.c_void_p), ("ntris", C.c_uint32),
-                ("face_rgb", C.c_void_p)]
+                ("face_rgb", C.c_void_p), ("on_device", C.c_int32)]
+
+
+class PartResult(C.Structure):
+    """bs_part_result: one part's outputs of bs_sample_order_batched."""
+    _fields_ = [("key", C.c_void_p), ("nrm", C.c_void_p), ("rgb", C.c_void_p), ("src", C.c_void_p),
+                ("perm", C.c_void_p), ("rad2", C.c_void_p), ("radius", C.c_void_p), ("cap", C.c_uint64),
+                ("n", C.c_uint64), ("bbox_min", C.c_float * 3), ("scale", C.c_double)]
 
 
 class Dir(C.Structure):
@@ -86,6 +95,7 @@ def load(build_if_stale: bool = True) -> C.CDLL:
             lib.bs_sample_visible_batched.argtypes = [C.POINTER(Mesh), C.POINTER(C.c_int), C.c_int, C.POINTER(Dir),
                                                       C.c_int, C.POINTER(Surfels), P]
             lib.bs_prefix_for_radius_batched.argtypes = [P, P, P, C.c_int, P, P, P]
+            lib.bs_sample_order_batched.argtypes = [P, P, C.c_int, P, C.c_int, P, P, C.c_int, P]
             lib.bs_parent_frames.argtypes = [P, P, P, C.c_int, P, P, P, P]
             lib.bs_render_mesh.argtypes = [C.POINTER(Mesh), C.POINTER(Dir), C.c_int, P, P]
             lib.bs_render_splats.argtypes = [C.POINTER(SplatSet), C.c_int, C.POINTER(SplatNode), C.POINTER(Dir), P, P]
@@ -131,6 +141,13 @@ def _torch():
     if not torch.cuda.is_available():
         raise RuntimeError("libbs needs a CUDA GPU; none is available")
     return torch
+
+
+def _out_device(t):
+    """Where the library writes its outputs: the tensor's own device, or the current CUDA
+    device for a host (CPU) tensor -- the kernels write only device memory."""
+    torch = _torch()
+    return t.device if t.is_cuda else torch.device("cuda", torch.cuda.current_device())
 
 
 def _stream(stream):
@@ -252,6 +269,79 @@ def parent_frames(child_mins, child_scales, children_of, parent_res):
     return fmin, fs, r2
 
 
+def sample_order_batched(xyz, tri, rgb, vofs, nverts, tofs, ntris, res, dirs, caps, seeds=0, part_ids=None,
+                         max_counts=0, stream=None, out=None):
+    """bs_sample_order_batched over parts packed in shared buffers, host to host or device to
+    device: xyz float32 (V,3), tri uint32/int32 (T,3) with part-local indices, rgb uint8
+    (T,3) or None -- numpy arrays (host meshes, uploaded by the library) or CUDA tensors.
+    Part i: vertices vofs[i]:+nverts[i], triangles tofs[i]:+ntris[i], at most caps[i]
+    surfels.  out: optional dict of preallocated flat outputs (key, nrm, rgb, src, perm,
+    rad2, radius; host numpy arrays or CUDA tensors, sum(caps) rows, part i at
+    ofs[i] = sum(caps[:i])); host outputs are allocated when out is None and the meshes
+    are numpy arrays.  Returns dict(out arrays..., ofs, n, bbox_min, scale)."""
+    lib = load()
+    vofs, nverts = np.asarray(vofs, np.int64), np.asarray(nverts, np.int64)
+    tofs, ntris = np.asarray(tofs, np.int64), np.asarray(ntris, np.int64)
+    P = len(vofs)
+
+    def is_dev(a):
+        return hasattr(a, "is_cuda") and a.is_cuda
+
+    def addr(a):  # torch tensors (host or device) or numpy arrays (host)
+        return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+
+    on_dev = is_dev(xyz)
+    if any(is_dev(a) != on_dev for a in (tri, rgb) if a is not None):
+        raise ValueError("xyz, tri and rgb must all be host arrays or all device tensors")
+    d = np.asarray(dirs, dtype=np.int8).reshape(-1, 3)
+    darr = (Dir * len(d))(*[Dir(int(a), int(b), int(c)) for a, b, c in d])
+    capv = np.asarray(caps, np.int64)
+    ofs = np.concatenate([[0], np.cumsum(capv)]).astype(np.int64)
+    tot = int(ofs[-1])
+    if out is None:
+        if on_dev:
+            torch = _torch()
+            dev = _out_device(xyz)
+            out = dict(key=torch.empty(tot, dtype=torch.int64, device=dev),
+                       nrm=torch.empty((tot, 3), dtype=torch.int16, device=dev),
+                       rgb=torch.empty((tot, 3), dtype=torch.uint8, device=dev),
+                       src=torch.empty(tot, dtype=torch.int32, device=dev),
+                       perm=torch.empty(tot, dtype=torch.int32, device=dev),
+                       rad2=torch.empty(tot, dtype=torch.int64, device=dev),
+                       radius=torch.empty(tot, dtype=torch.float32, device=dev))
+        else:
+            out = dict(key=np.empty(tot, np.uint64), nrm=np.empty((tot, 3), np.int16), rgb=np.empty((tot, 3), np.uint8),
+                       src=np.empty(tot, np.uint32), perm=np.empty(tot, np.uint32), rad2=np.empty(tot, np.int64),
+                       radius=np.empty(tot, np.float32))
+    out_dev = is_dev(out["perm"])
+    if any(is_dev(a) != out_dev for a in out.values() if a is not None):
+        raise ValueError("the outputs must all be host arrays or all device tensors")
+    mnp, marr = _struct_array(Mesh, P)
+    mnp["xyz"] = addr(xyz) + 12 * vofs
+    mnp["nverts"] = nverts
+    mnp["tri"] = addr(tri) + 12 * tofs
+    mnp["ntris"] = ntris
+    mnp["face_rgb"] = 0 if rgb is None else addr(rgb) + 3 * tofs
+    mnp["on_device"] = 1 if on_dev else 0
+    onp, oarr = _struct_array(PartResult, P)
+    width = dict(key=8, nrm=6, rgb=3, src=4, perm=4, rad2=8, radius=4)
+    for name, w in width.items():
+        a = out.get(name)
+        onp[name] = 0 if a is None else addr(a) + w * ofs[:-1]
+    onp["cap"] = capv
+    opts = (OrderOpts * P)()
+    pid = range(P) if part_ids is None else part_ids
+    sd = np.broadcast_to(np.asarray(seeds, np.int64), (P,))
+    mc = np.broadcast_to(np.asarray(max_counts, np.int64), (P,))
+    for i, p_ in enumerate(pid):
+        opts[i] = _opts(int(sd[i]), int(p_), -1, int(mc[i]))
+    rarr = (C.c_int * P)(*np.broadcast_to(np.asarray(res, np.int64), (P,)).tolist())
+    st = lib.bs_sample_order_batched(marr, rarr, P, darr, len(d), opts, oarr, 1 if out_dev else 0, _stream(stream))
+    _check(st, "bs_sample_order_batched")
+    return dict(out, ofs=ofs, n=onp["n"].astype(np.int64), bbox_min=onp["bbox_min"].copy(),
+                scale=onp["scale"].copy())
+
+
 def prefix_estimate(pm: int, rm2: int, r2: int) -> float:
     """The paper's p(r) = pm (r_m / r)^2."""
     return load().bs_prefix_estimate(int(pm), int(rm2), int(r2))
@@ -268,12 +358,12 @@ def sample_visible(xyz, tri, rgb, dirs, res: int, stream=None, cap: int | None =
     lib = load()
     d = np.asarray(dirs, dtype=np.int8).reshape(-1, 3)
     darr = (Dir * len(d))(*[Dir(int(a), int(b), int(c)) for a, b, c in d])
-    dev = xyz.device
+    dev = _out_device(xyz)
     xyz = xyz.contiguous()
     tri = tri.contiguous()
     rgb = rgb.contiguous() if rgb is not None else None
     mesh = Mesh(xyz.data_ptr(), xyz.shape[0], tri.data_ptr() if tri.numel() else None, tri.shape[0],
-                rgb.data_ptr() if rgb is not None else None)
+                rgb.data_ptr() if rgb is not None else None, 1 if xyz.is_cuda else 0)
     if cap is None:
         cap = len(d) * res * res
     key = torch.empty(cap, dtype=torch.int64, device=dev)
@@ -303,7 +393,7 @@ def sample_visible_batched(meshes, res, dirs, stream=None, caps=None):
     keep = []
     capl = [int(caps[i]) if caps is not None else len(d) * int(res[i]) ** 2 for i in range(P)]
     ofs = np.concatenate([[0], np.cumsum(capl)]).astype(np.int64)
-    dev = meshes[0][0].device if P else None
+    dev = _out_device(meshes[0][0]) if P else None
     tot = int(ofs[-1])
     # one allocation per field; part i owns rows ofs[i]:ofs[i+1]
     key = torch.empty(tot, dtype=torch.int64, device=dev)
@@ -315,7 +405,7 @@ def sample_visible_batched(meshes, res, dirs, stream=None, caps=None):
         rgb = rgb.contiguous() if rgb is not None else None
         keep.append((xyz, tri, rgb))
         marr[i] = Mesh(xyz.data_ptr(), xyz.shape[0], tri.data_ptr() if tri.numel() else None, tri.shape[0],
-                       rgb.data_ptr() if rgb is not None else None)
+                       rgb.data_ptr() if rgb is not None else None, 1 if xyz.is_cuda else 0)
         o = int(ofs[i])
         outs[i] = Surfels(key.data_ptr() + 8 * o, nrm.data_ptr() + 6 * o, col.data_ptr() + 3 * o,
                           src.data_ptr() + 4 * o, 0, capl[i], (C.c_float * 3)(), 0.0)
@@ -382,8 +472,9 @@ def render_mesh(xyz, tri, d, res: int, stream=None):
     torch = _torch()
     lib = load()
     xyz, tri = xyz.contiguous(), tri.contiguous()
-    m = Mesh(xyz.data_ptr(), xyz.shape[0], tri.data_ptr() if tri.numel() else None, tri.shape[0], None)
-    img = torch.empty((res, res), dtype=torch.int64, device=xyz.device)
+    m = Mesh(xyz.data_ptr(), xyz.shape[0], tri.data_ptr() if tri.numel() else None, tri.shape[0], None,
+             1 if xyz.is_cuda else 0)
+    img = torch.empty((res, res), dtype=torch.int64, device=_out_device(xyz))
     dd = Dir(*[int(x) for x in d])
     _check(lib.bs_render_mesh(C.byref(m), C.byref(dd), int(res), C.c_void_p(img.data_ptr()), _stream(stream)),
            "bs_render_mesh")
@@ -451,7 +542,7 @@ def sample_visible_packed(xyz, tri, rgb, vofs, nverts, tofs, ntris, res, dirs, c
     resv = np.broadcast_to(np.asarray(res, np.int64), (P,))
     capv = (len(d) * resv * resv) if caps is None else np.broadcast_to(np.asarray(caps, np.int64), (P,))
     ofs = np.concatenate([[0], np.cumsum(capv)]).astype(np.int64)
-    dev = xyz.device
+    dev = _out_device(xyz)
     tot = int(ofs[-1])
     key = torch.empty(tot, dtype=torch.int64, device=dev)
     nrm = torch.empty((tot, 3), dtype=torch.int16, device=dev)
@@ -463,6 +554,7 @@ def sample_visible_packed(xyz, tri, rgb, vofs, nverts, tofs, ntris, res, dirs, c
     mnp["tri"] = tri.data_ptr() + 12 * tofs
     mnp["ntris"] = ntris
     mnp["face_rgb"] = 0 if rgb is None else rgb.data_ptr() + 3 * tofs
+    mnp["on_device"] = 1 if xyz.is_cuda else 0
     onp, oarr = _struct_array(Surfels, P)
     onp["key"] = key.data_ptr() + 8 * ofs[:-1]
     onp["nrm"] = nrm.data_ptr() + 6 * ofs[:-1]

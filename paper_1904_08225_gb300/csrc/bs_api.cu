@@ -163,16 +163,57 @@ bs_status bs_last_launch_ms(const char *kernel, double *ms) {
     return st;
 }
 
+// The scalar arguments of a sampling call, checked before any mesh is staged.
+static bs_status check_sample_args(const char *fn, const int *res, int nparts, const bs_dir *dirs, int ndirs) {
+    if (nparts < 1 || nparts > 65535 || !res || !dirs) { set_error("%s: NULL argument or nparts outside [1, 65535]", fn); return BS_EINVAL; }
+    if (ndirs < 1 || ndirs > BS_MAX_DIRS) { set_error("%s: ndirs=%d outside [1,%d]", fn, ndirs, BS_MAX_DIRS); return BS_EINVAL; }
+    for (int i = 0; i < ndirs; ++i) {
+        const bs_dir &d = dirs[i];
+        if (d.x < -1 || d.x > 1 || d.y < -1 || d.y > 1 || d.z < -1 || d.z > 1 || (d.x == 0 && d.y == 0 && d.z == 0)) {
+            set_error("%s: direction %d is not a nonzero vector in {-1,0,1}^3", fn, i);
+            return BS_EINVAL;
+        }
+    }
+    for (int p = 0; p < nparts; ++p)
+        if (res[p] < 1 || res[p] > BS_MAX_RES) { set_error("%s: part %d: res=%d outside [1,%d]", fn, p, res[p], BS_MAX_RES); return BS_EINVAL; }
+    return BS_OK;
+}
+
 bs_status bs_sample_visible(const bs_mesh *mesh, const bs_dir *dirs, int ndirs, int res, bs_surfels *out,
                             void *cuda_stream) {
     clear_error();
-    return sample_visible(mesh, dirs, ndirs, res, out, (cudaStream_t)cuda_stream);
+    if (!mesh || !out) { set_error("bs_sample_visible: NULL argument"); return BS_EINVAL; }
+    if (check_sample_args("bs_sample_visible", &res, 1, dirs, ndirs) != BS_OK) return BS_EINVAL;
+    std::vector<bs_mesh> dm;
+    char *block = nullptr;
+    bs_status st = stage_meshes(mesh, 1, dm, &block, (cudaStream_t)cuda_stream);
+    if (st != BS_OK) return st;
+    st = sample_visible(dm.data(), dirs, ndirs, res, out, (cudaStream_t)cuda_stream);
+    if (block) cudaFreeAsync(block, (cudaStream_t)cuda_stream);
+    return st;
 }
 
 bs_status bs_sample_visible_batched(const bs_mesh *meshes, const int *res, int nparts, const bs_dir *dirs, int ndirs,
                                     bs_surfels *out, void *cuda_stream) {
     clear_error();
-    return sample_visible_parts(meshes, res, nparts, dirs, ndirs, out, (cudaStream_t)cuda_stream);
+    if (!meshes || !out) { set_error("bs_sample_visible_batched: NULL argument"); return BS_EINVAL; }
+    if (check_sample_args("bs_sample_visible_batched", res, nparts, dirs, ndirs) != BS_OK) return BS_EINVAL;
+    std::vector<bs_mesh> dm;
+    char *block = nullptr;
+    bs_status st = stage_meshes(meshes, nparts, dm, &block, (cudaStream_t)cuda_stream);
+    if (st != BS_OK) return st;
+    st = sample_visible_parts(dm.data(), res, nparts, dirs, ndirs, out, (cudaStream_t)cuda_stream);
+    if (block) cudaFreeAsync(block, (cudaStream_t)cuda_stream);
+    return st;
+}
+
+bs_status bs_sample_order_batched(const bs_mesh *meshes, const int *res, int nparts, const bs_dir *dirs, int ndirs,
+                                  const bs_order_opts *opts, bs_part_result *out, int out_on_device,
+                                  void *cuda_stream) {
+    clear_error();
+    if (!meshes || !opts || !out) { set_error("bs_sample_order_batched: NULL argument"); return BS_EINVAL; }
+    if (check_sample_args("bs_sample_order_batched", res, nparts, dirs, ndirs) != BS_OK) return BS_EINVAL;
+    return sample_order_batched(meshes, res, nparts, dirs, ndirs, opts, out, out_on_device, (cudaStream_t)cuda_stream);
 }
 
 bs_status bs_order(const bs_surfels *s, const bs_order_opts *opts, uint32_t *perm, int64_t *rad2, float *radius,
@@ -205,7 +246,15 @@ bs_status bs_scene_generate(uint64_t seed, const uint64_t *part_ids, const int32
 
 bs_status bs_render_mesh(const bs_mesh *mesh, const bs_dir *dir, int res, unsigned long long *image, void *cuda_stream) {
     clear_error();
-    return render_mesh(mesh, dir, res, image, (cudaStream_t)cuda_stream);
+    if (!mesh || !dir || !image) { set_error("bs_render_mesh: NULL argument"); return BS_EINVAL; }
+    if (check_sample_args("bs_render_mesh", &res, 1, dir, 1) != BS_OK) return BS_EINVAL;
+    std::vector<bs_mesh> dm;
+    char *block = nullptr;
+    bs_status st = stage_meshes(mesh, 1, dm, &block, (cudaStream_t)cuda_stream);
+    if (st != BS_OK) return st;
+    st = render_mesh(dm.data(), dir, res, image, (cudaStream_t)cuda_stream);
+    if (block) cudaFreeAsync(block, (cudaStream_t)cuda_stream);
+    return st;
 }
 
 bs_status bs_render_splats(const bs_splat_set *sets, int nsets, const bs_splat_node *node, const bs_dir *dir,

@@ -164,6 +164,11 @@ void pool_set_keep(uint64_t bytes);
 void pool_fail_next(int k);
 bs_status sample_splats(const bs_splat_set *sets, int nsets, const bs_splat_node *nodes, int nnodes, const bs_dir *dirs,
                         int ndirs, bs_surfels *out, cudaStream_t stream);
+// host meshes (on_device == 0) copied into one device block (*block, freed by the caller
+// with cudaFreeAsync on stream); dev receives the meshes with device pointers
+bs_status stage_meshes(const bs_mesh *in, int n, std::vector<bs_mesh> &dev, char **block, cudaStream_t stream);
+bs_status sample_order_batched(const bs_mesh *meshes, const int *res, int nparts, const bs_dir *dirs, int ndirs,
+                               const bs_order_opts *opts, bs_part_result *out, int out_on_device, cudaStream_t stream);
 bs_status sample_visible_parts(const bs_mesh *meshes, const int *res, int nparts, const bs_dir *dirs, int ndirs,
                                bs_surfels *out, cudaStream_t stream, unsigned long long *image = nullptr);
 

@@ -51,8 +51,15 @@ def test_bad_arguments_rejected_without_gpu():
     out = bs.Surfels(None, None, None, None, 0, 0, (C.c_float * 3)(), 0.0)
     assert lib.bs_sample_visible(C.byref(mesh), d, 1, 64, C.byref(out), None) == bs.BS_EINVAL
     mesh.nverts = 3
-    mesh.xyz = 16
+    mesh.xyz = 16          # a placeholder device address: never dereferenced, the checks come first
+    mesh.on_device = 1
     assert lib.bs_sample_visible(C.byref(mesh), d, 1, 0, C.byref(out), None) == bs.BS_EINVAL
+    host = bs.Mesh(16, 3, None, 0, None, 0)  # host arrays: scalar checks come before any upload
+    assert lib.bs_sample_visible(C.byref(host), d, 1, 0, C.byref(out), None) == bs.BS_EINVAL
+    assert lib.bs_sample_visible(C.byref(host), d, 0, 64, C.byref(out), None) == bs.BS_EINVAL
+    ress = (C.c_int * 1)(5000)
+    res_ = (bs.PartResult * 1)()
+    assert lib.bs_sample_order_batched(C.byref(host), ress, 1, d, 1, C.byref(o), res_, 0, None) == bs.BS_EINVAL
     assert lib.bs_sample_visible(C.byref(mesh), d, 0, 64, C.byref(out), None) == bs.BS_EINVAL
     bad = (bs.Dir * 1)(bs.Dir(0, 0, 0))
     assert lib.bs_sample_visible(C.byref(mesh), bad, 1, 64, C.byref(out), None) == bs.BS_EINVAL
