@@ -356,6 +356,7 @@ struct SrvSlot {
     char *kstage = nullptr;  // pinned host staging for the launch's keys (one upload)
     size_t kstage_cap = 0;
     char *dblock = nullptr;  // the launch's device block: every request's keys, then outputs
+    std::vector<char *> retired_pinned;  // outgrown staging, freed with the server
     uint32_t *flags_h = nullptr;  // host-mapped completion flags, set by the ordering kernel
     uint32_t *flags_d = nullptr;  // the same memory as the device sees it
     bool busy = false;
@@ -446,9 +447,11 @@ static void finish_copy(SrvSlot &slot, SrvReq *r) {
 }
 
 // Grows a pinned host staging buffer to at least `need` bytes (twice that when it grows).
-static bool ensure_pinned(char **buf, size_t *cap, size_t need) {
+// The outgrown buffer is kept until the server is destroyed: cudaFreeHost would wait for
+// all work on the device, stalling every launch in flight.
+static bool ensure_pinned(SrvSlot &slot, char **buf, size_t *cap, size_t need) {
     if (need <= *cap) return true;
-    if (*buf) cudaFreeHost(*buf);
+    if (*buf) slot.retired_pinned.push_back(*buf);
     *buf = nullptr;
     *cap = 0;
     if (cudaHostAlloc((void **)buf, need * 2, cudaHostAllocDefault) != cudaSuccess) {
@@ -476,7 +479,8 @@ static void launch_batch(bs_server *S, SrvSlot &slot, std::vector<SrvReq *> &bat
         outs += align256(r->m * 4) + align256(r->m * 8) + align256(r->m * 4);
     }
     err.assign(batch.size(), BS_OK);
-    bool ok = ensure_pinned(&slot.stage, &slot.stage_cap, stage) && ensure_pinned(&slot.kstage, &slot.kstage_cap, keys);
+    bool ok = ensure_pinned(slot, &slot.stage, &slot.stage_cap, stage) &&
+              ensure_pinned(slot, &slot.kstage, &slot.kstage_cap, keys);
     if (ok && pool_malloc_async((void **)&slot.dblock, keys + outs, slot.stream) != cudaSuccess) {
         cudaGetLastError();
         slot.dblock = nullptr;
@@ -661,7 +665,8 @@ bs_server *bs_server_create(uint64_t device_budget_bytes, int max_inflight, bs_s
             cudaEventCreateWithFlags(&slot.done, cudaEventDisableTiming) != cudaSuccess ||
             cudaHostAlloc((void **)&slot.flags_h, SLOT_FLAGS * sizeof(uint32_t), cudaHostAllocMapped) != cudaSuccess ||
             cudaHostGetDevicePointer((void **)&slot.flags_d, slot.flags_h, 0) != cudaSuccess ||
-            cudaHostAlloc((void **)&slot.stage, SLOT_STAGE_BYTES, cudaHostAllocDefault) != cudaSuccess) {
+            cudaHostAlloc((void **)&slot.stage, SLOT_STAGE_BYTES, cudaHostAllocDefault) != cudaSuccess ||
+            cudaHostAlloc((void **)&slot.kstage, SLOT_STAGE_BYTES, cudaHostAllocDefault) != cudaSuccess) {
             set_error("bs_server_create: stream/event creation failed: %s", cudaGetErrorString(cudaGetLastError()));
             if (st) *st = BS_ECUDA;
             for (SrvSlot &s2 : S->slots) {
@@ -669,12 +674,14 @@ bs_server *bs_server_create(uint64_t device_budget_bytes, int max_inflight, bs_s
                 if (s2.done) cudaEventDestroy(s2.done);
                 if (s2.flags_h) cudaFreeHost(s2.flags_h);
                 if (s2.stage) cudaFreeHost(s2.stage);
+                if (s2.kstage) cudaFreeHost(s2.kstage);
             }
             cudaStreamDestroy(S->copy);
             delete S;
             return nullptr;
         }
         slot.stage_cap = SLOT_STAGE_BYTES;
+        slot.kstage_cap = SLOT_STAGE_BYTES;
     }
     S->driver = std::thread(driver_loop, S);
     if (st) *st = BS_OK;
@@ -820,6 +827,7 @@ void bs_server_destroy(bs_server *S) {
         }
         if (slot.stage) cudaFreeHost(slot.stage);
         if (slot.kstage) cudaFreeHost(slot.kstage);
+        for (char *b : slot.retired_pinned) cudaFreeHost(b);
         if (slot.flags_h) cudaFreeHost(slot.flags_h);
         cudaEventDestroy(slot.done);
         cudaStreamDestroy(slot.stream);

@@ -1165,6 +1165,20 @@ bs_status order_last_launch_ms(int which, double *ms) {
     return BS_OK;
 }
 
+// Lets a kernel launch with up to the device's opt-in shared memory per block.  Every
+// call sets the same value, so calls from several host threads (each launching with its
+// own dynamic size) cannot lower the limit under another thread's launch.
+template <typename K>
+static cudaError_t allow_smem(K kern) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    int dev = 0, optin = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
 static size_t rounds_smem_full(int ngmax) { return slot_bytes<MAX_SG>(rounds_nbsm(ngmax), ngmax); }
 
 // quarter-mode bucket capacity: what is left of a quarter of the shared memory
@@ -1179,7 +1193,7 @@ static cudaError_t launch_rounds(const PartDesc *d_parts, int nparts, int nfull,
     const int nbq = QU ? quarter_nbq(ngq) : 0;
     size_t smem = rounds_smem_full(ngmax);
     if (QU) smem = std::max(smem, 4 * slot_bytes<Q_SG>(nbq, ngq));
-    cudaError_t e = cudaFuncSetAttribute(k_order_rounds<CT, QU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_smem(k_order_rounds<CT, QU>);
     if (e != cudaSuccess) return e;
     k_order_rounds<CT, QU><<<grid, CT, smem, stream>>>(d_parts, nparts, nfull, d_next, ngmax, rounds_nbsm(ngmax), ngq,
                                                         nbq);
@@ -1191,7 +1205,7 @@ static cudaError_t launch_loop(const PartDesc *d_parts, int nparts, uint32_t *d_
                                cudaStream_t stream, int algo) {
     if (algo == 1) {
         const size_t smem = (size_t)ngmax * 36;
-        cudaError_t e = cudaFuncSetAttribute(k_order_loop<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = allow_smem(k_order_loop<T>);
         if (e != cudaSuccess) return e;
         k_order_loop<T><<<grid, T, smem, stream>>>(d_parts, nparts, d_next, ngmax);
         return cudaGetLastError();
@@ -1208,11 +1222,11 @@ static int occupancy(int ngmax, int algo) {
     cudaError_t e = cudaSuccess;
     if (algo == 1) {
         const size_t smem = (size_t)ngmax * 36;
-        cudaFuncSetAttribute(k_order_loop<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_smem(k_order_loop<T>);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_order_loop<T>, T, smem);
     } else if constexpr (T >= CAP && T >= SMAX) {
         const size_t smem = rounds_smem_full(ngmax);
-        cudaFuncSetAttribute(k_order_rounds<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_smem(k_order_rounds<T, false>);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_order_rounds<T, false>, T, smem);
     } else {
         blocks = 1;
@@ -1274,7 +1288,12 @@ static cudaError_t launch_set(const PartDesc *d_parts, int nparts, uint32_t *d_n
         if (g_full_parts > 0) nfull = std::max(kmin, std::min(g_full_parts, nparts));
         else if (g_quarters == 2) nfull = kmin;
         else if (nparts >= 2 * sms) nfull = quarter_split(ns, sms, kmin);
-        else if (throughput && nparts - kmin >= 8) nfull = kmin;
+        else if (throughput && nparts - kmin >= 8) {
+            // a server launch: parts of 64k points and more keep whole CTAs (a quarter
+            // orders one at about 0.41 of a whole CTA's speed), the rest share SMs
+            nfull = kmin;
+            while (nfull < nparts && ns[nfull] >= 65536u) ++nfull;
+        }
         if (nfull >= 0 && nfull < nparts) {
             const int ngq = (int)ngs[nfull];
             // a small launch takes only the CTAs its parts fill (other launches share the GPU)
@@ -1308,7 +1327,7 @@ static cudaError_t launch_cluster(const PartDesc *d_parts, int nparts, uint32_t 
                                   int nclusters, cudaStream_t stream) {
     const size_t smem = slot_bytes<MAX_SG>(0, ngmax);
     auto kern = k_order_cluster<1024>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_smem(kern);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
