@@ -653,11 +653,15 @@ def main():
             # the autotuner over the batch's ordering launch (all parts in one launch)
             from paper_1904_08225_gb300 import autotune
             keys_t = [key_all[int(coff[i]):int(coff[i]) + int(ns[i])] for i in range(P)]
-            best, times = autotune.autotune(keys_t, repeats=1, apply=False)
-            extras["autotune"] = {"best": {"order_threads": best[0], "order_quarters": best[1],
-                                           "order_full_parts": best[2]},
-                                  "ms": {f"threads={c[0]},quarters={c[1]},full_parts={c[2]}": round(t, 2)
-                                         for c, t in times.items()},
+            best, times = autotune.autotune(keys_t, repeats=3, apply=False)
+            spread = getattr(autotune.autotune, "last_spread", {})
+            lbl = lambda c: ",".join(f"{n.split('_', 1)[1]}={v}" for n, v in zip(autotune.NAMES, c))  # noqa: E731
+            extras["autotune"] = {"best": dict(zip(autotune.NAMES, best)),
+                                  "median_ms": {lbl(c): round(t, 2) for c, t in times.items()},
+                                  "min_max_ms": {lbl(c): [round(x, 2) for x in spread[c]] for c in spread},
+                                  "repeats": 3,
+                                  "knobs": "CTA size, slot mode, whole-CTA parts, parts per CTA (2/4/8 slots); "
+                                           "the 32-point bucket (grid cell) is fixed by the data layout",
                                   "launch": f"bs_order_batched over all {P} parts"}
         if "served" in legs:
             extras["served"] = serve_leg(bs, key_all, coff, ns, out_structs, args, orig)

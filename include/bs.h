@@ -419,6 +419,10 @@ bs_status bs_scene_generate(uint64_t seed, const uint64_t *part_ids, const int32
  *                       1 = never, 2 = always (parts over 524,288 points stay whole)
  *  "order_full_parts"   k > 0: the k largest parts run on whole CTAs before the quarters
  *                       (0 = the cost model decides)
+ *  "order_slots"        parts a 1024-thread CTA orders at once after its whole-CTA parts:
+ *                       2, 4 (the default; 0 restores it) or 8 slots of 512, 256 or 128
+ *                       threads taking parts of at most 1M, 512k or 256k points (8 slots
+ *                       only when no part of the launch uses the sampler, variant 1)
  *  "server_slots"       launches a server created afterwards keeps in flight (1..256,
  *                       16 by default; each holds 64 MB of pinned result staging)
  *  "server_timeout_ms"  a request of a server created afterwards that is still on the

@@ -130,6 +130,13 @@ bs_status bs_set_tuning(const char *name, int value) {
         if (value < 0) { set_error("bs_set_tuning: order_full_parts=%d negative", value); return BS_EINVAL; }
         order_set_full_parts(value);
         return BS_OK;
+    } else if (!strcmp(name, "order_slots")) {
+        if (value != 0 && value != 2 && value != 4 && value != 8) {
+            set_error("bs_set_tuning: order_slots=%d not 0, 2, 4 or 8", value);
+            return BS_EINVAL;
+        }
+        order_set_slots(value == 0 ? 4 : value);
+        return BS_OK;
     } else if (!strcmp(name, "order_cluster")) {
         if (value < 0 || value > 16) { set_error("bs_set_tuning: order_cluster=%d outside [0,16]", value); return BS_EINVAL; }
         order_set_cluster(value, 0);

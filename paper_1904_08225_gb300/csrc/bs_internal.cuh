@@ -149,6 +149,7 @@ bs_status scene_generate(uint64_t seed, const uint64_t *part_ids, const int32_t 
 void order_set_tuning(int threads, int ctas_per_sm);
 void order_set_quarters(int v);
 void order_set_full_parts(int k);
+void order_set_slots(int v);
 void order_set_cluster(int c, int min_points);
 void order_set_kernel_timing(bool on);
 void order_set_algo(int algo);

@@ -231,7 +231,7 @@ constexpr int TIE_GROUPS = 8;  // groups a tie window may span
 constexpr int SMAX = 256;      // variant 1: largest random subset per round
 constexpr int SPL = SMAX / 32;
 constexpr int NB_SMEM = 2048;  // parts with at most this many buckets keep bucket records in shared memory
-constexpr size_t SMEM_LIMIT = 227 * 1024;
+constexpr size_t SMEM_LIMIT = 227 * 1024 - 128;  // dynamic shared memory per CTA: the opt-in limit less the static part
 // Quarter mode: a 1024-thread CTA runs four parts at once, 256 threads each, so four
 // independent latency chains share the SM (one part's single simulating warp overlaps
 // the others' sweeps).  A quarter takes parts of at most Q_SG super-groups.
@@ -239,6 +239,9 @@ constexpr int QT = 256;
 constexpr int LB = 4;          // buckets whose loads are issued together in the gather and apply sweeps
 constexpr int Q_SG = 16;       // 524,288 points
 constexpr int Q_NB = 1024;     // bucket records in shared memory up to 32,768 points
+// Other slot counts per 1024-thread CTA (bs_set_tuning "order_slots"): the largest part a
+// slot takes (super-groups) for 2, 4 and 8 slots.
+__host__ __device__ constexpr int slot_sg(int slots) { return slots == 2 ? 32 : slots == 4 ? Q_SG : 8; }
 
 // Per-part shared state of the rounds kernel (one per part slot).
 template <int SG>
@@ -332,7 +335,10 @@ __device__ __forceinline__ uint64_t pick_mask(uint32_t np, const uint32_t *pi, c
 template <int TP, int SG, bool CL = false>
 __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm, unsigned char *slot, int nbsm,
                                             int ngcap, int tid, int bar, int simw, int crank = 0, int csize = 1) {
-    static_assert(TP >= CAP && TP >= SMAX, "the candidate and sample sorts need one thread per entry");
+    static_assert(TP >= CAP, "the candidate sort needs one thread per candidate");
+    // the sampler (variant 1) sorts its sample with one thread per entry: slots of fewer
+    // than SMAX threads order exact parts only (the host routes sampler parts elsewhere)
+    constexpr bool SAMPLER = TP >= SMAX;
     constexpr int NW = TP / 32;
     const int lane = tid & 31, warp = tid >> 5;
     uint64_t *s_bkey = (uint64_t *)(slot + align16(sizeof(RoundsSm<SG>)));
@@ -385,7 +391,7 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
         Sm.tieD = -2;
         Sm.ccnt = 0; Sm.gcnt = 0; Sm.sgcnt = 0; Sm.icut = 0xffffffffu;
         Sm.cc2[0] = 0; Sm.cc2[1] = 0;
-        if (!CL && P.variant == 1) {  // remove the start from the remaining set (swap with the last)
+        if (SAMPLER && !CL && P.variant == 1) {  // remove the start from the remaining set (swap with the last)
             const uint32_t y = P.R[n - 1];
             P.R[P.start] = y;
             P.pos[y] = P.start;
@@ -415,7 +421,8 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
     part_sync(bar, TP);
     uint32_t k = 1;
     while (k < m) {
-      if (!CL && P.variant == 1) {
+      if (SAMPLER && !CL && P.variant == 1) {
+       if constexpr (SAMPLER) {
         // (S1) the round's random subset of the remaining set R[0, n - k)
         const uint32_t L = n - k, S = P.sample_size;
         uint32_t c = 0, slot = 0;
@@ -515,6 +522,7 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
         }
         ++round_t;
         part_sync(bar, TP);
+       }
       } else {
         // (1) current maximum (every warp computes it; no barrier needed).  Cluster mode:
         //     each CTA's best over its own super-groups, combined after a cluster barrier
@@ -1042,11 +1050,12 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
 // QUARTERS (CT = 1024) the CTA then splits into four 256-thread quarters that take the
 // remaining parts [nfull, nparts) one each, on named barriers 1-4.  next[0] and next[1]
 // are the two phases' work counters.
-template <int CT, bool QUARTERS>
+template <int CT, int SLOTS>
 __global__ void __launch_bounds__(CT) k_order_rounds(const PartDesc *__restrict__ parts, int nparts, int nfull,
                                                      uint32_t *__restrict__ next, int ngmax, int nbsm, int ngq, int nbq) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ uint32_t s_part[4];
+    static_assert(SLOTS == 1 || SLOTS == 2 || SLOTS == 4 || SLOTS == 8, "1, 2, 4 or 8 part slots per CTA");
+    __shared__ uint32_t s_part[8];  // one entry per slot
     for (;;) {
         if (threadIdx.x == 0) s_part[0] = atomicAdd(&next[0], 1u);
         __syncthreads();
@@ -1055,16 +1064,18 @@ __global__ void __launch_bounds__(CT) k_order_rounds(const PartDesc *__restrict_
         if (p >= (uint32_t)nfull) break;
         rounds_part<CT, MAX_SG>(parts[p], *(RoundsSm<MAX_SG> *)smraw, smraw, nbsm, ngmax, threadIdx.x, 0, 0);
     }
-    if constexpr (QUARTERS) {
-        const int q = threadIdx.x / QT, tid = threadIdx.x % QT;
-        unsigned char *slot = smraw + (size_t)q * slot_bytes<Q_SG>(nbq, ngq);
+    if constexpr (SLOTS > 1) {
+        constexpr int ST = CT / SLOTS, S_SG = slot_sg(SLOTS), SW = ST / 32;
+        const int q = threadIdx.x / ST, tid = threadIdx.x % ST;
+        unsigned char *slot = smraw + (size_t)q * slot_bytes<S_SG>(nbq, ngq);
         for (;;) {
             if (tid == 0) s_part[q] = (uint32_t)nfull + atomicAdd(&next[1], 1u);
-            part_sync(1 + q, QT);
+            part_sync(1 + q, ST);
             const uint32_t p = s_part[q];
-            part_sync(1 + q, QT);
+            part_sync(1 + q, ST);
             if (p >= (uint32_t)nparts) break;
-            rounds_part<QT, Q_SG>(parts[p], *(RoundsSm<Q_SG> *)slot, slot, nbq, ngq, tid, 1 + q, q);
+            // the slots' serial warps sit on different schedulers (warp index modulo 4)
+            rounds_part<ST, S_SG>(parts[p], *(RoundsSm<S_SG> *)slot, slot, nbq, ngq, tid, 1 + q, q % SW);
         }
     }
 }
@@ -1115,6 +1126,7 @@ static int g_order_algo = 2;              // 1 = one pick per step, 2 = exact mu
 static int g_ctas_per_sm_override = 0;    // set by bs_set_tuning("order_ctas_per_sm", v)
 static int g_quarters = 0;                // set by bs_set_tuning("order_quarters", v): 0 auto, 1 off, 2 on
 static int g_full_parts = 0;              // set by bs_set_tuning("order_full_parts", k); 0 = cost model
+static int g_slots = 4;                   // set by bs_set_tuning("order_slots", v): parts per 1024-thread CTA
 static int g_cluster = 1;                 // bs_set_tuning("order_cluster", c): 0 auto, 1 off, 2..16 CTAs
 static uint32_t g_cluster_min = 262144;   // bs_set_tuning("order_cluster_min", n): smallest cluster part
 
@@ -1128,6 +1140,8 @@ void order_set_algo(int algo) { g_order_algo = algo; }
 void order_set_quarters(int v) { g_quarters = v; }
 
 void order_set_full_parts(int k) { g_full_parts = k; }
+
+void order_set_slots(int v) { g_slots = v; }
 
 void order_set_cluster(int c, int min_points) {
     if (c >= 0) g_cluster = c;
@@ -1181,22 +1195,28 @@ static cudaError_t allow_smem(K kern) {
 
 static size_t rounds_smem_full(int ngmax) { return slot_bytes<MAX_SG>(rounds_nbsm(ngmax), ngmax); }
 
-// quarter-mode bucket capacity: what is left of a quarter of the shared memory
-static int quarter_nbq(int ngq) {
-    const long left = (long)(SMEM_LIMIT / 4) - (long)align16(sizeof(RoundsSm<Q_SG>)) - (long)align16((size_t)ngq * 28);
+// slot-mode bucket capacity: what is left of a slot's share of the shared memory
+template <int SLOTS>
+static int slot_nb(int ngq) {
+    constexpr int S_SG = slot_sg(SLOTS);
+    const long left = (long)(SMEM_LIMIT / SLOTS) - (long)align16(sizeof(RoundsSm<S_SG>)) - (long)align16((size_t)ngq * 28);
     return (int)std::max(0L, std::min((long)Q_NB, left / 24));
 }
 
-template <int CT, bool QU>
+template <int CT, int SLOTS>
 static cudaError_t launch_rounds(const PartDesc *d_parts, int nparts, int nfull, uint32_t *d_next, int ngmax, int ngq,
                                  int grid, cudaStream_t stream) {
-    const int nbq = QU ? quarter_nbq(ngq) : 0;
+    int nbq = 0;
     size_t smem = rounds_smem_full(ngmax);
-    if (QU) smem = std::max(smem, 4 * slot_bytes<Q_SG>(nbq, ngq));
-    cudaError_t e = allow_smem(k_order_rounds<CT, QU>);
+    if constexpr (SLOTS > 1) {
+        nbq = slot_nb<SLOTS>(ngq);
+        smem = std::max(smem, SLOTS * slot_bytes<slot_sg(SLOTS)>(nbq, ngq));
+    }
+    if (smem > SMEM_LIMIT) return cudaErrorInvalidConfiguration;
+    cudaError_t e = allow_smem(k_order_rounds<CT, SLOTS>);
     if (e != cudaSuccess) return e;
-    k_order_rounds<CT, QU><<<grid, CT, smem, stream>>>(d_parts, nparts, nfull, d_next, ngmax, rounds_nbsm(ngmax), ngq,
-                                                        nbq);
+    k_order_rounds<CT, SLOTS><<<grid, CT, smem, stream>>>(d_parts, nparts, nfull, d_next, ngmax, rounds_nbsm(ngmax),
+                                                           ngq, nbq);
     return cudaGetLastError();
 }
 
@@ -1210,7 +1230,7 @@ static cudaError_t launch_loop(const PartDesc *d_parts, int nparts, uint32_t *d_
         k_order_loop<T><<<grid, T, smem, stream>>>(d_parts, nparts, d_next, ngmax);
         return cudaGetLastError();
     } else if constexpr (T >= CAP && T >= SMAX) {
-        return launch_rounds<T, false>(d_parts, nparts, nparts, d_next, ngmax, 0, grid, stream);
+        return launch_rounds<T, 1>(d_parts, nparts, nparts, d_next, ngmax, 0, grid, stream);
     } else {
         return cudaErrorInvalidConfiguration;  // the rounds kernel needs at least CAP threads
     }
@@ -1226,8 +1246,8 @@ static int occupancy(int ngmax, int algo) {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_order_loop<T>, T, smem);
     } else if constexpr (T >= CAP && T >= SMAX) {
         const size_t smem = rounds_smem_full(ngmax);
-        allow_smem(k_order_rounds<T, false>);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_order_rounds<T, false>, T, smem);
+        allow_smem(k_order_rounds<T, 1>);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_order_rounds<T, 1>, T, smem);
     } else {
         blocks = 1;
     }
@@ -1254,19 +1274,20 @@ static int pick_threads(int ngmax, bool batched, int algo) {
 // are predicted faster.  Cost model (measured on GB300): a part costs n ln n; a whole CTA
 // orders at speed 1, a quarter at 0.41 with four per SM.  kmin parts are too large for a
 // quarter.
-static int quarter_split(const std::vector<uint32_t> &ns, int sms, int kmin) {
+static int quarter_split(const std::vector<uint32_t> &ns, int sms, int kmin, int slots = 4) {
     const int P = (int)ns.size();
     if (kmin >= P) return -1;
     std::vector<double> w(P), tail(P + 1, 0.0);
     for (int i = 0; i < P; ++i) w[i] = (double)ns[i] * std::log((double)ns[i] + 2.0);
     for (int i = P - 1; i >= 0; --i) tail[i] = tail[i + 1] + w[i];
-    const double RQ = 0.41;
+    // speed of one part slot relative to a whole CTA (measured for quarters; assumed for 2 and 8)
+    const double RQ = slots == 2 ? 0.7 : slots == 8 ? 0.22 : 0.41;
     double best = std::max(tail[0] / sms, w[0]);  // whole CTAs only
     int pick = -1;
     for (int k = kmin; k <= std::min(P - 1, std::max(kmin, sms)); ++k) {
         const double tfull = k > 0 ? std::max(w[0], tail[0] - tail[k] > 0 ? (tail[0] - tail[k]) / sms : 0.0) : 0.0;
         const int free_sms = std::max(1, sms - std::min(k, sms / 2));
-        const double tq = std::max(tail[k] / (4.0 * RQ * free_sms), w[k] / RQ);
+        const double tq = std::max(tail[k] / (slots * RQ * free_sms), w[k] / RQ);
         const double t = std::max(tfull, tq);
         if (t < best * 0.97) {  // a clear predicted gain only
             best = t;
@@ -1280,14 +1301,17 @@ static int quarter_split(const std::vector<uint32_t> &ns, int sms, int kmin) {
 // their sizes, ngs their group counts); d_next holds two zeroed work counters
 static cudaError_t launch_set(const PartDesc *d_parts, int nparts, uint32_t *d_next, int ngmax, int T, int sms,
                               cudaStream_t stream, int algo, const std::vector<uint32_t> &ns,
-                              const std::vector<uint32_t> &ngs, bool throughput = false) {
+                              const std::vector<uint32_t> &ngs, bool throughput = false, bool any_sampler = false) {
     if (algo == 2 && g_quarters != 1 && !(g_loop_threads_override && g_loop_threads_override != 1024)) {
+        // parts per CTA after the whole-CTA parts: order_slots (4 by default); eight 128-thread
+        // slots cannot run the sampler variant
+        const int slots = (g_slots == 8 && any_sampler) ? 4 : g_slots;
         int kmin = 0;
-        while (kmin < nparts && ngs[kmin] > (uint32_t)(Q_SG * 32)) ++kmin;
+        while (kmin < nparts && ngs[kmin] > (uint32_t)(slot_sg(slots) * 32)) ++kmin;
         int nfull = -1;
         if (g_full_parts > 0) nfull = std::max(kmin, std::min(g_full_parts, nparts));
         else if (g_quarters == 2) nfull = kmin;
-        else if (nparts >= 2 * sms) nfull = quarter_split(ns, sms, kmin);
+        else if (nparts >= 2 * sms) nfull = quarter_split(ns, sms, kmin, slots);
         else if (throughput && nparts - kmin >= 8) {
             // a server launch: parts of 64k points and more keep whole CTAs (a quarter
             // orders one at about 0.41 of a whole CTA's speed), the rest share SMs
@@ -1297,8 +1321,12 @@ static cudaError_t launch_set(const PartDesc *d_parts, int nparts, uint32_t *d_n
         if (nfull >= 0 && nfull < nparts) {
             const int ngq = (int)ngs[nfull];
             // a small launch takes only the CTAs its parts fill (other launches share the GPU)
-            const int grid = throughput ? std::min(sms, nfull + (nparts - nfull + 3) / 4) : sms;
-            return launch_rounds<1024, true>(d_parts, nparts, nfull, d_next, ngmax, ngq, grid, stream);
+            const int grid = throughput ? std::min(sms, nfull + (nparts - nfull + slots - 1) / slots) : sms;
+            switch (slots) {
+                case 2: return launch_rounds<1024, 2>(d_parts, nparts, nfull, d_next, ngmax, ngq, grid, stream);
+                case 8: return launch_rounds<1024, 8>(d_parts, nparts, nfull, d_next, ngmax, ngq, grid, stream);
+                default: return launch_rounds<1024, 4>(d_parts, nparts, nfull, d_next, ngmax, ngq, grid, stream);
+            }
         }
     }
     int per_sm = 1;
@@ -1444,8 +1472,11 @@ bs_status order_parts(std::vector<PartDesc> &hp, cudaStream_t stream, bool batch
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         // the one-pick-per-step kernel only knows the exact greedy permutation
         // (and only the rounds kernel publishes per-part completion flags)
-        bool sampled = false;
-        for (const auto &q : sorted) sampled |= q.variant == 1 || q.done != nullptr;
+        bool sampled = false, any_variant1 = false;
+        for (const auto &q : sorted) {
+            sampled |= q.variant == 1 || q.done != nullptr;
+            any_variant1 |= q.variant == 1;
+        }
         const int algo = sampled ? 2 : g_order_algo;
         timing_mark(1, 0, stream);
         std::vector<uint32_t> ns(nparts), ngs(nparts);
@@ -1487,7 +1518,8 @@ bs_status order_parts(std::vector<PartDesc> &hp, cudaStream_t stream, bool batch
                     uint32_t ngr = 1;
                     for (int r = kc; r < nparts; ++r) ngr = std::max(ngr, sorted[r].ng);
                     e = launch_set(d_parts + kc, nparts - kc, d_next, (int)ngr,
-                                   pick_threads((int)ngr, batched, algo), sms, stream, algo, ns2, ngs2);
+                                   pick_threads((int)ngr, batched, algo), sms, stream, algo, ns2, ngs2, throughput,
+                                   any_variant1);
                 }
                 if (e == cudaSuccess) e = cudaEventRecord(ev[1], side);
                 if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, ev[1], 0);
@@ -1496,7 +1528,7 @@ bs_status order_parts(std::vector<PartDesc> &hp, cudaStream_t stream, bool batch
             }
         } else {
             e = launch_set(d_parts, nparts, d_next, (int)ngmax, pick_threads((int)ngmax, batched, algo), sms, stream,
-                           algo, ns, ngs, throughput);
+                           algo, ns, ngs, throughput, any_variant1);
         }
         timing_mark(1, 1, stream);
         if (e != cudaSuccess) {

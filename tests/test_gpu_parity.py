@@ -222,6 +222,39 @@ def test_order_quarter_mode(bs, threads, quarters, full_parts):
         assert np.array_equal(_np(got[i][0], np.uint32), rp) and np.array_equal(_np(got[i][1]), rr), i
 
 
+@pytest.mark.parametrize("slots", [2, 8])
+def test_order_slots_per_cta(bs, slots):
+    """Two or eight parts per 1024-thread CTA (512- or 128-thread slots) after the whole-CTA
+    parts: every part equals the plain launch's result and the oracle's; a launch with a
+    sampler part falls back to quarters for eight slots."""
+    g = np.random.default_rng(17)
+    keys, starts = [], []
+    for i in range(600):
+        n = int(g.integers(30, 5000)) if i % 50 else int(g.integers(30000, 300000))
+        pts = np.unique(g.integers(0, 1 << int(g.integers(6, 21)), size=(n, 3)), axis=0)
+        order = np.argsort(oracle.pack(pts), kind="stable")
+        keys.append(_dev(oracle.pack(pts[order]).view(np.int64)))
+        starts.append(int(g.integers(0, len(pts))))
+    try:
+        bs.set_tuning("order_quarters", 1)
+        base = bs.order_batched(keys, starts=starts)
+        bs.set_tuning("order_quarters", 2)
+        bs.set_tuning("order_slots", slots)
+        got = bs.order_batched(keys, starts=starts)
+        mixed = bs.order_batched(keys[:40], starts=starts[:40], variants=[1] + [0] * 39)
+    finally:
+        bs.set_tuning("order_quarters", 0)
+        bs.set_tuning("order_slots", 0)
+    for i in range(len(keys)):
+        assert torch.equal(base[i][0], got[i][0]) and torch.equal(base[i][1], got[i][1]), i
+        assert torch.equal(base[i][2], got[i][2]), i
+    for i in range(1, 40):
+        assert torch.equal(base[i][0], mixed[i][0]), i
+    for i in (0, 1, 50, 599):
+        rp, rr = oracle.greedy(_np(keys[i]).view(np.uint64), starts[i], nthreads=oracle.num_threads())
+        assert np.array_equal(_np(got[i][0], np.uint32), rp) and np.array_equal(_np(got[i][1]), rr), i
+
+
 @pytest.mark.parametrize("threads", [64, 128, 256, 512, 1024])
 def test_order_launch_shape_independent(bs, threads):
     g = np.random.default_rng(4)
@@ -563,7 +596,7 @@ def test_autotune_picks_a_shape_and_keeps_results(bs):
         assert best in times and set(times) == set(autotune.DEFAULT_CANDIDATES)
         got = bs.order_batched(keys)
     finally:
-        for n in ("order_threads", "order_quarters", "order_full_parts"):
+        for n in autotune.NAMES:
             bs.set_tuning(n, 0)
     for a, b in zip(base, got):
         assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
