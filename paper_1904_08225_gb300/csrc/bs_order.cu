@@ -261,6 +261,7 @@ struct RoundsSm {
     uint32_t ppos[MAXP], tail[MAXP];
     uint32_t part, ccnt, gcnt, sgcnt, npick, icut;  // gather counters (reset when the previous round applies)
     uint32_t agcnt, asgcnt, nheavy;                 // apply counters (reset when the round's picks are written)
+    uint32_t gnext, anext;  // the next listed group a warp takes in the gather and in the bucket updates
     int shift;
     int64_t tieD;
     // cluster mode: this CTA's best (top key) and the leader's candidate counters, one
@@ -284,6 +285,13 @@ static int rounds_nbsm(int ngmax) {
 
 __device__ __forceinline__ void part_sync(int bar, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthreads) : "memory");
+}
+
+// The next work item for the calling warp from a shared counter (lane 0 takes it).
+__device__ __forceinline__ uint32_t take_next(uint32_t *ctr, int lane) {
+    uint32_t v = 0;
+    if (lane == 0) v = atomicAdd(ctr, 1u);
+    return __shfl_sync(0xffffffffu, v, 0);
 }
 
 // A box with its corners unpacked.
@@ -390,6 +398,7 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
         Sm.shift = 3;
         Sm.tieD = -2;
         Sm.ccnt = 0; Sm.gcnt = 0; Sm.sgcnt = 0; Sm.icut = 0xffffffffu;
+        Sm.gnext = 0; Sm.anext = 0;
         Sm.cc2[0] = 0; Sm.cc2[1] = 0;
         if (SAMPLER && !CL && P.variant == 1) {  // remove the start from the remaining set (swap with the last)
             const uint32_t y = P.R[n - 1];
@@ -612,7 +621,9 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
             }
             part_sync(bar, TP);
             const uint32_t ngl = Sm.gcnt;
-            for (uint32_t li = warp; li < ngl; li += NW) {
+            // each warp takes the next listed group when it is done with one (the groups'
+            // costs differ widely; a fixed stride leaves the slot waiting for the busiest warp)
+            for (uint32_t li = take_next(&Sm.gnext, lane); li < ngl; li = take_next(&Sm.gnext, lane)) {
                 const uint32_t g = s_glist[li];
                 const uint32_t b = g * 32 + lane;
                 const uint64_t bk = b < nb ? bkey[b] : 0ull;
@@ -700,7 +711,7 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
                 }
             }
             part_sync(bar, TP);  // every thread has read the counters
-            if (tid == 0) { Sm.ccnt = 0; Sm.gcnt = 0; Sm.sgcnt = 0; Sm.icut = 0xffffffffu; }
+            if (tid == 0) { Sm.ccnt = 0; Sm.gcnt = 0; Sm.sgcnt = 0; Sm.icut = 0xffffffffu; Sm.gnext = 0; }
             part_sync(bar, TP);
             continue;
         }
@@ -885,8 +896,8 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
         if (tid == 0) {
             // the next round's gather counters (this round read them before the last
             // barrier) and this round's apply counters
-            Sm.ccnt = 0; Sm.gcnt = 0; Sm.sgcnt = 0; Sm.icut = 0xffffffffu;
-            Sm.asgcnt = 0; Sm.agcnt = 0; Sm.nheavy = 0;
+            Sm.ccnt = 0; Sm.gcnt = 0; Sm.sgcnt = 0; Sm.icut = 0xffffffffu; Sm.gnext = 0;
+            Sm.asgcnt = 0; Sm.agcnt = 0; Sm.nheavy = 0; Sm.anext = 0;
         }
         part_sync(bar, TP);
         const uint64_t all = np >= 64 ? ~0ull : ((1ull << np) - 1ull);
@@ -941,7 +952,7 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
         }
         part_sync(bar, TP);
         const uint32_t ngl = Sm.agcnt;
-        for (uint32_t li = warp; li < ngl; li += NW) {
+        for (uint32_t li = take_next(&Sm.anext, lane); li < ngl; li = take_next(&Sm.anext, lane)) {
             const uint32_t g = s_glist[li];
             const uint64_t gm = pick_mask(np, Sm.pi, Sm.px, Sm.py, Sm.pz, Sm.sgmask[g >> 5], 10, g, s_glo[g], s_ghi[g],
                                           (int64_t)(s_gkey[g] >> 10) - 1);
