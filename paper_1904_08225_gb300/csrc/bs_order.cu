@@ -283,6 +283,20 @@ static int rounds_nbsm(int ngmax) {
     return slot_bytes<MAX_SG>(NB_SMEM, ngmax) <= SMEM_LIMIT ? NB_SMEM : 0;
 }
 
+// Candidate matrix of a whole 1024-thread CTA: row r holds, for every candidate c of the
+// round, min(2^32 - 1, d(r, c) - tau + 1), or 0 when d(r, c) < tau or r == c -- the
+// value the candidate greedy takes the minimum with when r is picked.  Rows of CAP
+// entries after the part's records, as many as the shared memory holds (at most CAP);
+// the matrix serves the rounds whose candidates fit it.
+constexpr size_t MAT_ROW = (size_t)CAP * 4;
+__host__ __device__ constexpr int mat_rows(int nbcap, int ngcap) {
+    return slot_bytes<MAX_SG>(nbcap, ngcap) >= SMEM_LIMIT
+               ? 0
+               : ((SMEM_LIMIT - slot_bytes<MAX_SG>(nbcap, ngcap)) / MAT_ROW >= (size_t)CAP
+                      ? CAP
+                      : (int)((SMEM_LIMIT - slot_bytes<MAX_SG>(nbcap, ngcap)) / MAT_ROW));
+}
+
 __device__ __forceinline__ void part_sync(int bar, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthreads) : "memory");
 }
@@ -342,8 +356,12 @@ __device__ __forceinline__ uint64_t pick_mask(uint32_t np, const uint32_t *pi, c
 // exact ordering (variant 0) runs in cluster mode, with bucket records in global memory.
 template <int TP, int SG, bool CL = false>
 __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm, unsigned char *slot, int nbsm,
-                                            int ngcap, int tid, int bar, int simw, int crank = 0, int csize = 1) {
+                                            int ngcap, int tid, int bar, int simw, int crank = 0, int csize = 1,
+                                            uint32_t *mat = nullptr, int matrows = 0) {
     static_assert(TP >= CAP, "the candidate sort needs one thread per candidate");
+    // the candidate matrix (whole 1024-thread CTAs only: it takes the shared memory that
+    // part slots divide among themselves)
+    constexpr bool MATRIX = TP == 1024 && !CL;
     // the sampler (variant 1) sorts its sample with one thread per entry: slots of fewer
     // than SMAX threads order exact parts only (the host routes sampler parts elsewhere)
     constexpr bool SAMPLER = TP >= SMAX;
@@ -716,7 +734,11 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
             continue;
         }
         // (4) candidates in index order: slot order is the lowest-index tie-break (the
-        //     leader's candidates in cluster mode; the other CTAs wait at the next barrier)
+        //     leader's candidates in cluster mode; the other CTAs wait at the next barrier).
+        //     With the candidate matrix (a round of 32-bit keys whose candidates fit it) the
+        //     sorted candidates go to the sample arrays, which the exact variant leaves
+        //     unused, and every thread then fills rows of the matrix
+        const bool usemat = MATRIX && !tie && ccnt <= (uint32_t)matrows && D1 - tau < (int64_t)(1u << OFF_BITS) - 1;
         if (leader && !tie) {
             uint32_t ci = 0, rank = 0;
             int64_t cd = 0;
@@ -726,9 +748,30 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
                 cd = Sm.cd[tid];
                 ck = Sm.ck[tid];
                 for (uint32_t u = 0; u < ccnt; ++u) rank += Sm.ci[u] < ci ? 1u : 0u;
+                if (usemat) {
+                    Sm.sc[rank] = ci;
+                    Sm.sd[rank] = cd;
+                    Sm.sk[rank] = ck;
+                }
             }
             part_sync(bar, TP);
-            if (tid < ccnt) {
+            if constexpr (MATRIX) {
+                if (usemat) {
+                    for (uint32_t r = warp; r < ccnt; r += NW) {
+                        const uint64_t pr = Sm.sk[r];
+                        const int32_t rx = (int32_t)pos_x(pr), ry = (int32_t)pos_y(pr), rz = (int32_t)pos_z(pr);
+                        for (uint32_t c = lane; c < ccnt; c += 32) {
+                            const uint64_t qc = Sm.sk[c];
+                            const int32_t dx = (int32_t)pos_x(qc) - rx, dy = (int32_t)pos_y(qc) - ry,
+                                          dz = (int32_t)pos_z(qc) - rz;
+                            const int64_t t = (int64_t)dx * dx + (int64_t)dy * dy + (int64_t)dz * dz - tau;
+                            mat[r * CAP + c] = (c == r || t < 0) ? 0u
+                                                                 : (t >= (int64_t)0xfffffffeu ? 0xffffffffu : (uint32_t)t + 1u);
+                        }
+                    }
+                }
+            }
+            if (!usemat && tid < ccnt) {
                 Sm.ci[rank] = ci;
                 Sm.cd[rank] = cd;
                 Sm.ck[rank] = ck;
@@ -739,7 +782,47 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
         //     slot lane + 32u lives in lane's register u.  The updates are branch-free (a
         //     branch per register keeps the four updates from overlapping); pick t is
         //     recorded in lane t & 31 and written out after the loop.
-        if (leader && warp == simw) {
+        if (leader && warp == simw && usemat) {
+            // the matrix greedy: a pick lowers every candidate's key to its row's entry
+            // (an entry of 0 leaves the round, the picked candidate's own entry among
+            // them); 0 << CAP_BITS | slot marks a candidate out of the round
+            const uint32_t budget = min((uint32_t)MAXP, m - k);
+            uint32_t np = 0;
+            uint32_t rp[CPL];
+            uint32_t rec[2] = {0u, 0u};  // slot << OFF_BITS | (D - tau)
+#pragma unroll
+            for (int u = 0; u < CPL; ++u) {
+                const uint32_t sl = lane + 32 * u;
+                rp[u] = sl < ccnt ? (uint32_t)(Sm.sd[sl] - tau) + 1u : 0u;
+            }
+            const uint32_t *mcol = mat + lane;
+            while (np < budget) {
+                uint32_t kmax = 0;
+#pragma unroll
+                for (int u = 0; u < CPL; ++u) kmax = max(kmax, (rp[u] << CAP_BITS) | (uint32_t)(CAP - 1 - (lane + 32 * u)));
+                const uint32_t best = __reduce_max_sync(FULL, kmax);
+                if (best < (uint32_t)CAP) break;
+                const uint32_t slot = (uint32_t)(CAP - 1) - (best & (uint32_t)(CAP - 1));
+                const uint32_t r = (slot << OFF_BITS) | ((best >> CAP_BITS) - 1u);
+                rec[0] = (lane == (int)(np & 31) && np < 32) ? r : rec[0];
+                rec[1] = (lane == (int)(np & 31) && np >= 32) ? r : rec[1];
+                ++np;
+                const uint32_t *row = mcol + slot * CAP;
+#pragma unroll
+                for (int u = 0; u < CPL; ++u) rp[u] = min(rp[u], row[32 * u]);
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t t = lane + 32 * h;
+                if (t < np) {
+                    const uint32_t slot = rec[h] >> OFF_BITS;
+                    Sm.pi[t] = Sm.sc[slot];
+                    Sm.pk[t] = Sm.sk[slot];
+                    Sm.pd[t] = tau + (int64_t)(rec[h] & ((1u << OFF_BITS) - 1u));
+                }
+            }
+            if (lane == 0) Sm.npick = np;
+        } else if (leader && warp == simw) {
             const uint32_t budget = min((uint32_t)MAXP, m - k);
             const bool tiecut = icut != 0xffffffffu;
             uint32_t np = 0;
@@ -1073,7 +1156,9 @@ __global__ void __launch_bounds__(CT) k_order_rounds(const PartDesc *__restrict_
         const uint32_t p = s_part[0];
         __syncthreads();
         if (p >= (uint32_t)nfull) break;
-        rounds_part<CT, MAX_SG>(parts[p], *(RoundsSm<MAX_SG> *)smraw, smraw, nbsm, ngmax, threadIdx.x, 0, 0);
+        const int mrows = CT == 1024 ? mat_rows(nbsm, ngmax) : 0;
+        rounds_part<CT, MAX_SG>(parts[p], *(RoundsSm<MAX_SG> *)smraw, smraw, nbsm, ngmax, threadIdx.x, 0, 0, 0, 1,
+                                (uint32_t *)(smraw + slot_bytes<MAX_SG>(nbsm, ngmax)), mrows);
     }
     if constexpr (SLOTS > 1) {
         constexpr int ST = CT / SLOTS, S_SG = slot_sg(SLOTS), SW = ST / 32;
@@ -1204,7 +1289,11 @@ static cudaError_t allow_smem(K kern) {
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
 }
 
-static size_t rounds_smem_full(int ngmax) { return slot_bytes<MAX_SG>(rounds_nbsm(ngmax), ngmax); }
+// whole-CTA shared memory: the part's records, then (1024-thread CTAs) the candidate matrix
+static size_t rounds_smem_full(int ngmax, int ct) {
+    const int nbsm = rounds_nbsm(ngmax);
+    return slot_bytes<MAX_SG>(nbsm, ngmax) + (ct == 1024 ? (size_t)mat_rows(nbsm, ngmax) * MAT_ROW : 0);
+}
 
 // slot-mode bucket capacity: what is left of a slot's share of the shared memory
 template <int SLOTS>
@@ -1218,7 +1307,7 @@ template <int CT, int SLOTS>
 static cudaError_t launch_rounds(const PartDesc *d_parts, int nparts, int nfull, uint32_t *d_next, int ngmax, int ngq,
                                  int grid, cudaStream_t stream) {
     int nbq = 0;
-    size_t smem = rounds_smem_full(ngmax);
+    size_t smem = rounds_smem_full(ngmax, CT);
     if constexpr (SLOTS > 1) {
         nbq = slot_nb<SLOTS>(ngq);
         smem = std::max(smem, SLOTS * slot_bytes<slot_sg(SLOTS)>(nbq, ngq));
@@ -1256,7 +1345,7 @@ static int occupancy(int ngmax, int algo) {
         allow_smem(k_order_loop<T>);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_order_loop<T>, T, smem);
     } else if constexpr (T >= CAP && T >= SMAX) {
-        const size_t smem = rounds_smem_full(ngmax);
+        const size_t smem = rounds_smem_full(ngmax, T);
         allow_smem(k_order_rounds<T, 1>);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_order_rounds<T, 1>, T, smem);
     } else {
