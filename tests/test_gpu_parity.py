@@ -272,6 +272,34 @@ def test_order_launch_shape_independent(bs, threads):
     assert torch.equal(base[0], gotb[0][0]) and torch.equal(base[1], gotb[0][1])
 
 
+def test_whole_cta_matrix_greedy(bs):
+    """Whole 1024-thread CTAs run the candidate greedy on the shared-memory distance
+    matrix; 512-thread CTAs keep the candidates in registers.  Parts of 70k-300k points,
+    one with coarse coordinates (many equal distances and tie rounds) and one spread over
+    the whole grid (rounds whose distances need 64 bits): both launch shapes give the
+    same permutation and radii, and the oracle's on one part."""
+    g = np.random.default_rng(23)
+    keys, starts = [], []
+    for n, bits in ((70_000, 21), (150_000, 14), (300_000, 9), (120_000, 21)):
+        pts = np.unique(g.integers(0, 1 << bits, size=(n, 3)), axis=0)
+        order = np.argsort(oracle.pack(pts), kind="stable")
+        keys.append(_dev(oracle.pack(pts[order]).view(np.int64)))
+        starts.append(int(g.integers(0, len(pts))))
+    runs = {}
+    try:
+        for threads in (512, 1024):
+            bs.set_tuning("order_threads", threads)
+            runs[threads] = bs.order_batched(keys, starts=starts)
+    finally:
+        bs.set_tuning("order_threads", 0)
+    for i in range(len(keys)):
+        for j in range(3):
+            assert torch.equal(runs[512][i][j], runs[1024][i][j]), (i, j)
+    rp, rr = oracle.greedy(_np(keys[0]).view(np.uint64), starts[0], nthreads=oracle.num_threads())
+    got = runs[1024][0]
+    assert np.array_equal(_np(got[0], np.uint32), rp) and np.array_equal(_np(got[1]), rr)
+
+
 def test_cad_part_full_size(bs):
     """The CAD-like part (2000 boxes + 500 cylinders, ~192k tris) from 6 axis + 2 diagonal
     directions at 1024^2: surfel arrays identical to the oracle; the whole ordering of its
