@@ -50,11 +50,11 @@ BYTES_PER_VISIT = 16   # 8 B key + 8 B D read
 BYTES_PER_IMPROVE = 8  # 8 B D write
 BYTES_OUT = 16         # perm 4 + rad2 8 + radius 4
 # DRAM bytes (read + write) per surfel ordered of the dominant launch (the ordering of the
-# non-lead parts, k_order_rounds<1024, 1>), from an ncu capture of the same launch on a
+# non-lead parts, k_order_rounds<1024, 4>), from an ncu capture of the same launch on a
 # seeded 1216-part subset of that band (bench.py --order-subset 1216), scaled per surfel:
 # profiles/k_order_rounds_traffic_subset1216.md.  Must be re-measured (or set to None)
 # whenever k_order_rounds changes.
-DRAM_BYTES_PER_SURFEL = 1079.4
+DRAM_BYTES_PER_SURFEL = 1073.6
 
 
 def band_layout(ns, thresholds):
@@ -698,7 +698,7 @@ def main():
                          "unit": "GB/s", "frac": achieved / peak,
                          "traffic": (DRAM_BYTES_PER_SURFEL * float(ns[rest].sum())) if DRAM_BYTES_PER_SURFEL else None,
                          "traffic_source": "ncu dram__bytes_read+write of this kernel on a seeded 1216-part subset "
-                                           "of the band (bench.py --order-subset 1216), 1079.4 B per surfel, scaled "
+                                           f"of the band (bench.py --order-subset 1216), {DRAM_BYTES_PER_SURFEL} B per surfel, scaled "
                                            "to the launch's surfels",
                          "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured" else "fallback 6800 GB/s",
                          "algorithmic_bytes_per_launch": bytes_launch, "loop_ms_per_launch": loop_avg,
