@@ -359,9 +359,11 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
                                             int ngcap, int tid, int bar, int simw, int crank = 0, int csize = 1,
                                             uint32_t *mat = nullptr, int matrows = 0) {
     static_assert(TP >= CAP, "the candidate sort needs one thread per candidate");
-    // the candidate matrix (whole 1024-thread CTAs only: it takes the shared memory that
-    // part slots divide among themselves)
-    constexpr bool MATRIX = TP == 1024 && !CL;
+    // the candidate matrix: rows of MS entries, CAP on whole 1024-thread CTAs and 64 in
+    // part slots (rounds of at most 64 candidates there: the slots share the CTA's memory)
+    constexpr bool MATRIX = !CL;
+    constexpr int MS = TP == 1024 ? CAP : 64;
+    constexpr int CPLM = MS / 32;
     // the sampler (variant 1) sorts its sample with one thread per entry: slots of fewer
     // than SMAX threads order exact parts only (the host routes sampler parts elsewhere)
     constexpr bool SAMPLER = TP >= SMAX;
@@ -738,7 +740,7 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
         //     With the candidate matrix (a round of 32-bit keys whose candidates fit it) the
         //     sorted candidates go to the sample arrays, which the exact variant leaves
         //     unused, and every thread then fills rows of the matrix
-        const bool usemat = MATRIX && !tie && ccnt <= (uint32_t)matrows && D1 - tau < (int64_t)(1u << OFF_BITS) - 1;
+        const bool usemat = MATRIX && !tie && ccnt <= (uint32_t)min(matrows, MS) && D1 - tau < (int64_t)(1u << OFF_BITS) - 1;
         if (leader && !tie) {
             uint32_t ci = 0, rank = 0;
             int64_t cd = 0;
@@ -765,7 +767,7 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
                             const int32_t dx = (int32_t)pos_x(qc) - rx, dy = (int32_t)pos_y(qc) - ry,
                                           dz = (int32_t)pos_z(qc) - rz;
                             const int64_t t = (int64_t)dx * dx + (int64_t)dy * dy + (int64_t)dz * dz - tau;
-                            mat[r * CAP + c] = (c == r || t < 0) ? 0u
+                            mat[r * MS + c] = (c == r || t < 0) ? 0u
                                                                  : (t >= (int64_t)0xfffffffeu ? 0xffffffffu : (uint32_t)t + 1u);
                         }
                     }
@@ -788,10 +790,10 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
             // them); 0 << CAP_BITS | slot marks a candidate out of the round
             const uint32_t budget = min((uint32_t)MAXP, m - k);
             uint32_t np = 0;
-            uint32_t rp[CPL];
+            uint32_t rp[CPLM];
             uint32_t rec[2] = {0u, 0u};  // slot << OFF_BITS | (D - tau)
 #pragma unroll
-            for (int u = 0; u < CPL; ++u) {
+            for (int u = 0; u < CPLM; ++u) {
                 const uint32_t sl = lane + 32 * u;
                 rp[u] = sl < ccnt ? (uint32_t)(Sm.sd[sl] - tau) + 1u : 0u;
             }
@@ -799,7 +801,7 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
             while (np < budget) {
                 uint32_t kmax = 0;
 #pragma unroll
-                for (int u = 0; u < CPL; ++u) kmax = max(kmax, (rp[u] << CAP_BITS) | (uint32_t)(CAP - 1 - (lane + 32 * u)));
+                for (int u = 0; u < CPLM; ++u) kmax = max(kmax, (rp[u] << CAP_BITS) | (uint32_t)(CAP - 1 - (lane + 32 * u)));
                 const uint32_t best = __reduce_max_sync(FULL, kmax);
                 if (best < (uint32_t)CAP) break;
                 const uint32_t slot = (uint32_t)(CAP - 1) - (best & (uint32_t)(CAP - 1));
@@ -807,9 +809,9 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
                 rec[0] = (lane == (int)(np & 31) && np < 32) ? r : rec[0];
                 rec[1] = (lane == (int)(np & 31) && np >= 32) ? r : rec[1];
                 ++np;
-                const uint32_t *row = mcol + slot * CAP;
+                const uint32_t *row = mcol + slot * MS;
 #pragma unroll
-                for (int u = 0; u < CPL; ++u) rp[u] = min(rp[u], row[32 * u]);
+                for (int u = 0; u < CPLM; ++u) rp[u] = min(rp[u], row[32 * u]);
             }
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -1146,7 +1148,8 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
 // are the two phases' work counters.
 template <int CT, int SLOTS>
 __global__ void __launch_bounds__(CT) k_order_rounds(const PartDesc *__restrict__ parts, int nparts, int nfull,
-                                                     uint32_t *__restrict__ next, int ngmax, int nbsm, int ngq, int nbq) {
+                                                     uint32_t *__restrict__ next, int ngmax, int nbsm, int ngq, int nbq,
+                                                     int qmat) {
     extern __shared__ __align__(16) unsigned char smraw[];
     static_assert(SLOTS == 1 || SLOTS == 2 || SLOTS == 4 || SLOTS == 8, "1, 2, 4 or 8 part slots per CTA");
     __shared__ uint32_t s_part[8];  // one entry per slot
@@ -1163,7 +1166,9 @@ __global__ void __launch_bounds__(CT) k_order_rounds(const PartDesc *__restrict_
     if constexpr (SLOTS > 1) {
         constexpr int ST = CT / SLOTS, S_SG = slot_sg(SLOTS), SW = ST / 32;
         const int q = threadIdx.x / ST, tid = threadIdx.x % ST;
-        unsigned char *slot = smraw + (size_t)q * slot_bytes<S_SG>(nbq, ngq);
+        // a slot: its records, then (qmat = 64) a 64 x 64 candidate matrix
+        const size_t sb = slot_bytes<S_SG>(nbq, ngq);
+        unsigned char *slot = smraw + (size_t)q * (sb + (size_t)qmat * 64 * 4);
         for (;;) {
             if (tid == 0) s_part[q] = (uint32_t)nfull + atomicAdd(&next[1], 1u);
             part_sync(1 + q, ST);
@@ -1171,7 +1176,8 @@ __global__ void __launch_bounds__(CT) k_order_rounds(const PartDesc *__restrict_
             part_sync(1 + q, ST);
             if (p >= (uint32_t)nparts) break;
             // the slots' serial warps sit on different schedulers (warp index modulo 4)
-            rounds_part<ST, S_SG>(parts[p], *(RoundsSm<S_SG> *)slot, slot, nbq, ngq, tid, 1 + q, q % SW);
+            rounds_part<ST, S_SG>(parts[p], *(RoundsSm<S_SG> *)slot, slot, nbq, ngq, tid, 1 + q, q % SW, 0, 1,
+                                  (uint32_t *)(slot + sb), qmat);
         }
     }
 }
@@ -1307,16 +1313,20 @@ template <int CT, int SLOTS>
 static cudaError_t launch_rounds(const PartDesc *d_parts, int nparts, int nfull, uint32_t *d_next, int ngmax, int ngq,
                                  int grid, cudaStream_t stream) {
     int nbq = 0;
+    int qmat = 0;
     size_t smem = rounds_smem_full(ngmax, CT);
     if constexpr (SLOTS > 1) {
         nbq = slot_nb<SLOTS>(ngq);
-        smem = std::max(smem, SLOTS * slot_bytes<slot_sg(SLOTS)>(nbq, ngq));
+        // a 64 x 64 candidate matrix per slot where the slots' records leave room for it
+        const size_t sb = slot_bytes<slot_sg(SLOTS)>(nbq, ngq);
+        qmat = SLOTS * (sb + 64 * 64 * 4) <= SMEM_LIMIT ? 64 : 0;
+        smem = std::max(smem, SLOTS * (sb + (size_t)qmat * 64 * 4));
     }
     if (smem > SMEM_LIMIT) return cudaErrorInvalidConfiguration;
     cudaError_t e = allow_smem(k_order_rounds<CT, SLOTS>);
     if (e != cudaSuccess) return e;
     k_order_rounds<CT, SLOTS><<<grid, CT, smem, stream>>>(d_parts, nparts, nfull, d_next, ngmax, rounds_nbsm(ngmax),
-                                                           ngq, nbq);
+                                                           ngq, nbq, qmat);
     return cudaGetLastError();
 }
 
