@@ -653,11 +653,21 @@ __global__ void __launch_bounds__(256) k_rs_hist(const uint64_t *__restrict__ ke
     counts[(uint64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
+// One digit pass: each block ranks its TILE rows by digit (stable: input order within a
+// digit), stages them in shared memory in digit order and writes every digit's run to its
+// place, so that consecutive threads store to consecutive addresses.
+constexpr size_t RS_SMEM = (size_t)TILE * 12 + (size_t)TILE_WARPS * 257 * 4 + 2 * 257 * 4 + 32 * 4;
 __global__ void __launch_bounds__(256) k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
                                                     uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
                                                     uint32_t n, int shift, const uint32_t *__restrict__ offsets,
                                                     uint32_t ntiles) {
-    __shared__ uint32_t cnt[TILE_WARPS][257];
+    extern __shared__ __align__(16) unsigned char rs_sm[];
+    uint64_t *sk = (uint64_t *)rs_sm;                         // the tile's keys in digit order
+    uint32_t *sv = (uint32_t *)(sk + TILE);                   // and values
+    uint32_t(*cnt)[257] = (uint32_t(*)[257])(sv + TILE);      // per warp and digit
+    uint32_t *dstart = &cnt[TILE_WARPS][0];                   // a digit's first staged row
+    uint32_t *soff = dstart + 257;                            // its output offset less dstart
+    uint32_t *wsum = soff + 257;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int d = threadIdx.x; d < TILE_WARPS * 257; d += 256) (&cnt[0][0])[d] = 0;
     __syncthreads();
@@ -680,6 +690,7 @@ __global__ void __launch_bounds__(256) k_rs_scatter(const uint64_t *__restrict__
     }
     __syncthreads();
     {
+        // digit d: the warps' exclusive prefix, then the digits' exclusive prefix in the tile
         const int d = threadIdx.x;
         uint32_t run = 0;
         for (int w = 0; w < TILE_WARPS; ++w) {
@@ -687,6 +698,19 @@ __global__ void __launch_bounds__(256) k_rs_scatter(const uint64_t *__restrict__
             cnt[w][d] = run;
             run += c;
         }
+        uint32_t x = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        uint32_t pre = 0;
+        for (int w = 0; w < warp; ++w) pre += wsum[w];
+        const uint32_t st = pre + x - run;
+        dstart[d] = st;
+        soff[d] = offsets[(uint64_t)d * ntiles + blockIdx.x] - st;
     }
     __syncthreads();
 #pragma unroll
@@ -694,10 +718,19 @@ __global__ void __launch_bounds__(256) k_rs_scatter(const uint64_t *__restrict__
         const uint64_t i = base + (uint64_t)r * 32 + lane;
         if (i < n) {
             const uint32_t d = (uint32_t)((k[r] >> shift) & 255u);
-            const uint32_t dst = offsets[(uint64_t)d * ntiles + blockIdx.x] + cnt[warp][d] + rank[r];
-            kout[dst] = k[r];
-            vout[dst] = v[r];
+            const uint32_t pos = dstart[d] + cnt[warp][d] + rank[r];
+            sk[pos] = k[r];
+            sv[pos] = v[r];
         }
+    }
+    __syncthreads();
+    const uint64_t b0 = (uint64_t)blockIdx.x * TILE;
+    const uint32_t nvalid = (uint32_t)min((uint64_t)TILE, (uint64_t)n - b0);
+    for (uint32_t j = threadIdx.x; j < nvalid; j += 256) {
+        const uint64_t key = sk[j];
+        const uint32_t dst = soff[(uint32_t)((key >> shift) & 255u)] + j;
+        kout[dst] = key;
+        vout[dst] = sv[j];
     }
 }
 
@@ -709,10 +742,11 @@ static void radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *ktmp, uint32_t 
     const uint32_t ntiles = (n + TILE - 1) / TILE;
     uint64_t *ka = keys, *kb = ktmp;
     uint32_t *va = vals, *vb = vtmp;
+    cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_SMEM);
     for (int shift = 0; shift < bits; shift += 8) {
         k_rs_hist<<<ntiles, 256, 0, stream>>>(ka, n, shift, counts, ntiles);
         scan_excl(counts, 256ull * ntiles, nullptr, scan_tmp, stream);
-        k_rs_scatter<<<ntiles, 256, 0, stream>>>(ka, va, kb, vb, n, shift, counts, ntiles);
+        k_rs_scatter<<<ntiles, 256, RS_SMEM, stream>>>(ka, va, kb, vb, n, shift, counts, ntiles);
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
     }
