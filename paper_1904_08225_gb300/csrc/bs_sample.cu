@@ -35,6 +35,7 @@ namespace bs {
 struct View {
     int32_t u[3], v[3], d[3];
     int64_t ulo, vlo, U1, V1, wbias;
+    uint64_t mU, mV;  // floor((2^64 - 1) / (2 U1)) and likewise for V1: exact division in project
 };
 
 struct Views {
@@ -67,6 +68,8 @@ static void make_frame(const bs_dir &dir, View &V) {
     V.U1 = uspan + 1;
     V.V1 = vspan + 1;
     V.wbias = wb;
+    V.mU = ~0ull / (uint64_t)(2 * V.U1);
+    V.mV = ~0ull / (uint64_t)(2 * V.V1);
 }
 
 // ---------------------------------------------------------------------------
@@ -252,15 +255,61 @@ __device__ __forceinline__ void project(const View &V, int res, const int32_t *q
     const int64_t uq = V.u[0] * x + V.u[1] * y + V.u[2] * z;
     const int64_t vq = V.v[0] * x + V.v[1] * y + V.v[2] * z;
     const int64_t dq = V.d[0] * x + V.d[1] * y + V.d[2] * z;
-    X = (int32_t)(((uq - V.ulo) * res * 512 + V.U1) / (2 * V.U1));
-    Y = (int32_t)(((vq - V.vlo) * res * 512 + V.V1) / (2 * V.V1));
+    // the numerators are non-negative (ulo and vlo are the smallest projections of the
+    // quantised cube), so the quotients are floors: div_area with the view's reciprocals
+    X = (int32_t)div_area((uint64_t)((uq - V.ulo) * res * 512 + V.U1), (uint64_t)(2 * V.U1), V.mU);
+    Y = (int32_t)div_area((uint64_t)((vq - V.vlo) * res * 512 + V.V1), (uint64_t)(2 * V.V1), V.mV);
     W = (uint32_t)(-dq + V.wbias);
 }
 
-// grid: (triangles of all parts, directions); setup[dir * T + global triangle]
+// The triangle normal n: integer cross product of its quantised edges, input vertex order.
+__device__ __forceinline__ void tri_normal(const int32_t *a, const int32_t *b, const int32_t *c, int64_t n[3]) {
+    int64_t e1[3], e2[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        e1[k] = (int64_t)b[k] - a[k];
+        e2[k] = (int64_t)c[k] - a[k];
+    }
+    n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+    n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+    n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+}
+
+// n as snorm16 components round(32767 n_a / |n|), round half to even, in double
+// precision (0 for a degenerate triangle).  Turning n toward a camera negates every
+// component exactly (the rounding is symmetric), so this is computed once per triangle.
+__device__ __noinline__ uint64_t snorm_pack(const int64_t n[3]) {
+    const double f0 = (double)n[0], f1 = (double)n[1], f2 = (double)n[2];
+    double ss = __dadd_rn(__dmul_rn(f0, f0), __dmul_rn(f1, f1));
+    ss = __dadd_rn(ss, __dmul_rn(f2, f2));
+    uint64_t np = 0;
+    if (ss != 0.0) {
+        const double len = __dsqrt_rn(ss);
+        const double c[3] = {f0, f1, f2};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int v = __double2int_rn(__ddiv_rn(__dmul_rn(32767.0, c[a]), len));
+            np |= (uint64_t)(uint16_t)(int16_t)v << (16 * a);
+        }
+    }
+    return np;
+}
+
+// packed snorm16 components negated
+__device__ __forceinline__ uint64_t snorm_negate(uint64_t np) {
+    uint64_t r = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) r |= (uint64_t)(uint16_t)(int16_t)(-(int)(int16_t)(uint16_t)(np >> (16 * a))) << (16 * a);
+    return r;
+}
+
+// grid: (triangles of all parts, directions); setup[dir * T + global triangle].  Bit 24
+// of a kept setup's ord: the triangle's normal points away from this view's camera (the
+// surfel takes the negated normal); the first direction writes each triangle's snorm16
+// normal to tnrm.
 __global__ void k_setup(const SPart *__restrict__ parts, const uint64_t *__restrict__ tofs, int nparts,
                         uint64_t T, const int32_t *__restrict__ q, SState *__restrict__ st, const Views views,
-                        TriSetup *__restrict__ out) {
+                        TriSetup *__restrict__ out, uint64_t *__restrict__ tnrm) {
     const int dir = blockIdx.y;
     const View &V = views.v[dir];
     for (uint64_t tg = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; tg < T; tg += (uint64_t)gridDim.x * blockDim.x) {
@@ -289,7 +338,12 @@ __global__ void k_setup(const SPart *__restrict__ parts, const uint64_t *__restr
         s.x[0] = X[0]; s.y[0] = Y[0]; s.w[0] = W[0];
         s.x[1] = X[o1]; s.y[1] = Y[o1]; s.w[1] = W[o1];
         s.x[2] = X[o2]; s.y[2] = Y[o2]; s.w[2] = W[o2];
-        s.ord = a2 == 0 ? 0xffffffffu : (uint32_t)(0 | (o1 << 2) | (o2 << 4) | ((uint32_t)p << 8));
+        int64_t n[3];
+        tri_normal(qp + 3ull * v0, qp + 3ull * v1, qp + 3ull * v2, n);
+        const bool flip = n[0] * V.d[0] + n[1] * V.d[1] + n[2] * V.d[2] < 0;
+        if (dir == 0) tnrm[tg] = snorm_pack(n);
+        s.ord = a2 == 0 ? 0xffffffffu
+                        : (uint32_t)(0 | (o1 << 2) | (o2 << 4) | ((uint32_t)p << 8) | ((uint32_t)flip << 24));
         s.area2 = a2;
         s.rcp = a2 == 0 ? 0ull : ~0ull / (uint64_t)a2;
         out[(uint64_t)dir * T + tg] = s;
@@ -537,9 +591,9 @@ struct Rows {
 // Resolve one covered pixel of direction dir: integer barycentric interpolation of
 // the quantised vertices (floor), normal of the triangle turned toward the camera
 // (snorm16, round half to even), face colour.
-__device__ void resolve_pixel(const View &V, const TriSetup &s, const int32_t *__restrict__ q,
-                              const uint32_t *__restrict__ tri, const uint8_t *__restrict__ rgb, uint32_t t,
-                              int32_t px, int32_t py, uint64_t &key, uint64_t &nrm_packed, uint32_t &rgb_packed) {
+__device__ void resolve_pixel(const TriSetup &s, const int32_t *__restrict__ q, const uint32_t *__restrict__ tri,
+                              const uint8_t *__restrict__ rgb, uint32_t t, uint64_t tn, int32_t px, int32_t py,
+                              uint64_t &key, uint64_t &nrm_packed, uint32_t &rgb_packed) {
     int64_t lam[3];
     cover(s, px, py, lam);
     const uint32_t vi[3] = {tri[3ull * t + 0], tri[3ull * t + 1], tri[3ull * t + 2]};
@@ -553,29 +607,7 @@ __device__ void resolve_pixel(const View &V, const TriSetup &s, const int32_t *_
         pos[a] = div_area(num, (uint64_t)s.area2, s.rcp);
     }
     key = pack_pos(pos[0], pos[1], pos[2]);
-    int64_t e1[3], e2[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        e1[a] = (int64_t)q[3ull * vi[1] + a] - q[3ull * vi[0] + a];
-        e2[a] = (int64_t)q[3ull * vi[2] + a] - q[3ull * vi[0] + a];
-    }
-    int64_t n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
-    const int64_t nd = n[0] * V.d[0] + n[1] * V.d[1] + n[2] * V.d[2];
-    if (nd < 0) { n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; }
-    const double f0 = (double)n[0], f1 = (double)n[1], f2 = (double)n[2];
-    double ss = __dadd_rn(__dmul_rn(f0, f0), __dmul_rn(f1, f1));
-    ss = __dadd_rn(ss, __dmul_rn(f2, f2));
-    uint64_t np = 0;
-    if (ss != 0.0) {
-        const double len = __dsqrt_rn(ss);
-        const double c[3] = {f0, f1, f2};
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const int v = __double2int_rn(__ddiv_rn(__dmul_rn(32767.0, c[a]), len));
-            np |= (uint64_t)(uint16_t)(int16_t)v << (16 * a);
-        }
-    }
-    nrm_packed = np;
+    nrm_packed = ((s.ord >> 24) & 1u) ? snorm_negate(tn) : tn;
     rgb_packed = rgb ? ((uint32_t)rgb[3ull * t] | ((uint32_t)rgb[3ull * t + 1] << 8) | ((uint32_t)rgb[3ull * t + 2] << 16))
                      : 0u;
 }
@@ -583,7 +615,7 @@ __device__ void resolve_pixel(const View &V, const TriSetup &s, const int32_t *_
 __global__ void __launch_bounds__(256) k_resolve(const unsigned long long *__restrict__ depth, uint64_t npix,
                                                  const SPart *__restrict__ parts, const uint64_t *__restrict__ pofs,
                                                  int nparts, uint64_t T, const int32_t *__restrict__ q,
-                                                 const TriSetup *__restrict__ setup, const Views views,
+                                                 const TriSetup *__restrict__ setup, const uint64_t *__restrict__ tnrm,
                                                  const uint32_t *__restrict__ blockofs, Rows rows) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t base = (uint64_t)blockIdx.x * TILE + (uint64_t)warp * TILE_ROUNDS * 32;
@@ -614,16 +646,18 @@ __global__ void __launch_bounds__(256) k_resolve(const unsigned long long *__res
                 p_hi = p + 1 < nparts ? pofs[p + 1] : npix;
             }
             const SPart &P = parts[p];
-            const uint64_t res2 = (uint64_t)P.res * P.res;
-            const uint64_t local = i - P.pofs;
-            const int dir = (int)(local / res2);
-            const uint64_t pix = local - (uint64_t)dir * res2;
-            const int32_t py = (int32_t)(pix / P.res), px = (int32_t)(pix % P.res);
+            // a part's pixels number below BS_MAX_DIRS * BS_MAX_RES^2 < 2^32
+            const uint32_t res = (uint32_t)P.res, res2 = res * res;
+            const uint32_t local = (uint32_t)(i - P.pofs);
+            const uint32_t dir = local / res2;
+            const uint32_t pix = local - dir * res2;
+            const uint32_t pyu = pix / res;
+            const int32_t py = (int32_t)pyu, px = (int32_t)(pix - pyu * res);
             const uint32_t t = (uint32_t)(dv & 0xffffffffull);
             const TriSetup s = setup[(uint64_t)dir * T + P.tofs + t];
             uint64_t key, np;
             uint32_t cp;
-            resolve_pixel(views.v[dir], s, q + 3ull * P.vofs, P.tri, P.rgb, t, px, py, key, np, cp);
+            resolve_pixel(s, q + 3ull * P.vofs, P.tri, P.rgb, t, tnrm[P.tofs + t], px, py, key, np, cp);
             rows.morton[o] = morton_of(key);
             rows.key[o] = key;
             rows.nrm[o] = np;
@@ -1023,6 +1057,7 @@ bs_status sample_visible_parts(const bs_mesh *meshes, const int *res, int nparts
         probe.take((size_t)nparts * 8);
         probe.take(3 * V * sizeof(int32_t));
         probe.take((size_t)ndirs * T * sizeof(TriSetup));
+        probe.take((size_t)T * 8);
         if (!image) probe.take(NP * sizeof(unsigned long long));
         probe.take(((size_t)ptiles + 1) * 4);
         probe.take(scan_tmp_words(ptiles) * 4);
@@ -1038,6 +1073,7 @@ bs_status sample_visible_parts(const bs_mesh *meshes, const int *res, int nparts
     uint64_t *d_cofs = (uint64_t *)A.take((size_t)nparts * 8);
     int32_t *q = (int32_t *)A.take(3 * V * sizeof(int32_t));
     TriSetup *setup = (TriSetup *)A.take((size_t)ndirs * T * sizeof(TriSetup));
+    uint64_t *tnrm = (uint64_t *)A.take((size_t)T * 8);
     // the depth buffer: the caller's image when only the depth pass is wanted
     unsigned long long *depth = image ? image : (unsigned long long *)A.take(NP * sizeof(unsigned long long));
     uint32_t *bc = (uint32_t *)A.take(((size_t)ptiles + 1) * 4);
@@ -1063,7 +1099,7 @@ bs_status sample_visible_parts(const bs_mesh *meshes, const int *res, int nparts
         k_quantise<<<(unsigned)NC, 256, 0, stream>>>(d_parts, d_cofs, nparts, d_st, q);
         if (T > 0) {
             dim3 gs((unsigned)std::min<uint64_t>((T + 255) / 256, (uint64_t)sms * 32), ndirs);
-            k_setup<<<gs, 256, 0, stream>>>(d_parts, d_tofs, nparts, T, q, d_st, views, setup);
+            k_setup<<<gs, 256, 0, stream>>>(d_parts, d_tofs, nparts, T, q, d_st, views, setup, tnrm);
             dim3 gr((unsigned)std::min<uint64_t>((T + 255) / 256, (uint64_t)sms * 16), ndirs);
             k_raster<<<gr, 256, 0, stream>>>(d_parts, T, setup, depth);
         }
@@ -1082,7 +1118,7 @@ bs_status sample_visible_parts(const bs_mesh *meshes, const int *res, int nparts
         }
         // ---- phase 2: resolve, sort, merge, write ----
         rc = merge_rows(nrows, nparts, d_parts, d_st, tot, sms, stream, &B, [&](const Rows &rows) {
-            k_resolve<<<ptiles, 256, 0, stream>>>(depth, NP, d_parts, d_pofs, nparts, T, q, setup, views, bc, rows);
+            k_resolve<<<ptiles, 256, 0, stream>>>(depth, NP, d_parts, d_pofs, nparts, T, q, setup, tnrm, bc, rows);
         });
         if (rc != BS_OK) break;
         rc = finish_parts(nparts, d_st, hs, out, stream, "bs_sample_visible");
