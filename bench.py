@@ -344,6 +344,9 @@ def main():
     from paper_1904_08225_gb300 import bs
     torch.cuda.set_device(local)
     if args.order_subset:
+        for kv in args.tune:
+            name, val = kv.split("=")
+            bs.set_tuning(name, int(val))
         return order_subset(bs, specs, args)
     dist = None
     if world > 1:
