@@ -395,6 +395,15 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
     const bool one_sg = !CL && ns == 1 && P.variant == 0;
     // bucket records: shared memory when they fit (generic pointers either way)
     const bool bsm = !CL && nb <= (uint32_t)nbsm;
+    if constexpr (MATRIX && TP == 1024) {
+        // a whole-CTA part whose bucket records stay in global memory: the candidate
+        // matrix may take their shared-memory space when that holds more rows
+        const int brows = (int)min((size_t)CAP, (size_t)nbsm * 24 / MAT_ROW);
+        if (!bsm && brows > matrows) {
+            mat = (uint32_t *)s_bkey;
+            matrows = brows;
+        }
+    }
     uint64_t *bkey = bsm ? s_bkey : P.bkey;
     const uint64_t *blo_p = bsm ? s_blo : P.blo;
     const uint64_t *bhi_p = bsm ? s_bhi : P.bhi;
