@@ -278,9 +278,12 @@ __host__ __device__ constexpr size_t slot_bytes(int nbcap, int ngcap) {
     return align16(sizeof(RoundsSm<SG>)) + (size_t)nbcap * 24 + align16((size_t)ngcap * 28);
 }
 
-// full-mode bucket capacity for a launch whose largest part has ngmax groups
-static int rounds_nbsm(int ngmax) {
-    return slot_bytes<MAX_SG>(NB_SMEM, ngmax) <= SMEM_LIMIT ? NB_SMEM : 0;
+// full-mode bucket capacity for a launch whose largest part has ngmax groups; nbmin =
+// buckets of its smallest whole-CTA part (0: unknown): when that part has more than
+// NB_SMEM buckets no whole-CTA part keeps bucket records in shared memory, and the
+// space is left to the candidate matrix and the L1 cache
+static int rounds_nbsm(int ngmax, int nbmin = 0) {
+    return nbmin <= NB_SMEM && slot_bytes<MAX_SG>(NB_SMEM, ngmax) <= SMEM_LIMIT ? NB_SMEM : 0;
 }
 
 // Candidate matrix of a whole 1024-thread CTA: row r holds, for every candidate c of the
@@ -1305,8 +1308,8 @@ static cudaError_t allow_smem(K kern) {
 }
 
 // whole-CTA shared memory: the part's records, then (1024-thread CTAs) the candidate matrix
-static size_t rounds_smem_full(int ngmax, int ct) {
-    const int nbsm = rounds_nbsm(ngmax);
+static size_t rounds_smem_full(int ngmax, int ct, int nbmin = 0) {
+    const int nbsm = rounds_nbsm(ngmax, nbmin);
     return slot_bytes<MAX_SG>(nbsm, ngmax) + (ct == 1024 ? (size_t)mat_rows(nbsm, ngmax) * MAT_ROW : 0);
 }
 
@@ -1320,10 +1323,10 @@ static int slot_nb(int ngq) {
 
 template <int CT, int SLOTS>
 static cudaError_t launch_rounds(const PartDesc *d_parts, int nparts, int nfull, uint32_t *d_next, int ngmax, int ngq,
-                                 int grid, cudaStream_t stream) {
+                                 int grid, cudaStream_t stream, int nbmin = 0) {
     int nbq = 0;
     int qmat = 0;
-    size_t smem = rounds_smem_full(ngmax, CT);
+    size_t smem = rounds_smem_full(ngmax, CT, nbmin);
     if constexpr (SLOTS > 1) {
         nbq = slot_nb<SLOTS>(ngq);
         // a 64 x 64 candidate matrix per slot where the slots' records leave room for it
@@ -1334,14 +1337,14 @@ static cudaError_t launch_rounds(const PartDesc *d_parts, int nparts, int nfull,
     if (smem > SMEM_LIMIT) return cudaErrorInvalidConfiguration;
     cudaError_t e = allow_smem(k_order_rounds<CT, SLOTS>);
     if (e != cudaSuccess) return e;
-    k_order_rounds<CT, SLOTS><<<grid, CT, smem, stream>>>(d_parts, nparts, nfull, d_next, ngmax, rounds_nbsm(ngmax),
-                                                           ngq, nbq, qmat);
+    k_order_rounds<CT, SLOTS><<<grid, CT, smem, stream>>>(d_parts, nparts, nfull, d_next, ngmax,
+                                                           rounds_nbsm(ngmax, nbmin), ngq, nbq, qmat);
     return cudaGetLastError();
 }
 
 template <int T>
 static cudaError_t launch_loop(const PartDesc *d_parts, int nparts, uint32_t *d_next, int ngmax, int grid,
-                               cudaStream_t stream, int algo) {
+                               cudaStream_t stream, int algo, int nbmin = 0) {
     if (algo == 1) {
         const size_t smem = (size_t)ngmax * 36;
         cudaError_t e = allow_smem(k_order_loop<T>);
@@ -1349,14 +1352,14 @@ static cudaError_t launch_loop(const PartDesc *d_parts, int nparts, uint32_t *d_
         k_order_loop<T><<<grid, T, smem, stream>>>(d_parts, nparts, d_next, ngmax);
         return cudaGetLastError();
     } else if constexpr (T >= CAP && T >= SMAX) {
-        return launch_rounds<T, 1>(d_parts, nparts, nparts, d_next, ngmax, 0, grid, stream);
+        return launch_rounds<T, 1>(d_parts, nparts, nparts, d_next, ngmax, 0, grid, stream, nbmin);
     } else {
         return cudaErrorInvalidConfiguration;  // the rounds kernel needs at least CAP threads
     }
 }
 
 template <int T>
-static int occupancy(int ngmax, int algo) {
+static int occupancy(int ngmax, int algo, int nbmin = 0) {
     int blocks = 0;
     cudaError_t e = cudaSuccess;
     if (algo == 1) {
@@ -1364,7 +1367,7 @@ static int occupancy(int ngmax, int algo) {
         allow_smem(k_order_loop<T>);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_order_loop<T>, T, smem);
     } else if constexpr (T >= CAP && T >= SMAX) {
-        const size_t smem = rounds_smem_full(ngmax, T);
+        const size_t smem = rounds_smem_full(ngmax, T, nbmin);
         allow_smem(k_order_rounds<T, 1>);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_order_rounds<T, 1>, T, smem);
     } else {
@@ -1441,29 +1444,33 @@ static cudaError_t launch_set(const PartDesc *d_parts, int nparts, uint32_t *d_n
             const int ngq = (int)ngs[nfull];
             // a small launch takes only the CTAs its parts fill (other launches share the GPU)
             const int grid = throughput ? std::min(sms, nfull + (nparts - nfull + slots - 1) / slots) : sms;
+            // buckets of the smallest whole-CTA part (none: no whole-CTA bucket records)
+            const int nbmin = nfull > 0 ? (int)((ns[nfull - 1] + 31u) / 32u) : NB_SMEM + 1;
             switch (slots) {
-                case 2: return launch_rounds<1024, 2>(d_parts, nparts, nfull, d_next, ngmax, ngq, grid, stream);
-                case 8: return launch_rounds<1024, 8>(d_parts, nparts, nfull, d_next, ngmax, ngq, grid, stream);
-                default: return launch_rounds<1024, 4>(d_parts, nparts, nfull, d_next, ngmax, ngq, grid, stream);
+                case 2: return launch_rounds<1024, 2>(d_parts, nparts, nfull, d_next, ngmax, ngq, grid, stream, nbmin);
+                case 8: return launch_rounds<1024, 8>(d_parts, nparts, nfull, d_next, ngmax, ngq, grid, stream, nbmin);
+                default: return launch_rounds<1024, 4>(d_parts, nparts, nfull, d_next, ngmax, ngq, grid, stream, nbmin);
             }
         }
     }
+    // every part of this launch runs on a whole CTA: the smallest one's buckets
+    const int nbmin = nparts > 0 ? (int)((ns[nparts - 1] + 31u) / 32u) : 0;
     int per_sm = 1;
     switch (T) {
-        case 64: per_sm = occupancy<64>(ngmax, algo); break;
-        case 128: per_sm = occupancy<128>(ngmax, algo); break;
-        case 256: per_sm = occupancy<256>(ngmax, algo); break;
-        case 512: per_sm = occupancy<512>(ngmax, algo); break;
-        default: per_sm = occupancy<1024>(ngmax, algo); break;
+        case 64: per_sm = occupancy<64>(ngmax, algo, nbmin); break;
+        case 128: per_sm = occupancy<128>(ngmax, algo, nbmin); break;
+        case 256: per_sm = occupancy<256>(ngmax, algo, nbmin); break;
+        case 512: per_sm = occupancy<512>(ngmax, algo, nbmin); break;
+        default: per_sm = occupancy<1024>(ngmax, algo, nbmin); break;
     }
     if (g_ctas_per_sm_override) per_sm = std::min(per_sm, g_ctas_per_sm_override);
     const int grid = std::max(1, std::min(nparts, sms * per_sm));
     switch (T) {
-        case 64: return launch_loop<64>(d_parts, nparts, d_next, ngmax, grid, stream, algo);
-        case 128: return launch_loop<128>(d_parts, nparts, d_next, ngmax, grid, stream, algo);
-        case 256: return launch_loop<256>(d_parts, nparts, d_next, ngmax, grid, stream, algo);
-        case 512: return launch_loop<512>(d_parts, nparts, d_next, ngmax, grid, stream, algo);
-        default: return launch_loop<1024>(d_parts, nparts, d_next, ngmax, grid, stream, algo);
+        case 64: return launch_loop<64>(d_parts, nparts, d_next, ngmax, grid, stream, algo, nbmin);
+        case 128: return launch_loop<128>(d_parts, nparts, d_next, ngmax, grid, stream, algo, nbmin);
+        case 256: return launch_loop<256>(d_parts, nparts, d_next, ngmax, grid, stream, algo, nbmin);
+        case 512: return launch_loop<512>(d_parts, nparts, d_next, ngmax, grid, stream, algo, nbmin);
+        default: return launch_loop<1024>(d_parts, nparts, d_next, ngmax, grid, stream, algo, nbmin);
     }
 }
 
