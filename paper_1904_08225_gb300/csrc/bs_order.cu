@@ -311,6 +311,22 @@ __device__ __forceinline__ uint32_t take_next(uint32_t *ctr, int lane) {
     return __shfl_sync(0xffffffffu, v, 0);
 }
 
+
+// L2 eviction priority as a per-access cache hint (a policy operand of the load or store)
+__device__ __forceinline__ uint64_t l2_first_policy() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t ld_hint_u64(const void *a, uint64_t pol) {
+    uint64_t v;
+    asm volatile("ld.global.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_hint_u64(void *a, uint64_t v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.u64 [%0], %1, %2;" :: "l"(a), "l"(v), "l"(pol));
+}
+
 // A box with its corners unpacked.
 struct Box {
     int32_t lx, ly, lz, hx, hy, hz;
@@ -365,6 +381,12 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
     // the candidate matrix: rows of MS entries, CAP on whole 1024-thread CTAs and 64 in
     // part slots (rounds of at most 64 candidates there: the slots share the CTA's memory)
     constexpr bool MATRIX = !CL;
+    // parts on fewer than 1024 threads (part slots, and the CTAs of smaller parts) read
+    // and write their distances and keys with an L2 evict-first hint: the many parts of
+    // such launches stream through L2, and the hint leaves the lines of the large parts
+    // on 1024-thread CTAs (the longest chains, often running alongside) in place longer
+    constexpr bool STREAM = TP < 1024 && !CL;
+    const uint64_t pol = STREAM ? l2_first_policy() : 0ull;
     constexpr int MS = TP == 1024 ? CAP : 64;
     constexpr int CPLM = MS / 32;
     // the sampler (variant 1) sorts its sample with one thread per entry: slots of fewer
@@ -674,8 +696,8 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
                     for (int u = 0; u < LB; ++u) {
                         const uint32_t i = (g * 32 + (u < nb8 ? bbs[u] : 0)) * 32 + lane;
                         const bool ok = u < nb8 && i < n;
-                        d[u] = ok ? Dg[i] : -1;
-                        ki[u] = ok ? key[i] : 0ull;
+                        d[u] = ok ? (STREAM ? (int64_t)ld_hint_u64(&Dg[i], pol) : Dg[i]) : -1;
+                        ki[u] = ok ? (STREAM ? ld_hint_u64(&key[i], pol) : key[i]) : 0ull;
                     }
 #pragma unroll
                     for (int u = 0; u < LB; ++u) {
@@ -1085,8 +1107,8 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
                 for (int u = 0; u < LB; ++u) {
                     const uint32_t i = (g * 32 + (u < nb8 ? bbs[u] : 0)) * 32 + lane;
                     const bool ok = u < nb8 && i < n;
-                    d[u] = ok ? Dg[i] : -1;
-                    ki[u] = ok ? key[i] : 0ull;
+                    d[u] = ok ? (STREAM ? (int64_t)ld_hint_u64(&Dg[i], pol) : Dg[i]) : -1;
+                    ki[u] = ok ? (STREAM ? ld_hint_u64(&key[i], pol) : key[i]) : 0ull;
                 }
 #pragma unroll
                 for (int u = 0; u < LB; ++u) {
@@ -1107,7 +1129,8 @@ __device__ __forceinline__ void rounds_part(const PartDesc &P, RoundsSm<SG> &Sm,
                         }
                         if (dd > 0 && nd < dd) {  // chosen points (-1) and duplicates (0) stay
                             dd = nd;
-                            Dg[i] = nd;
+                            if (STREAM) st_hint_u64(&Dg[i], (uint64_t)nd, pol);
+                            else Dg[i] = nd;
                         }
                     }
                     const uint64_t nk = i < n ? (((uint64_t)(dd + 1) << 5) | (uint64_t)(31 - lane)) : 0ull;
