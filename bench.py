@@ -54,7 +54,7 @@ BYTES_OUT = 16         # perm 4 + rad2 8 + radius 4
 # seeded 1216-part subset of that band (bench.py --order-subset 1216), scaled per surfel:
 # profiles/k_order_rounds_traffic_subset1216.md.  Must be re-measured (or set to None)
 # whenever k_order_rounds changes.
-DRAM_BYTES_PER_SURFEL = 1073.6
+DRAM_BYTES_PER_SURFEL = 1613.3
 
 
 def band_layout(ns, thresholds):
