@@ -550,15 +550,20 @@ def main():
         e2e_calls.append((hm, (C.c_int * k)(*[specs[i].res for i in range(p0, p1)]), k,
                           (bs.OrderOpts * k)(*[opts[i] for i in range(p0, p1)]), ho, csx))
 
+    e2e_band_ms = {}
+
     def step_e2e():
         errs = []
+        t0 = time.perf_counter()
 
-        def call(args):
+        def call(j, args):
             hm, hres, k, hopts, ho, csx = args
             st = lib.bs_sample_order_batched(hm, hres, k, dirs, 6, hopts, ho, 0, csx)
+            # host wall time from the step's start to this band's return (results on the host)
+            e2e_band_ms[j] = round((time.perf_counter() - t0) * 1e3, 2)
             if st != bs.BS_OK:
                 errs.append(bs.BsError(st, "bs_sample_order_batched", bs.last_error()))
-        th = [threading.Thread(target=call, args=(a,)) for a in e2e_calls]
+        th = [threading.Thread(target=call, args=(j, a)) for j, a in enumerate(e2e_calls)]
         for t in th:
             t.start()
         for t in th:
@@ -696,6 +701,7 @@ def main():
                                                   "step_milestones_ms": breakdown},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d_bytes),
                     "d2h_bytes_per_step": int(d2h_bytes)},
+            "e2e_band_returned_ms": {f"band{j}": v for j, v in sorted(e2e_band_ms.items())},
             "gpu_launches": args.steps * (nsample_kernels + 3) * (1 + sum(1 for g in leads if g)),
             "roofline": {"bound": "hbm", "kernel": "k_order_rounds", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak,
